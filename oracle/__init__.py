@@ -1,0 +1,269 @@
+"""CPU oracle for the 3D Jacobi stencil path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` / ``--impl reference`` legs may import this package.  The
+product package ``paper_2409_18824_gb300`` never imports it and it never
+imports the product: the two share no code.  Inputs come from the seeded
+generators in ``stencil_inputs`` (random numbers and shapes only).
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, k-j-i loops,
+built with ``-O2 -ffp-contract=off`` so that no multiply-add is fused).  This
+module compiles it with gcc into ``liboracle.so`` beside the source and wraps
+each function for numpy arrays laid out as the library expects: a C-contiguous
+array of shape (nz+2r, ny+2r, nx+2r), which is the Fortran column-major array
+u(1:nx+2r, 1:ny+2r, 1:nz+2r) (arXiv 2409.18824 Sec. 5.2, Listing 7).
+
+Pins (tests/test_oracle.py): closed-form eigenmode decay, constant and linear
+invariants, dense brute force, Gaussian elimination, symmetry of the
+variable-coefficient operator.  The refinement driver
+(``varcoef_refined_solve``) is pinned only through its end state (the double
+residual it reports is recomputed independently) -- its inner steps are
+"parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64 = ctypes.c_int64
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, no FP contraction, OpenMP off)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        sig = {
+            "oracle_sweep_f64": (None, [_dp, _dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int]),
+            "oracle_sweep_f32": (None, [_fp, _fp, _fp, _i64, _i64, _i64, _fp, ctypes.c_int]),
+            "oracle_stencil_sweep_f64": (ctypes.c_int, [_dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int, _i64]),
+            "oracle_stencil_sweep_f32": (ctypes.c_int, [_fp, _fp, _i64, _i64, _i64, _fp, ctypes.c_int, _i64]),
+            "oracle_residual_norm_f64": (ctypes.c_double, [_dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int]),
+            "oracle_residual_norm_f32": (ctypes.c_double, [_fp, _fp, _i64, _i64, _i64, _fp, ctypes.c_int]),
+            "oracle_interior_norm_f64": (ctypes.c_double, [_dp, _i64, _i64, _i64, ctypes.c_int]),
+            "oracle_jacobi_solve_f64": (ctypes.c_int, [_dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int,
+                                                       ctypes.c_double, _i64, _i64,
+                                                       ctypes.POINTER(_i64), _dp]),
+            "oracle_varcoef_apply_f64": (None, [_dp, _dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int]),
+            "oracle_varcoef_sweep_f64": (None, [_dp, _dp, _dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int]),
+            "oracle_varcoef_sweep_f32": (None, [_fp, _fp, _fp, _fp, _i64, _i64, _i64, _fp, ctypes.c_int]),
+            "oracle_varcoef_residual_norm_f64": (ctypes.c_double, [_dp, _dp, _dp, _i64, _i64, _i64, _dp,
+                                                                   ctypes.c_int]),
+            "oracle_varcoef_jacobi_solve_f64": (ctypes.c_int, [_dp, _dp, _dp, _i64, _i64, _i64, _dp,
+                                                               ctypes.c_int, ctypes.c_double, _i64, _i64,
+                                                               ctypes.POINTER(_i64), _dp]),
+            "oracle_varcoef_refined_solve": (ctypes.c_int, [_dp, _dp, _dp, _i64, _i64, _i64, _dp,
+                                                            ctypes.c_int, ctypes.c_double, _i64, _i64,
+                                                            ctypes.POINTER(_i64), _dp]),
+            "oracle_dense_solve": (ctypes.c_int, [_dp, _dp, _i64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _grid(a: np.ndarray, dtype) -> np.ndarray:
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"] or a.ndim != 3:
+        raise ValueError(f"oracle wants a C-contiguous 3D {np.dtype(dtype).name} array, got "
+                         f"{a.dtype} {a.shape}")
+    return a
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def interior_shape(u: np.ndarray, r: int):
+    nz, ny, nx = (s - 2 * r for s in u.shape)
+    if min(nx, ny, nz) < 1:
+        raise ValueError("grid smaller than its halo")
+    return nx, ny, nz
+
+
+def sweep(u: np.ndarray, coeffs, r: int, b: np.ndarray | None = None) -> np.ndarray:
+    """One sweep; returns a new padded array whose halo is u's halo."""
+    lib = _load()
+    if u.dtype == np.float64:
+        _grid(u, np.float64)
+        out = u.copy()
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        if b is not None:
+            _grid(b, np.float64)
+        lib.oracle_sweep_f64(_ptr(u, ctypes.c_double), _ptr(b, ctypes.c_double), _ptr(out, ctypes.c_double),
+                             *interior_shape(u, r), _ptr(c, ctypes.c_double), r)
+    elif u.dtype == np.float32:
+        _grid(u, np.float32)
+        out = u.copy()
+        c = np.asarray(coeffs, dtype=np.float64).astype(np.float32)
+        if b is not None:
+            _grid(b, np.float32)
+        lib.oracle_sweep_f32(_ptr(u, ctypes.c_float), _ptr(b, ctypes.c_float), _ptr(out, ctypes.c_float),
+                             *interior_shape(u, r), _ptr(c, ctypes.c_float), r)
+    else:
+        raise TypeError(u.dtype)
+    return out
+
+
+def stencil_sweep(u: np.ndarray, coeffs, r: int, iters: int) -> np.ndarray:
+    """`iters` sweeps (no source term), returns the final padded grid."""
+    lib = _load()
+    out = np.empty_like(u)
+    if u.dtype == np.float64:
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        rc = lib.oracle_stencil_sweep_f64(_ptr(u, ctypes.c_double), _ptr(out, ctypes.c_double),
+                                          *interior_shape(u, r), _ptr(c, ctypes.c_double), r, iters)
+    else:
+        c = np.asarray(coeffs, dtype=np.float64).astype(np.float32)
+        rc = lib.oracle_stencil_sweep_f32(_ptr(_grid(u, np.float32), ctypes.c_float), _ptr(out, ctypes.c_float),
+                                          *interior_shape(u, r), _ptr(c, ctypes.c_float), r, iters)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def residual_norm(u: np.ndarray, coeffs, r: int, b: np.ndarray | None = None) -> float:
+    lib = _load()
+    if u.dtype == np.float64:
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        return lib.oracle_residual_norm_f64(_ptr(_grid(u, np.float64), ctypes.c_double), _ptr(b, ctypes.c_double),
+                                            *interior_shape(u, r), _ptr(c, ctypes.c_double), r)
+    c = np.asarray(coeffs, dtype=np.float64).astype(np.float32)
+    return lib.oracle_residual_norm_f32(_ptr(_grid(u, np.float32), ctypes.c_float), _ptr(b, ctypes.c_float),
+                                        *interior_shape(u, r), _ptr(c, ctypes.c_float), r)
+
+
+def interior_norm(x: np.ndarray, r: int) -> float:
+    lib = _load()
+    return lib.oracle_interior_norm_f64(_ptr(_grid(x, np.float64), ctypes.c_double), *interior_shape(x, r), r)
+
+
+def jacobi_solve(b: np.ndarray | None, u0: np.ndarray, coeffs, r: int, tol: float, max_iters: int,
+                 check_every: int):
+    """Returns (u, iters, rel_res, status) with status 0 converged / 1 not."""
+    lib = _load()
+    u = _grid(u0, np.float64).copy()
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    it = _i64(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.oracle_jacobi_solve_f64(_ptr(b, ctypes.c_double), _ptr(u, ctypes.c_double), *interior_shape(u, r),
+                                     _ptr(c, ctypes.c_double), r, tol, max_iters, check_every,
+                                     ctypes.byref(it), ctypes.byref(rel))
+    if st < 0:
+        raise MemoryError("oracle allocation failed")
+    return u, it.value, rel.value, st
+
+
+def _w3(w):
+    w = np.asarray(w, dtype=np.float64)
+    out = np.zeros(3, dtype=np.float64)
+    out[1:1 + len(w) - 1] = w[1:]
+    return out
+
+
+def varcoef_apply(u: np.ndarray, a: np.ndarray, w, R: int) -> np.ndarray:
+    """A u on the interior (halo of the result: zero)."""
+    lib = _load()
+    out = np.zeros_like(_grid(u, np.float64))
+    ww = _w3(w)
+    lib.oracle_varcoef_apply_f64(_ptr(u, ctypes.c_double), _ptr(_grid(a, np.float64), ctypes.c_double),
+                                 _ptr(out, ctypes.c_double), *interior_shape(u, R), _ptr(ww, ctypes.c_double), R)
+    return out
+
+
+def varcoef_sweep(u: np.ndarray, a: np.ndarray, f: np.ndarray, w, R: int) -> np.ndarray:
+    lib = _load()
+    out = u.copy()
+    if u.dtype == np.float64:
+        ww = _w3(w)
+        lib.oracle_varcoef_sweep_f64(_ptr(u, ctypes.c_double), _ptr(_grid(a, np.float64), ctypes.c_double),
+                                     _ptr(_grid(f, np.float64), ctypes.c_double), _ptr(out, ctypes.c_double),
+                                     *interior_shape(u, R), _ptr(ww, ctypes.c_double), R)
+    else:
+        ww = _w3(w).astype(np.float32)
+        lib.oracle_varcoef_sweep_f32(_ptr(_grid(u, np.float32), ctypes.c_float),
+                                     _ptr(_grid(a, np.float32), ctypes.c_float),
+                                     _ptr(_grid(f, np.float32), ctypes.c_float), _ptr(out, ctypes.c_float),
+                                     *interior_shape(u, R), _ptr(ww, ctypes.c_float), R)
+    return out
+
+
+def varcoef_residual_norm(u: np.ndarray, a: np.ndarray, f: np.ndarray, w, R: int) -> float:
+    lib = _load()
+    ww = _w3(w)
+    return lib.oracle_varcoef_residual_norm_f64(_ptr(_grid(u, np.float64), ctypes.c_double),
+                                                _ptr(_grid(a, np.float64), ctypes.c_double),
+                                                _ptr(_grid(f, np.float64), ctypes.c_double),
+                                                *interior_shape(u, R), _ptr(ww, ctypes.c_double), R)
+
+
+def varcoef_jacobi_solve(a, f, u0, w, R, tol, max_iters, check_every):
+    lib = _load()
+    u = _grid(u0, np.float64).copy()
+    ww = _w3(w)
+    it = _i64(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.oracle_varcoef_jacobi_solve_f64(_ptr(_grid(a, np.float64), ctypes.c_double),
+                                             _ptr(_grid(f, np.float64), ctypes.c_double),
+                                             _ptr(u, ctypes.c_double), *interior_shape(u, R),
+                                             _ptr(ww, ctypes.c_double), R, tol, max_iters, check_every,
+                                             ctypes.byref(it), ctypes.byref(rel))
+    if st < 0:
+        raise MemoryError("oracle allocation failed")
+    return u, it.value, rel.value, st
+
+
+def varcoef_refined_solve(a, f, u0, w, R, tol, inner_sweeps, max_outer):
+    lib = _load()
+    u = _grid(u0, np.float64).copy()
+    ww = _w3(w)
+    outer = _i64(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.oracle_varcoef_refined_solve(_ptr(_grid(a, np.float64), ctypes.c_double),
+                                          _ptr(_grid(f, np.float64), ctypes.c_double),
+                                          _ptr(u, ctypes.c_double), *interior_shape(u, R),
+                                          _ptr(ww, ctypes.c_double), R, tol, inner_sweeps, max_outer,
+                                          ctypes.byref(outer), ctypes.byref(rel))
+    if st < 0:
+        raise MemoryError("oracle allocation failed")
+    return u, outer.value, rel.value, st
+
+
+def dense_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Gaussian elimination with partial pivoting (textbook, in oracle.c)."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64).copy()
+    x = np.ascontiguousarray(b, dtype=np.float64).copy()
+    n = A.shape[0]
+    if lib.oracle_dense_solve(_ptr(A, ctypes.c_double), _ptr(x, ctypes.c_double), n) != 0:
+        raise np.linalg.LinAlgError("singular")
+    return x
