@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of the 3D Jacobi stencil path on GB300 (one JSON line on stdout).
+
+Workload (default, `--workload sweep512`): the 7-point FP64 Jacobi sweep on a
+512x512x512 interior (Fortran layout, 1-cell zero Dirichlet halo, interior
+U[0,1) from PCG64 seed 2, coefficients {0, 1/6}); one STEP is the whole job of
+that configuration: 1000 sweeps (stencil_sweep_f64) followed by the fused
+residual-norm reduction of the result (residual_norm_f64).  GLUP/s counts the
+1000 sweeps only.  Each array is 1 GiB (> 129 MB of L2), so no flush is needed
+between steps.  The paper's own jacobi benchmark (arXiv 2409.18824 Sec. 4) is
+a 2D 1024^2 CPU run; its data are not published and this seeded grid stands in
+for it.
+
+Arms:
+  default            the CUDA library through its C ABI, device-resident grids;
+                     `e2e` repeats the step with pinned HOST grids (the library
+                     stages them: H2D + D2H inside the timed region).
+  --impl reference   the CPU oracle as it stands, on the host cores, each step
+                     a bounded sample of the same workload (see `sample`).
+
+Multi-GPU: the path does not shard (one grid per GPU, no exchange), so with
+torchrun each rank runs an independent replica; value = all ranks' updates /
+the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import stencil_inputs as si  # noqa: E402
+
+WORKLOADS = {
+    # name: (nx, ny, nz, r, sweeps, dtype, seed)
+    "sweep512": dict(nx=512, ny=512, nz=512, r=1, sweeps=1000, dtype="f64", seed=2,
+                     desc="7-point Jacobi, 512^3 FP64, zero halo, interior U[0,1) seed 2, "
+                          "1000 sweeps + residual L2 norm"),
+    "sweep64": dict(nx=64, ny=64, nz=64, r=1, sweeps=100, dtype="f64", seed=1,
+                    desc="7-point Jacobi, 64^3 FP64, zero halo, interior U[0,1) seed 1, "
+                         "100 sweeps + residual L2 norm"),
+    "sweep512f32": dict(nx=512, ny=512, nz=512, r=1, sweeps=1000, dtype="f32", seed=2,
+                        desc="7-point Jacobi, 512^3 FP32, zero halo, interior U[0,1) seed 2, "
+                             "1000 sweeps + residual L2 norm"),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 issue rate of this GPU measured with a throughput probe: 2 double
+# fused-multiply-add instructions per clock per SM (every double add and
+# multiply of the sweep is issued as one), 152 SMs.
+FP64_OPS_PER_CLK_SM = 2.0
+N_SM = 152
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [v for v in sm if v > 0.5 * (mx or max(sm))] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- CUDA arm --
+def run_cuda(args, wl):
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    nx, ny, nz, r, sweeps = wl["nx"], wl["ny"], wl["nz"], wl["r"], wl["sweeps"]
+    f64 = wl["dtype"] == "f64"
+    npdt = np.float64 if f64 else np.float32
+    esize = 8 if f64 else 4
+    coeffs = si.LAPLACE7
+    u0 = si.uniform_interior(nx, ny, nz, r, seed=wl["seed"] + rank, dtype=npdt)
+    d_in = torch.from_numpy(u0).to(dev)
+    d_out = torch.empty_like(d_in)
+    sweep = stn.stencil_sweep_f64 if f64 else stn.stencil_sweep_f32
+    resid = stn.residual_norm_f64 if f64 else stn.residual_norm_f32
+    apply_ = stn.stencil_apply_f64 if f64 else stn.stencil_apply_f32
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sweep(d_in, d_out, coeffs, r, sweeps)
+        return resid(d_out, coeffs, r)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    norms = []
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t_wall0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            norms.append(step())
+        e1.record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    lups_rank = float(nx) * ny * nz * sweeps * args.steps
+    value = lups_rank * ws / (ms * 1e-3) / 1e9
+
+    # Dominant kernel alone: back-to-back single-sweep launches (stencil_apply,
+    # one kernel each) between two events on the launching stream.
+    n_apply = 20 if f64 else 60
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        apply_(d_in, d_out, coeffs, r)
+    torch.cuda.synchronize(dev)
+    a0.record(stream)
+    for i in range(n_apply):
+        if i % 2 == 0:
+            apply_(d_in, d_out, coeffs, r)
+        else:
+            apply_(d_out, d_in, coeffs, r)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    kern_ms = a0.elapsed_time(a1) / n_apply
+
+    # the same kernel's share inside the timed region
+    step_ms = ms / args.steps
+    launch_ms_in_step = step_ms / (sweeps + 1)
+
+    # e2e through the C ABI with pinned host grids
+    h_in = torch.from_numpy(u0).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    hin_np, hout_np = h_in.numpy(), h_out.numpy()
+    sweep(hin_np, hout_np, coeffs, r, sweeps)  # warm the staging path
+    resid(hout_np, coeffs, r)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sweep(hin_np, hout_np, coeffs, r, sweeps)
+        resid(hout_np, coeffs, r)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    grid_bytes = u0.nbytes
+    h2d = grid_bytes * 2        # in for the sweeps, out for the norm
+    d2h = grid_bytes * 2 + 8    # out, clobbered in, and the norm
+    e2e_val = float(nx) * ny * nz * sweeps / e2e_s / 1e9
+
+    peaks, peak_kind = load_peaks()
+    clocks = clk.summary()
+    lups_kernel = float(nx) * ny * nz
+    bytes_alg = 2.0 * esize * lups_kernel           # read u, write out: compulsory traffic
+    hbm_gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks["hbm_gbs"])
+    if f64:
+        # the double sweep is bound by the FP64 pipe: 6 double ops per update
+        ops = 6.0 * lups_kernel
+        sm_clock = float(peaks.get("sm_max_mhz", 2070.0))
+        fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_clock * 1e6 / 1e12  # Tops/s
+        achieved = ops / (kern_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None,
+                    "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
+                    "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
+                    "hbm_peak_kind": peak_kind, "kernel_ms": kern_ms, "kernel_ms_in_step": launch_ms_in_step}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                    "kernel_ms": kern_ms, "kernel_ms_in_step": launch_ms_in_step}
+
+    out = {
+        "metric": "GLUP/s (512^3 7-point Jacobi, FP64)" if wl is WORKLOADS["sweep512"] else f"GLUP/s ({args.workload})",
+        "value": value,
+        "unit": "GLUP/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": wl["dtype"],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "nx": nx, "ny": ny, "nz": nz, "radius": r,
+                   "sweeps_per_step": sweeps, "l2": "inputs larger than L2 (1 GiB per grid), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": {"value": e2e_val, "unit": "GLUP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (1 + sweeps + 2),
+        "roofline": roofline,
+        "clocks": clocks,
+        "wall_s_timed": t_wall,
+        "residual_norm": norms[-1],
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sweeps)
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ oracle (CPU) --
+def cpu_sample(wl, sweeps):
+    import oracle
+    nx, ny, nz, r = wl["nx"], wl["ny"], wl["nz"], wl["r"]
+    npdt = np.float64 if wl["dtype"] == "f64" else np.float32
+    u0 = si.uniform_interior(nx, ny, nz, r, seed=wl["seed"], dtype=npdt)
+    oracle.build()
+    t0 = time.perf_counter()
+    out = oracle.stencil_sweep(u0, si.LAPLACE7, r, sweeps)
+    oracle.residual_norm(out, si.LAPLACE7, r)
+    t = time.perf_counter() - t0
+    return float(nx) * ny * nz * sweeps / t / 1e9, t
+
+
+def cpu_baseline(wl, sweeps):
+    val, t = cpu_sample(wl, sweeps)
+    return {"value": val, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} sweeps + 1 residual norm of the same {wl['nx']}x{wl['ny']}x{wl['nz']} "
+                      f"grid, plain C oracle, single thread ({t:.1f} s)"}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    times = []
+    sweeps = args.cpu_sweeps
+    for _ in range(args.warmup):
+        cpu_sample(wl, 1)
+    for _ in range(args.steps):
+        _, t = cpu_sample(wl, sweeps)
+        times.append(t)
+    total = sum(times)
+    value = float(wl["nx"]) * wl["ny"] * wl["nz"] * sweeps * args.steps / total / 1e9
+    out = {
+        "impl": "reference",
+        "metric": "GLUP/s (512^3 7-point Jacobi, FP64)" if wl is WORKLOADS["sweep512"] else f"GLUP/s ({args.workload})",
+        "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+        "config": {"workload": wl["desc"], "nx": wl["nx"], "ny": wl["ny"], "nz": wl["nz"], "radius": wl["r"],
+                   "sweeps_per_step": sweeps, "parallelism": "single"},
+        "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {sweeps} sweeps + 1 residual norm of the workload's grid "
+                                   f"(plain C oracle, one thread) instead of the full sweep count"},
+        "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("steps >= 1, warmup >= 0")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_cuda(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * stencil.h -- C ABI of libstencil.so: iterated 3D structured-grid Jacobi
+ * stencil sweeps with a fused residual-norm reduction, on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * The operation is the "jacobi" benchmark of arXiv 2409.18824 (Sec. 4: a
+ * Jacobi iteration solving Laplace's equation on a structured grid), which
+ * the paper's compiler flow expresses as a stencil (Sec. 2.2) plus a sum
+ * reduction (Sec. 5.3, Listing 8).  Here it is three-dimensional.
+ *
+ * ---------------------------------------------------------------- layout ---
+ * Every grid argument is a Fortran array  u(1:nx+2r, 1:ny+2r, 1:nz+2r)  in
+ * column-major order: element (i,j,k) (1-based) sits at 0-based offset
+ *     (i-1) + (j-1)*NX + (k-1)*NX*NY,   NX = nx+2r, NY = ny+2r, NZ = nz+2r
+ * (Sec. 5.2, Listing 7: subtract the lower bound, first index fastest).
+ * nx, ny, nz are the INTERIOR extents; r is the stencil radius.  The outer r
+ * layers on every face are the Dirichlet halo: read, never written by a
+ * sweep.  A C caller sees the same memory as a row-major array [NZ][NY][NX].
+ * A grid holds NX*NY*NZ elements; no padding, no pitch.
+ *
+ * ---------------------------------------------------------------- stencil ---
+ * Constant-coefficient star stencil, radius r in {1, 2}, coefficients
+ * coeffs[0..r] (a HOST array of r+1 doubles): for each interior point
+ *     out = c0*u + sum_{d=1..r} c_d * S_d  (+ b)
+ *     S_d = ((u(i-d)+u(i+d)) + (u(j-d)+u(j+d))) + (u(k-d)+u(k+d))
+ * evaluated in exactly this order: acc = c_r*S_r, then acc += c_d*S_d for
+ * d = r-1..1, then acc += c0*u if c0 != 0, then acc += b if b is given; every
+ * product and sum rounded separately (no fused multiply-add), so the double
+ * path is bitwise reproducible.  The 7-point Laplace update is r = 1,
+ * coeffs = {0, 1/6}.  The _f32 entry points round the coefficients to float
+ * and compute in float.
+ *
+ * ------------------------------------------------------- pointers/streams ---
+ * Grid pointers may be DEVICE memory (cudaMalloc, a torch CUDA tensor) or
+ * HOST memory (pageable or pinned).  When every grid argument of a call is in
+ * device memory the call is asynchronous on `stream` (a cudaStream_t passed as
+ * void*; NULL = the legacy default stream) unless stated otherwise.  When any
+ * grid argument is host memory the library stages all of them through device
+ * memory it allocates for the call, runs on `stream`, copies the outputs back
+ * and synchronises `stream` before returning.  Mixing host and device grids in
+ * one call is allowed.  The caller owns every pointer it passes; the library
+ * keeps none of them after the call returns.
+ *
+ * Workspace: the library owns a small per-(device, stream) workspace
+ * (reduction partials, status words, one grid-sized ping-pong buffer for the
+ * solvers), allocated on first use and reused; stencil_release_workspace()
+ * frees it.  Calls on the same stream are ordered; calls on different streams
+ * use different workspaces.
+ *
+ * ------------------------------------------------------------------ errors ---
+ * Every entry point returns an int status.  It never aborts, exits or traps.
+ * On a negative status nothing asynchronous was left running by the call;
+ * outputs are unspecified.  stencil_last_error() gives a message for the last
+ * failing call on the calling thread.
+ */
+#ifndef STENCIL_H_
+#define STENCIL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STN_OK = 0,             /* success */
+  STN_NOT_CONVERGED = 1,  /* solver: result valid, tolerance not reached */
+  STN_EINVAL = -1,        /* bad argument: NULL, extent < 1, radius not 1/2, iters < 0,
+                             in == out or overlapping, unsupported pointer kind */
+  STN_ENOMEM = -2,        /* device or host allocation failed */
+  STN_ECUDA = -3,         /* a CUDA runtime call failed (message in stencil_last_error) */
+  STN_ETIMEOUT = -4,      /* a device-side wait reached its spin limit */
+  STN_EBUSY = -5          /* admission refused (server over its memory budget) */
+};
+
+/* Result of a solve (host struct filled by the solvers). */
+typedef struct stn_solve_info {
+  int64_t iters;     /* sweeps performed (inner float sweeps for the refined solver) */
+  int64_t outer;     /* refinement steps (0 for plain Jacobi) */
+  double rel_res;    /* last measured ||rho||/||rhs|| (absolute ||rho|| if ||rhs|| = 0) */
+  double res_norm;   /* last measured ||rho||_2 */
+  double rhs_norm;   /* ||rhs||_2 over the interior */
+  int status;        /* STN_OK or STN_NOT_CONVERGED */
+} stn_solve_info;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* stencil_last_error(void);
+
+/* Library version string. */
+const char* stencil_version(void);
+
+/* Frees every workspace the library holds on the current device.  Returns
+ * STN_OK, or STN_ECUDA.  Not safe while calls are in flight on that device. */
+int stencil_release_workspace(void);
+
+/*
+ * stencil_sweep_f64 / _f32 -- `iters` Jacobi sweeps of the constant-
+ * coefficient star stencil (no source term).  Sec. 4 (the benchmark repeats
+ * the sweep a fixed number of iterations).
+ *   in      grid holding the starting iterate (its halo is the boundary);
+ *           its INTERIOR is clobbered when iters > 1 (used as the ping-pong
+ *           buffer); unchanged when iters <= 1.
+ *   out     grid receiving the result: interior = iterate number `iters`,
+ *           halo = in's halo.  iters == 0 copies in to out.
+ *   coeffs  host, radius+1 doubles {c0, c1[, c2]}.
+ *   radius  1 or 2.
+ *   iters   >= 0.
+ * Errors: STN_EINVAL (NULL grid or coeffs, extents < 1, radius not 1/2,
+ * iters < 0, in and out overlap), STN_ENOMEM, STN_ECUDA.
+ */
+int stencil_sweep_f64(double* in, double* out, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, int64_t iters, void* stream);
+int stencil_sweep_f32(float* in, float* out, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, int64_t iters, void* stream);
+
+/*
+ * stencil_apply_f64 / _f32 -- ONE application of the star stencil (the
+ * stencil.apply of Sec. 2.2): out = S u + b on the interior, one kernel
+ * launch, asynchronous on `stream`.  The halo of `out` is not written.
+ *   u       grid (read only); b: source grid or NULL (read only).
+ *   out     grid; must not overlap u or b.  Device memory only (no staging).
+ * Errors: STN_EINVAL (NULL u/out/coeffs, bad extents/radius, overlap, a host
+ * pointer), STN_ECUDA.
+ */
+int stencil_apply_f64(const double* u, const double* b, double* out, int64_t nx, int64_t ny,
+                      int64_t nz, const double* coeffs, int radius, void* stream);
+int stencil_apply_f32(const float* u, const float* b, float* out, int64_t nx, int64_t ny,
+                      int64_t nz, const double* coeffs, int radius, void* stream);
+
+/*
+ * residual_norm_f64 / _f32 -- ||rho||_2 with rho = (S u + b) - u over the
+ * interior, i.e. the change one more sweep would make (Sec. 5.3, Listing 8:
+ * sum reduction from zero with an add combiner, here of rho^2, accumulated in
+ * double in a fixed order that depends only on the extents, then sqrt).
+ *   u         grid (read only).
+ *   b         grid of the source term, or NULL for none (read only; its halo
+ *             is not read).
+ *   norm_out  HOST double receiving the norm.  The call synchronises `stream`.
+ * For _f32 the stencil value is computed in float; rho and its square in
+ * double.
+ * Errors: STN_EINVAL (NULL u/coeffs/norm_out, bad extents or radius),
+ * STN_ENOMEM, STN_ECUDA.
+ */
+int residual_norm_f64(const double* u, const double* b, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, double* norm_out, void* stream);
+int residual_norm_f32(const float* u, const float* b, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, double* norm_out, void* stream);
+
+/*
+ * jacobi_solve_f64 -- solve u = S u + rhs by Jacobi iteration (Sec. 4).
+ * Sweeps run in groups of `check_every` (>= 1); the last sweep of each group
+ * is fused with the residual reduction of the iterate it starts from.  The
+ * solve stops after the first group whose measured ||rho|| <= tol*||rhs||
+ * (absolute ||rho|| <= tol when ||rhs|| = 0 or rhs == NULL), or after
+ * max_iters sweeps.
+ *   rhs       grid of the source term b (read only), or NULL for b = 0.
+ *   u         in: initial guess and Dirichlet halo; out: the last iterate
+ *             (one sweep past the iterate whose residual was measured).
+ *   info      HOST, filled on return (may be NULL).
+ * The call synchronises `stream`.  Returns STN_OK, STN_NOT_CONVERGED, or an
+ * error (STN_EINVAL for tol < 0, max_iters < 0, check_every < 1, ...).
+ */
+int jacobi_solve_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64_t nz,
+                     const double* coeffs, int radius, double tol, int64_t max_iters,
+                     int64_t check_every, stn_solve_info* info, void* stream);
+
+/*
+ * Variable-coefficient operator, radius R in {1, 2}, weights w[0..R] (HOST;
+ * w[0] unused), per-point coefficient field a on the full padded grid:
+ *   (A u)(p) = sum_{d=1..R} w_d sum_{q = p +- d e_x, e_y, e_z} kappa(p,q) (u(p) - u(q)),
+ *   kappa(p,q) = (a(p) + a(q)) / 2.
+ * With D(p) = sum w_d kappa and N(p) = sum w_d kappa u(q), both accumulated
+ * over d = 1..R, then axes x, y, z, minus neighbour before plus neighbour:
+ *   Jacobi update  u'(p) = (f(p) + N(p)) / D(p);   (A u)(p) = D(p) u(p) - N(p).
+ * The paper states only Laplace's equation (Sec. 4); this symmetric
+ * M-matrix form is the reading used for the variable-coefficient Poisson
+ * workload (a ~ U[0.5,1.5], w = {-, 1, 1/4}).
+ */
+
+/* out = A u on the interior; the halo of out is not written. */
+int varcoef_apply_f64(const double* u, const double* a, double* out, int64_t nx, int64_t ny,
+                      int64_t nz, const double* w, int radius, void* stream);
+
+/* `iters` Jacobi sweeps for A u = f; in/out semantics as stencil_sweep_f64
+ * (in's interior clobbered when iters > 1).  _f32 takes float a, f, grids;
+ * weights rounded to float. */
+int varcoef_sweep_f64(double* in, double* out, const double* a, const double* f, int64_t nx,
+                      int64_t ny, int64_t nz, const double* w, int radius, int64_t iters,
+                      void* stream);
+int varcoef_sweep_f32(float* in, float* out, const float* a, const float* f, int64_t nx,
+                      int64_t ny, int64_t nz, const double* w, int radius, int64_t iters,
+                      void* stream);
+
+/* ||f - A u||_2 over the interior, in double (host result; synchronises). */
+int varcoef_residual_norm_f64(const double* u, const double* a, const double* f, int64_t nx,
+                              int64_t ny, int64_t nz, const double* w, int radius,
+                              double* norm_out, void* stream);
+
+/* Plain double Jacobi solve of A u = f, same grouping/stopping rule as
+ * jacobi_solve_f64 with rho = f - A u.  Synchronises. */
+int jacobi_solve_varcoef_f64(const double* a, const double* f, double* u, int64_t nx, int64_t ny,
+                             int64_t nz, const double* w, int radius, double tol,
+                             int64_t max_iters, int64_t check_every, stn_solve_info* info,
+                             void* stream);
+
+/*
+ * jacobi_solve_varcoef_refined -- mixed-precision iterative refinement for
+ * A u = f (not in the paper; double kept only for the residual and update):
+ *   outer (double): rho = f - A u; stop if ||rho||/||f|| <= tol;
+ *                   s = max|rho|; r32 = float(rho / s)
+ *   inner (float) : `inner_sweeps` Jacobi sweeps on A e = r32 from e = 0
+ *                   (a and w rounded to float once per call)
+ *   update(double): u = u + s * double(e)
+ * up to max_outer outer steps.  info->outer = outer steps, info->iters =
+ * total float sweeps, info->rel_res = the last double relative residual.
+ * Synchronises.  Returns STN_OK or STN_NOT_CONVERGED.
+ */
+int jacobi_solve_varcoef_refined(const double* a, const double* f, double* u, int64_t nx,
+                                 int64_t ny, int64_t nz, const double* w, int radius, double tol,
+                                 int64_t inner_sweeps, int64_t max_outer, stn_solve_info* info,
+                                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_H_ */

@@ -1,0 +1,259 @@
+"""Thin Python binding of libstencil.so (C ABI in include/stencil.h).
+
+The functions below have the C ABI's names and only marshal arguments: every
+step of the Jacobi path runs in the library's CUDA kernels.  Grid arguments
+may be torch tensors (CUDA or CPU), numpy arrays, or raw integer addresses;
+a grid is the Fortran array u(1:nx+2r, 1:ny+2r, 1:nz+2r), i.e. a C-contiguous
+array of shape (nz+2r, ny+2r, nx+2r) (arXiv 2409.18824 Sec. 5.2, Listing 7).
+For tensor / array arguments the interior extents are taken from the shape
+when not given.
+
+There is no CPU fallback: importing this package raises if libstencil.so has
+not been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstencil.so")
+
+STN_OK = 0
+STN_NOT_CONVERGED = 1
+STN_EINVAL = -1
+STN_ENOMEM = -2
+STN_ECUDA = -3
+STN_ETIMEOUT = -4
+STN_EBUSY = -5
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libstencil error {code}: {msg}")
+        self.code = code
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("outer", ctypes.c_int64), ("rel_res", ctypes.c_double),
+                ("res_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_info_p = ctypes.POINTER(SolveInfo)
+
+#: every entry point of include/stencil.h with (restype, argtypes)
+SIGNATURES = {
+    "stencil_last_error": (ctypes.c_char_p, []),
+    "stencil_version": (ctypes.c_char_p, []),
+    "stencil_release_workspace": (_int, []),
+    "stencil_sweep_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
+    "stencil_sweep_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
+    "stencil_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
+    "stencil_apply_f32": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
+    "residual_norm_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
+    "residual_norm_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
+    "jacobi_solve_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _i64, _info_p, _vp]),
+    "varcoef_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
+    "varcoef_sweep_f64": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
+    "varcoef_sweep_f32": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
+    "varcoef_residual_norm_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
+    "jacobi_solve_varcoef_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _i64,
+                                        _info_p, _vp]),
+    "jacobi_solve_varcoef_refined": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _i64,
+                                            _info_p, _vp]),
+}
+for _name, (_res, _args) in SIGNATURES.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def last_error() -> str:
+    return _lib.stencil_last_error().decode()
+
+
+def version() -> str:
+    return _lib.stencil_version().decode()
+
+
+# ------------------------------------------------------------- marshalling --
+def _addr(x):
+    """Address of a grid argument (torch tensor, numpy array, int or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("grid arrays must be C-contiguous (Fortran column-major u(i,j,k))")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("grid tensors must be contiguous (Fortran column-major u(i,j,k))")
+        return x.data_ptr()
+    raise TypeError(f"unsupported grid argument {type(x)}")
+
+
+def _stream(stream, *grids):
+    """cudaStream_t for the call: explicit, else torch's current stream when a
+    grid is a CUDA tensor, else NULL (legacy default stream)."""
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    for g in grids:
+        if hasattr(g, "is_cuda") and g.is_cuda:
+            import torch
+            return torch.cuda.current_stream(g.device).cuda_stream
+    return None
+
+
+def _coeffs(c):
+    arr = (ctypes.c_double * len(c))(*[float(v) for v in c])
+    return ctypes.cast(arr, _dp), arr
+
+
+def _extents(grid, r, nx, ny, nz):
+    if nx is not None:
+        return nx, ny, nz
+    shape = tuple(grid.shape)
+    if len(shape) != 3:
+        raise ValueError("pass nx, ny, nz or a 3D grid")
+    return shape[2] - 2 * r, shape[1] - 2 * r, shape[0] - 2 * r
+
+
+def _check(rc):
+    if rc < 0:
+        raise StencilError(rc, last_error())
+    return rc
+
+
+# ------------------------------------------------------------ entry points --
+def stencil_sweep_f64(in_, out, coeffs, radius, iters, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(in_, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    return _check(_lib.stencil_sweep_f64(_addr(in_), _addr(out), nx, ny, nz, cp, radius, iters,
+                                         _stream(stream, in_, out)))
+
+
+def stencil_sweep_f32(in_, out, coeffs, radius, iters, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(in_, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    return _check(_lib.stencil_sweep_f32(_addr(in_), _addr(out), nx, ny, nz, cp, radius, iters,
+                                         _stream(stream, in_, out)))
+
+
+def stencil_apply_f64(u, out, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    return _check(_lib.stencil_apply_f64(_addr(u), _addr(b), _addr(out), nx, ny, nz, cp, radius,
+                                         _stream(stream, u, out, b)))
+
+
+def stencil_apply_f32(u, out, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    return _check(_lib.stencil_apply_f32(_addr(u), _addr(b), _addr(out), nx, ny, nz, cp, radius,
+                                         _stream(stream, u, out, b)))
+
+
+def residual_norm_f64(u, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None) -> float:
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    out = ctypes.c_double(0.0)
+    _check(_lib.residual_norm_f64(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
+                                  _stream(stream, u, b)))
+    return out.value
+
+
+def residual_norm_f32(u, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None) -> float:
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    out = ctypes.c_double(0.0)
+    _check(_lib.residual_norm_f32(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
+                                  _stream(stream, u, b)))
+    return out.value
+
+
+def jacobi_solve_f64(rhs, u, coeffs, radius, tol, max_iters, check_every=50, nx=None, ny=None, nz=None,
+                     stream=None):
+    """Returns (status, info dict)."""
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    info = SolveInfo()
+    rc = _check(_lib.jacobi_solve_f64(_addr(rhs), _addr(u), nx, ny, nz, cp, radius, tol, max_iters,
+                                      check_every, ctypes.byref(info), _stream(stream, u, rhs)))
+    return rc, info.as_dict()
+
+
+def varcoef_apply_f64(u, a, out, w, radius, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    wp, _keep = _coeffs(w)
+    return _check(_lib.varcoef_apply_f64(_addr(u), _addr(a), _addr(out), nx, ny, nz, wp, radius,
+                                         _stream(stream, u, a, out)))
+
+
+def varcoef_sweep_f64(in_, out, a, f, w, radius, iters, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(in_, radius, nx, ny, nz)
+    wp, _keep = _coeffs(w)
+    return _check(_lib.varcoef_sweep_f64(_addr(in_), _addr(out), _addr(a), _addr(f), nx, ny, nz, wp, radius,
+                                         iters, _stream(stream, in_, out, a, f)))
+
+
+def varcoef_sweep_f32(in_, out, a, f, w, radius, iters, nx=None, ny=None, nz=None, stream=None):
+    nx, ny, nz = _extents(in_, radius, nx, ny, nz)
+    wp, _keep = _coeffs(w)
+    return _check(_lib.varcoef_sweep_f32(_addr(in_), _addr(out), _addr(a), _addr(f), nx, ny, nz, wp, radius,
+                                         iters, _stream(stream, in_, out, a, f)))
+
+
+def varcoef_residual_norm_f64(u, a, f, w, radius, nx=None, ny=None, nz=None, stream=None) -> float:
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    wp, _keep = _coeffs(w)
+    out = ctypes.c_double(0.0)
+    _check(_lib.varcoef_residual_norm_f64(_addr(u), _addr(a), _addr(f), nx, ny, nz, wp, radius,
+                                          ctypes.byref(out), _stream(stream, u, a, f)))
+    return out.value
+
+
+def jacobi_solve_varcoef_f64(a, f, u, w, radius, tol, max_iters, check_every=50, nx=None, ny=None, nz=None,
+                             stream=None):
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    wp, _keep = _coeffs(w)
+    info = SolveInfo()
+    rc = _check(_lib.jacobi_solve_varcoef_f64(_addr(a), _addr(f), _addr(u), nx, ny, nz, wp, radius, tol,
+                                              max_iters, check_every, ctypes.byref(info),
+                                              _stream(stream, u, a, f)))
+    return rc, info.as_dict()
+
+
+def jacobi_solve_varcoef_refined(a, f, u, w, radius, tol, inner_sweeps, max_outer, nx=None, ny=None,
+                                 nz=None, stream=None):
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    wp, _keep = _coeffs(w)
+    info = SolveInfo()
+    rc = _check(_lib.jacobi_solve_varcoef_refined(_addr(a), _addr(f), _addr(u), nx, ny, nz, wp, radius, tol,
+                                                  inner_sweeps, max_outer, ctypes.byref(info),
+                                                  _stream(stream, u, a, f)))
+    return rc, info.as_dict()
+
+
+def release_workspace():
+    return _check(_lib.stencil_release_workspace())

@@ -1,0 +1,685 @@
+// C ABI of libstencil.so (declared in include/stencil.h): argument checks,
+// host-buffer staging, per-(device, stream) workspace and the drivers that
+// string the kernels of sweep.cu / varcoef.cu / reduce.cu / refine.cu into
+// the calls of the Jacobi path (arXiv 2409.18824 Sec. 4, Sec. 5.3).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "internal.h"
+
+namespace stn {
+
+// ------------------------------------------------------------------ errors --
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  set_error(buf);
+  return STN_ECUDA;
+}
+static int einval(const char* msg) {
+  set_error(std::string("invalid argument: ") + msg);
+  return STN_EINVAL;
+}
+
+// --------------------------------------------------------------- workspace --
+namespace {
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
+constexpr int kScalars = 64;
+}  // namespace
+
+static int grow(void** p, size_t* cap, size_t want) {
+  if (*cap >= want) return STN_OK;
+  if (*p) {
+    STN_CUDA_TRY(cudaDeviceSynchronize());
+    STN_CUDA_TRY(cudaFree(*p));
+    *p = nullptr;
+    *cap = 0;
+  }
+  cudaError_t e = cudaMalloc(p, want);
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    set_error("device allocation of workspace failed");
+    return STN_ENOMEM;
+  }
+  STN_CUDA_TRY(e);
+  *cap = want;
+  return STN_OK;
+}
+
+int get_workspace(cudaStream_t stream, i64 partials, size_t grid_bytes, Workspace** out) {
+  int dev = 0;
+  STN_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace*& ws = g_ws[{dev, stream}];
+  if (!ws) ws = new Workspace();
+  if (!ws->scalars) {
+    STN_CUDA_TRY(cudaMalloc(&ws->scalars, kScalars * sizeof(double)));
+    STN_CUDA_TRY(cudaMemset(ws->scalars, 0, kScalars * sizeof(double)));
+    STN_CUDA_TRY(cudaMallocHost(&ws->host_scalars, kScalars * sizeof(double)));
+  }
+  if (partials < 1024) partials = 1024;
+  size_t cap = (size_t)ws->partials_cap * sizeof(double);
+  int rc = grow((void**)&ws->partials, &cap, (size_t)partials * sizeof(double) * 2);
+  if (rc) return rc;
+  ws->partials_cap = (i64)(cap / sizeof(double));
+  if (grid_bytes) {
+    rc = grow(&ws->grid, &ws->grid_bytes, grid_bytes);
+    if (rc) return rc;
+  }
+  *out = ws;
+  return STN_OK;
+}
+int ensure_grid2(Workspace* ws, size_t bytes) { return grow(&ws->grid2, &ws->grid2_bytes, bytes); }
+int ensure_grid3(Workspace* ws, size_t bytes) { return grow(&ws->grid3, &ws->grid3_bytes, bytes); }
+
+static int release_all() {
+  int dev = 0;
+  STN_CUDA_TRY(cudaGetDevice(&dev));
+  STN_CUDA_TRY(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (it->first.first != dev) {
+      ++it;
+      continue;
+    }
+    Workspace* ws = it->second;
+    cudaFree(ws->partials);
+    cudaFree(ws->scalars);
+    cudaFree(ws->grid);
+    cudaFree(ws->grid2);
+    cudaFree(ws->grid3);
+    cudaFreeHost(ws->host_scalars);
+    delete ws;
+    it = g_ws.erase(it);
+  }
+  return STN_OK;
+}
+
+// ------------------------------------------------------------- validation --
+static int check_grid(i64 nx, i64 ny, i64 nz, int r) {
+  if (r != 1 && r != 2) return einval("radius must be 1 or 2");
+  if (nx < 1 || ny < 1 || nz < 1) return einval("interior extents must be >= 1");
+  const i64 lim = (i64)1 << 28;
+  if (nx > lim || ny > lim || nz > lim) return einval("extent too large");
+  const double cells = (double)(nx + 2 * r) * (double)(ny + 2 * r) * (double)(nz + 2 * r);
+  if (cells > 9.0e15) return einval("grid too large");
+  return STN_OK;
+}
+
+static bool overlap(const void* a, const void* b, size_t bytes) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+// ---------------------------------------------------------------- staging --
+// A grid argument: the caller's pointer and, when it is host memory, a device
+// copy for the duration of the call.
+struct Arg {
+  void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+  bool copy_in = false, copy_out = false;
+};
+
+static int classify(const void* p, bool* host) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+  *host = !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  return STN_OK;
+}
+
+class Stager {
+ public:
+  explicit Stager(cudaStream_t s) : s_(s) {}
+  ~Stager() {
+    for (int i = 0; i < n_; i++)
+      if (a_[i].host && a_[i].dev) cudaFreeAsync(a_[i].dev, s_);
+  }
+  // Registers a grid argument; returns its device pointer in *dev.
+  int add(const void* p, size_t bytes, bool in, bool out, void** dev) {
+    if (!p) {
+      *dev = nullptr;
+      return STN_OK;
+    }
+    Arg& a = a_[n_++];
+    a.user = const_cast<void*>(p);
+    a.bytes = bytes;
+    a.copy_in = in;
+    a.copy_out = out;
+    int rc = classify(p, &a.host);
+    if (rc) return rc;
+    if (!a.host) {
+      a.dev = a.user;
+    } else {
+      any_host_ = true;
+      cudaError_t e = cudaMallocAsync(&a.dev, bytes, s_);
+      if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        a.dev = nullptr;
+        set_error("device allocation for a host grid failed");
+        return STN_ENOMEM;
+      }
+      STN_CUDA_TRY(e);
+      if (in) STN_CUDA_TRY(cudaMemcpyAsync(a.dev, a.user, bytes, cudaMemcpyHostToDevice, s_));
+    }
+    *dev = a.dev;
+    return STN_OK;
+  }
+  // Copies host outputs back and, if any argument was host memory, waits.
+  int finish() {
+    for (int i = 0; i < n_; i++)
+      if (a_[i].host && a_[i].copy_out)
+        STN_CUDA_TRY(cudaMemcpyAsync(a_[i].user, a_[i].dev, a_[i].bytes, cudaMemcpyDeviceToHost, s_));
+    if (any_host_) STN_CUDA_TRY(cudaStreamSynchronize(s_));
+    return STN_OK;
+  }
+  bool any_host() const { return any_host_; }
+
+ private:
+  cudaStream_t s_;
+  Arg a_[8];
+  int n_ = 0;
+  bool any_host_ = false;
+};
+
+// --------------------------------------------------------------- drivers --
+template <typename T>
+static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeffs, int radius,
+                      i64 iters, void* stream) {
+  clear_error();
+  if (!in || !out) return einval("NULL grid");
+  if (!coeffs) return einval("NULL coeffs");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (iters < 0) return einval("iters < 0");
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  if (overlap(in, out, bytes)) return einval("in and out overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  T *din, *dout;
+  if (int rc = st.add(in, bytes, true, iters > 1, (void**)&din)) return rc;
+  if (int rc = st.add(out, bytes, false, true, (void**)&dout)) return rc;
+  if (iters == 0) {
+    STN_CUDA_TRY(cudaMemcpyAsync(dout, din, bytes, cudaMemcpyDeviceToDevice, s));
+    return st.finish();
+  }
+  if (int rc = launch_copy_halo<T>(din, dout, g, s)) return rc;
+  T* cur = din;
+  T* nxt = dout;
+  for (i64 it = 0; it < iters; it++) {
+    if (int rc = launch_star<T>(cur, nullptr, nxt, g, coeffs, kSweep, nullptr, s)) return rc;
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (cur != dout) STN_CUDA_TRY(cudaMemcpyAsync(dout, cur, bytes, cudaMemcpyDeviceToDevice, s));
+  return st.finish();
+}
+
+template <typename T>
+static int apply_impl(const T* u, const T* b, T* out, i64 nx, i64 ny, i64 nz, const double* coeffs,
+                      int radius, void* stream) {
+  clear_error();
+  if (!u || !out) return einval("NULL grid");
+  if (!coeffs) return einval("NULL coeffs");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  if (overlap(u, out, bytes) || (b && overlap(b, out, bytes))) return einval("out overlaps an input");
+  bool hu = false, ho = false, hb = false;
+  if (int rc = classify(u, &hu)) return rc;
+  if (int rc = classify(out, &ho)) return rc;
+  if (b)
+    if (int rc = classify(b, &hb)) return rc;
+  if (hu || ho || hb) return einval("stencil_apply takes device grids only");
+  return launch_star<T>(u, b, out, g, coeffs, kSweep, nullptr, (cudaStream_t)stream);
+}
+
+// Reads `n` device scalars of the workspace into its pinned mirror; waits.
+static int read_scalars(Workspace* ws, int first, int n, cudaStream_t s) {
+  STN_CUDA_TRY(cudaMemcpyAsync(ws->host_scalars + first, ws->scalars + first, n * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  return STN_OK;
+}
+
+template <typename T>
+static int residual_impl(const T* u, const T* b, i64 nx, i64 ny, i64 nz, const double* coeffs,
+                         int radius, double* norm_out, void* stream) {
+  clear_error();
+  if (!u) return einval("NULL grid");
+  if (!coeffs || !norm_out) return einval("NULL coeffs or norm_out");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  T *du, *db;
+  if (int rc = st.add(u, bytes, true, false, (void**)&du)) return rc;
+  if (int rc = st.add(b, bytes, true, false, (void**)&db)) return rc;
+  const ZPlan p = plan_star(g);
+  Workspace* ws;
+  if (int rc = get_workspace(s, p.blocks(), 0, &ws)) return rc;
+  if (int rc = launch_star<T>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s)) return rc;
+  if (int rc = launch_finalize(ws->partials, p.blocks(), ws->scalars, nullptr, 0.0, s)) return rc;
+  if (int rc = read_scalars(ws, 0, 2, s)) return rc;
+  *norm_out = ws->host_scalars[1];
+  return st.finish();
+}
+
+// Scalars layout used by the solvers: [0] sum, [1] norm, [2] rel, [3] flag,
+// [4] max|rho|, [8] rhs sum of squares, [9] rhs norm.
+template <typename Step>
+static int solve_loop(Workspace* ws, i64 max_iters, i64 check_every, i64 nparts, double tol,
+                      cudaStream_t s, Step&& step, i64* iters_out, double* rel_out, double* res_out,
+                      int* status) {
+  i64 it = 0;
+  double rel = INFINITY, res = INFINITY;
+  *status = STN_NOT_CONVERGED;
+  while (it < max_iters) {
+    i64 group = check_every < max_iters - it ? check_every : max_iters - it;
+    for (i64 gi = 0; gi < group; gi++)
+      if (int rc = step(it + gi, gi == group - 1)) return rc;
+    it += group;
+    if (int rc = launch_finalize(ws->partials, nparts, ws->scalars, ws->scalars + 9, tol, s)) return rc;
+    if (int rc = read_scalars(ws, 0, 4, s)) return rc;
+    res = ws->host_scalars[1];
+    rel = ws->host_scalars[2];
+    if (ws->host_scalars[3] != 0.0) {
+      *status = STN_OK;
+      break;
+    }
+  }
+  *iters_out = it;
+  *rel_out = rel;
+  *res_out = res;
+  return STN_OK;
+}
+
+template <typename T>
+static int rhs_norm(Workspace* ws, const T* f, const Grid& g, cudaStream_t s, double* out) {
+  i64 np = 0;
+  if (f) {
+    if (int rc = launch_interior_sumsq<T>(f, g, ws->partials, &np, s)) return rc;
+    if (int rc = launch_finalize(ws->partials, np, ws->scalars + 8, nullptr, 0.0, s)) return rc;
+  } else {
+    STN_CUDA_TRY(cudaMemsetAsync(ws->scalars + 8, 0, 2 * sizeof(double), s));
+  }
+  if (int rc = read_scalars(ws, 8, 2, s)) return rc;
+  *out = ws->host_scalars[9];
+  return STN_OK;
+}
+
+static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, const double* coeffs,
+                       int radius, double tol, i64 max_iters, i64 check_every, stn_solve_info* info,
+                       void* stream) {
+  clear_error();
+  if (!u) return einval("NULL grid");
+  if (!coeffs) return einval("NULL coeffs");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (!(tol >= 0.0)) return einval("tol must be >= 0");
+  if (max_iters < 0) return einval("max_iters < 0");
+  if (check_every < 1) return einval("check_every < 1");
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  if (rhs && overlap(rhs, u, bytes)) return einval("rhs and u overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *db;
+  if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
+  if (int rc = st.add(rhs, bytes, true, false, (void**)&db)) return rc;
+  const ZPlan p = plan_star(g);
+  Workspace* ws;
+  if (int rc = get_workspace(s, p.blocks(), bytes, &ws)) return rc;
+  double* tmp = (double*)ws->grid;
+  if (int rc = launch_copy_halo<double>(du, tmp, g, s)) return rc;
+  double bn = 0.0;
+  if (int rc = rhs_norm<double>(ws, db, g, s, &bn)) return rc;
+  double* cur = du;
+  double* nxt = tmp;
+  auto step = [&](i64, bool last) -> int {
+    int rc = launch_star<double>(cur, db, nxt, g, coeffs, last ? kSweepResidual : kSweep, ws->partials, s);
+    std::swap(cur, nxt);
+    return rc;
+  };
+  i64 iters = 0;
+  double rel = 0, res = 0;
+  int status = STN_NOT_CONVERGED;
+  if (int rc = solve_loop(ws, max_iters, check_every, p.blocks(), tol, s, step, &iters, &rel, &res, &status))
+    return rc;
+  if (max_iters == 0) {
+    // no sweep: measure the residual of the initial guess only
+    if (int rc = launch_star<double>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s)) return rc;
+    if (int rc = launch_finalize(ws->partials, p.blocks(), ws->scalars, ws->scalars + 9, tol, s)) return rc;
+    if (int rc = read_scalars(ws, 0, 4, s)) return rc;
+    res = ws->host_scalars[1];
+    rel = ws->host_scalars[2];
+    status = ws->host_scalars[3] != 0.0 ? STN_OK : STN_NOT_CONVERGED;
+  }
+  if (cur != du) STN_CUDA_TRY(cudaMemcpyAsync(du, cur, bytes, cudaMemcpyDeviceToDevice, s));
+  if (int rc = st.finish()) return rc;
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->outer = 0;
+    info->rel_res = rel;
+    info->res_norm = res;
+    info->rhs_norm = bn;
+    info->status = status;
+  }
+  return status;
+}
+
+// ----------------------------------------------------- variable coefficient --
+template <typename T>
+static int var_sweep_impl(T* in, T* out, const T* a, const T* f, i64 nx, i64 ny, i64 nz,
+                          const double* w, int radius, i64 iters, void* stream) {
+  clear_error();
+  if (!in || !out || !a || !f) return einval("NULL grid");
+  if (!w) return einval("NULL weights");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (iters < 0) return einval("iters < 0");
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  if (overlap(in, out, bytes)) return einval("in and out overlap");
+  if (overlap(a, out, bytes) || overlap(f, out, bytes) || overlap(a, in, bytes) || overlap(f, in, bytes))
+    return einval("coefficient or source grid overlaps an iterate");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  T *din, *dout, *da, *df;
+  if (int rc = st.add(in, bytes, true, iters > 1, (void**)&din)) return rc;
+  if (int rc = st.add(out, bytes, false, true, (void**)&dout)) return rc;
+  if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
+  if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
+  if (iters == 0) {
+    STN_CUDA_TRY(cudaMemcpyAsync(dout, din, bytes, cudaMemcpyDeviceToDevice, s));
+    return st.finish();
+  }
+  if (int rc = launch_copy_halo<T>(din, dout, g, s)) return rc;
+  T* cur = din;
+  T* nxt = dout;
+  for (i64 it = 0; it < iters; it++) {
+    if (int rc = launch_var<T>(cur, da, df, nxt, g, w, kVarSweep, nullptr, nullptr, s)) return rc;
+    std::swap(cur, nxt);
+  }
+  if (cur != dout) STN_CUDA_TRY(cudaMemcpyAsync(dout, cur, bytes, cudaMemcpyDeviceToDevice, s));
+  return st.finish();
+}
+
+static int var_apply_impl(const double* u, const double* a, double* out, i64 nx, i64 ny, i64 nz,
+                          const double* w, int radius, void* stream) {
+  clear_error();
+  if (!u || !a || !out) return einval("NULL grid");
+  if (!w) return einval("NULL weights");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  if (overlap(u, out, bytes) || overlap(a, out, bytes)) return einval("out overlaps an input");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *da, *dout;
+  if (int rc = st.add(u, bytes, true, false, (void**)&du)) return rc;
+  if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
+  if (int rc = st.add(out, bytes, true, true, (void**)&dout)) return rc;
+  if (int rc = launch_var<double>(du, da, nullptr, dout, g, w, kVarApply, nullptr, nullptr, s)) return rc;
+  return st.finish();
+}
+
+static int var_residual_impl(const double* u, const double* a, const double* f, i64 nx, i64 ny,
+                             i64 nz, const double* w, int radius, double* norm_out, void* stream) {
+  clear_error();
+  if (!u || !a || !f) return einval("NULL grid");
+  if (!w || !norm_out) return einval("NULL weights or norm_out");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *da, *df;
+  if (int rc = st.add(u, bytes, true, false, (void**)&du)) return rc;
+  if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
+  if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
+  const ZPlan p = plan_var(g);
+  Workspace* ws;
+  if (int rc = get_workspace(s, p.blocks(), 0, &ws)) return rc;
+  if (int rc = launch_var<double>(du, da, df, nullptr, g, w, kVarResidual, ws->partials, nullptr, s)) return rc;
+  if (int rc = launch_finalize(ws->partials, p.blocks(), ws->scalars, nullptr, 0.0, s)) return rc;
+  if (int rc = read_scalars(ws, 0, 2, s)) return rc;
+  *norm_out = ws->host_scalars[1];
+  return st.finish();
+}
+
+static int var_jacobi_impl(const double* a, const double* f, double* u, i64 nx, i64 ny, i64 nz,
+                           const double* w, int radius, double tol, i64 max_iters, i64 check_every,
+                           stn_solve_info* info, void* stream) {
+  clear_error();
+  if (!u || !a || !f) return einval("NULL grid");
+  if (!w) return einval("NULL weights");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (!(tol >= 0.0)) return einval("tol must be >= 0");
+  if (max_iters < 0) return einval("max_iters < 0");
+  if (check_every < 1) return einval("check_every < 1");
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  if (overlap(a, u, bytes) || overlap(f, u, bytes)) return einval("u overlaps a or f");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *da, *df;
+  if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
+  if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
+  if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
+  const ZPlan p = plan_var(g);
+  Workspace* ws;
+  if (int rc = get_workspace(s, p.blocks(), bytes, &ws)) return rc;
+  double* tmp = (double*)ws->grid;
+  if (int rc = launch_copy_halo<double>(du, tmp, g, s)) return rc;
+  double fn = 0.0;
+  if (int rc = rhs_norm<double>(ws, df, g, s, &fn)) return rc;
+  double* cur = du;
+  double* nxt = tmp;
+  auto step = [&](i64, bool last) -> int {
+    if (last) {
+      int rc = launch_var<double>(cur, da, df, nullptr, g, w, kVarResidual, ws->partials, nullptr, s);
+      if (rc) return rc;
+    }
+    int rc = launch_var<double>(cur, da, df, nxt, g, w, kVarSweep, nullptr, nullptr, s);
+    std::swap(cur, nxt);
+    return rc;
+  };
+  i64 iters = 0;
+  double rel = 0, res = 0;
+  int status = STN_NOT_CONVERGED;
+  if (int rc = solve_loop(ws, max_iters, check_every, p.blocks(), tol, s, step, &iters, &rel, &res, &status))
+    return rc;
+  if (cur != du) STN_CUDA_TRY(cudaMemcpyAsync(du, cur, bytes, cudaMemcpyDeviceToDevice, s));
+  if (int rc = st.finish()) return rc;
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->outer = 0;
+    info->rel_res = rel;
+    info->res_norm = res;
+    info->rhs_norm = fn;
+    info->status = status;
+  }
+  return status;
+}
+
+static int refined_impl(const double* a, const double* f, double* u, i64 nx, i64 ny, i64 nz,
+                        const double* w, int radius, double tol, i64 inner_sweeps, i64 max_outer,
+                        stn_solve_info* info, void* stream) {
+  clear_error();
+  if (!u || !a || !f) return einval("NULL grid");
+  if (!w) return einval("NULL weights");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (!(tol >= 0.0)) return einval("tol must be >= 0");
+  if (inner_sweeps < 0 || max_outer < 0) return einval("inner_sweeps or max_outer < 0");
+  const Grid g{nx, ny, nz, radius};
+  const i64 n = g.count();
+  const size_t bytes = (size_t)n * sizeof(double);
+  if (overlap(a, u, bytes) || overlap(f, u, bytes)) return einval("u overlaps a or f");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *da, *df;
+  if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
+  if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
+  if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
+  const ZPlan p = plan_var(g);
+  Workspace* ws;
+  // partials: sums in [0, nb), maxima in [nb, 2nb)
+  if (int rc = get_workspace(s, 2 * p.blocks(), bytes, &ws)) return rc;
+  const size_t b32 = (size_t)n * sizeof(float);
+  if (int rc = ensure_grid2(ws, 4 * b32)) return rc;
+  double* rho = (double*)ws->grid;
+  float* a32 = (float*)ws->grid2;
+  float* r32 = a32 + n;
+  float* e = r32 + n;
+  float* e2 = e + n;
+  if (int rc = launch_convert<double, float>(da, a32, n, s)) return rc;
+  STN_CUDA_TRY(cudaMemsetAsync(r32, 0, 3 * b32, s));
+  double fn = 0.0;
+  if (int rc = rhs_norm<double>(ws, df, g, s, &fn)) return rc;
+  double* pmax = ws->partials + p.blocks();
+  i64 outer = 0, sweeps = 0;
+  double rel = INFINITY, res = INFINITY;
+  int status = STN_NOT_CONVERGED;
+  for (;;) {
+    if (int rc = launch_var<double>(du, da, df, rho, g, w, kVarRefine, ws->partials, pmax, s)) return rc;
+    if (int rc = launch_finalize(ws->partials, p.blocks(), ws->scalars, ws->scalars + 9, tol, s)) return rc;
+    if (int rc = launch_max_finalize(pmax, p.blocks(), ws->scalars + 4, s)) return rc;
+    if (int rc = read_scalars(ws, 0, 5, s)) return rc;
+    res = ws->host_scalars[1];
+    rel = ws->host_scalars[2];
+    if (ws->host_scalars[3] != 0.0) {
+      status = STN_OK;
+      break;
+    }
+    if (outer >= max_outer || ws->host_scalars[4] == 0.0) break;
+    if (int rc = launch_refine_scale(rho, r32, g, ws->scalars + 4, s)) return rc;
+    STN_CUDA_TRY(cudaMemsetAsync(e, 0, 2 * b32, s));
+    float* cur = e;
+    float* nxt = e2;
+    for (i64 it = 0; it < inner_sweeps; it++) {
+      if (int rc = launch_var<float>(cur, a32, r32, nxt, g, w, kVarSweep, nullptr, nullptr, s)) return rc;
+      std::swap(cur, nxt);
+    }
+    sweeps += inner_sweeps;
+    if (int rc = launch_refine_update(du, cur, g, ws->scalars + 4, s)) return rc;
+    outer++;
+  }
+  if (int rc = st.finish()) return rc;
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = sweeps;
+    info->outer = outer;
+    info->rel_res = rel;
+    info->res_norm = res;
+    info->rhs_norm = fn;
+    info->status = status;
+  }
+  return status;
+}
+
+}  // namespace stn
+
+// ===================================================================== ABI ==
+using namespace stn;
+
+extern "C" {
+
+const char* stencil_last_error(void) { return g_err.c_str(); }
+
+const char* stencil_version(void) { return "libstencil 0.1 (sm_103a)"; }
+
+int stencil_release_workspace(void) {
+  clear_error();
+  return release_all();
+}
+
+int stencil_sweep_f64(double* in, double* out, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, int64_t iters, void* stream) {
+  return sweep_impl<double>(in, out, nx, ny, nz, coeffs, radius, iters, stream);
+}
+
+int stencil_sweep_f32(float* in, float* out, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, int64_t iters, void* stream) {
+  return sweep_impl<float>(in, out, nx, ny, nz, coeffs, radius, iters, stream);
+}
+
+int stencil_apply_f64(const double* u, const double* b, double* out, int64_t nx, int64_t ny,
+                      int64_t nz, const double* coeffs, int radius, void* stream) {
+  return apply_impl<double>(u, b, out, nx, ny, nz, coeffs, radius, stream);
+}
+
+int stencil_apply_f32(const float* u, const float* b, float* out, int64_t nx, int64_t ny,
+                      int64_t nz, const double* coeffs, int radius, void* stream) {
+  return apply_impl<float>(u, b, out, nx, ny, nz, coeffs, radius, stream);
+}
+
+int residual_norm_f64(const double* u, const double* b, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, double* norm_out, void* stream) {
+  return residual_impl<double>(u, b, nx, ny, nz, coeffs, radius, norm_out, stream);
+}
+
+int residual_norm_f32(const float* u, const float* b, int64_t nx, int64_t ny, int64_t nz,
+                      const double* coeffs, int radius, double* norm_out, void* stream) {
+  return residual_impl<float>(u, b, nx, ny, nz, coeffs, radius, norm_out, stream);
+}
+
+int jacobi_solve_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64_t nz,
+                     const double* coeffs, int radius, double tol, int64_t max_iters,
+                     int64_t check_every, stn_solve_info* info, void* stream) {
+  return jacobi_impl(rhs, u, nx, ny, nz, coeffs, radius, tol, max_iters, check_every, info, stream);
+}
+
+int varcoef_apply_f64(const double* u, const double* a, double* out, int64_t nx, int64_t ny,
+                      int64_t nz, const double* w, int radius, void* stream) {
+  return var_apply_impl(u, a, out, nx, ny, nz, w, radius, stream);
+}
+
+int varcoef_sweep_f64(double* in, double* out, const double* a, const double* f, int64_t nx,
+                      int64_t ny, int64_t nz, const double* w, int radius, int64_t iters,
+                      void* stream) {
+  return var_sweep_impl<double>(in, out, a, f, nx, ny, nz, w, radius, iters, stream);
+}
+
+int varcoef_sweep_f32(float* in, float* out, const float* a, const float* f, int64_t nx,
+                      int64_t ny, int64_t nz, const double* w, int radius, int64_t iters,
+                      void* stream) {
+  return var_sweep_impl<float>(in, out, a, f, nx, ny, nz, w, radius, iters, stream);
+}
+
+int varcoef_residual_norm_f64(const double* u, const double* a, const double* f, int64_t nx,
+                              int64_t ny, int64_t nz, const double* w, int radius,
+                              double* norm_out, void* stream) {
+  return var_residual_impl(u, a, f, nx, ny, nz, w, radius, norm_out, stream);
+}
+
+int jacobi_solve_varcoef_f64(const double* a, const double* f, double* u, int64_t nx, int64_t ny,
+                             int64_t nz, const double* w, int radius, double tol,
+                             int64_t max_iters, int64_t check_every, stn_solve_info* info,
+                             void* stream) {
+  return var_jacobi_impl(a, f, u, nx, ny, nz, w, radius, tol, max_iters, check_every, info, stream);
+}
+
+int jacobi_solve_varcoef_refined(const double* a, const double* f, double* u, int64_t nx,
+                                 int64_t ny, int64_t nz, const double* w, int radius, double tol,
+                                 int64_t inner_sweeps, int64_t max_outer, stn_solve_info* info,
+                                 void* stream) {
+  return refined_impl(a, f, u, nx, ny, nz, w, radius, tol, inner_sweeps, max_outer, info, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Internal declarations shared by the translation units of libstencil.so.
+// Nothing here is part of the public ABI (include/stencil.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/stencil.h"
+
+namespace stn {
+
+using i64 = int64_t;
+
+// Thread-local error message behind stencil_last_error().
+void set_error(const std::string& msg);
+void clear_error();
+
+// Returns STN_ECUDA with a message when `e` is an error.
+int cuda_fail(cudaError_t e, const char* what);
+
+#define STN_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::stn::cuda_fail(_e, #expr); \
+  } while (0)
+
+// Geometry of one padded grid.
+struct Grid {
+  i64 nx, ny, nz;  // interior extents
+  int r;           // halo width
+  i64 NX() const { return nx + 2 * r; }
+  i64 NY() const { return ny + 2 * r; }
+  i64 NZ() const { return nz + 2 * r; }
+  i64 count() const { return NX() * NY() * NZ(); }
+  i64 interior() const { return nx * ny * nz; }
+};
+
+// Launch configuration of the z-streaming kernels: tiles of TX x TY columns,
+// each block streams a chunk of `kchunk` planes.
+struct ZPlan {
+  int tiles_x, tiles_y, chunks;
+  int kchunk;
+  i64 blocks() const { return (i64)tiles_x * tiles_y * chunks; }
+};
+
+// Per-(device, stream) workspace.
+struct Workspace {
+  double* partials = nullptr;  // per-block partial sums
+  i64 partials_cap = 0;
+  double* scalars = nullptr;   // small device scalars (norms, flags); 64 doubles
+  void* grid = nullptr;        // ping-pong grid for solvers
+  size_t grid_bytes = 0;
+  void* grid2 = nullptr;       // second solver buffer (refinement)
+  size_t grid2_bytes = 0;
+  void* grid3 = nullptr;
+  size_t grid3_bytes = 0;
+  double* host_scalars = nullptr;  // pinned host mirror of scalars
+};
+
+// Returns the workspace of the current device and `stream`, with at least
+// `partials` partial slots and (if grid_bytes > 0) a grid buffer of that size.
+int get_workspace(cudaStream_t stream, i64 partials, size_t grid_bytes, Workspace** ws);
+int ensure_grid2(Workspace* ws, size_t bytes);
+int ensure_grid3(Workspace* ws, size_t bytes);
+
+// ---- constant-coefficient star stencil (sweep.cu) --------------------------
+enum SweepMode { kSweep = 0, kSweepResidual = 1, kResidualOnly = 2 };
+
+ZPlan plan_star(const Grid& g);
+// One launch: out = S u + b over the interior; in residual modes also the
+// per-block partial sums of rho^2 into `partials` (ZPlan::blocks() entries).
+template <typename T>
+int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
+                SweepMode mode, double* partials, cudaStream_t s);
+// Copies the halo cells of `src` into `dst` (same geometry).
+template <typename T>
+int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s);
+
+// ---- reductions (reduce.cu) -------------------------------------------------
+// Sums partials[0..n) in a fixed order into dst[0] = sum, dst[1] = sqrt(sum),
+// and, if scale_src is not NULL, dst[2] = sqrt(sum) / scale with
+// scale = *scale_src (1 when that is 0), and dst[3] = (dst[2] <= tol).
+int launch_finalize(const double* partials, i64 n, double* dst, const double* scale_src,
+                    double tol, cudaStream_t s);
+// Interior sum of squares of a grid (per-block partials) then finalize.
+template <typename T>
+int launch_interior_sumsq(const T* x, const Grid& g, double* partials, i64* nparts,
+                          cudaStream_t s);
+
+// ---- variable coefficient (varcoef.cu) --------------------------------------
+enum VarMode { kVarSweep = 0, kVarApply = 1, kVarResidual = 2, kVarRefine = 3 };
+ZPlan plan_var(const Grid& g);
+// kVarRefine writes rho = f - A u (double) into out's interior and per-block
+// partial sums of rho^2 / maxima of |rho| into partials / partials_max.
+template <typename T>
+int launch_var(const T* u, const T* a, const T* f, T* out, const Grid& g, const double* w,
+               VarMode mode, double* partials, double* partials_max, cudaStream_t s);
+
+// ---- refinement helpers (refine.cu) ----------------------------------------
+// r32 = float(rho / s), s = dst_scalar[0] (device); e = 0 on the interior.
+int launch_refine_scale(const double* rho, float* r32, const Grid& g, const double* smax,
+                        cudaStream_t s);
+// u += s * double(e) on the interior.
+int launch_refine_update(double* u, const float* e, const Grid& g, const double* smax,
+                         cudaStream_t s);
+int launch_max_finalize(const double* partials, i64 n, double* dst, cudaStream_t s);
+template <typename T, typename U>
+int launch_convert(const T* src, U* dst, i64 n, cudaStream_t s);
+
+}  // namespace stn

@@ -1,0 +1,108 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+that include/stencil.h declares, and rejects bad arguments with STN_EINVAL
+before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stencil.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|const char\s*\*)\s*\**\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for required in ("stencil_sweep_f64", "residual_norm_f64", "jacobi_solve_f64"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = lib.lib()
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+    # and the binding wraps each of them
+    assert set(declared_functions()) <= set(lib.SIGNATURES)
+
+
+def test_version_and_empty_error(lib):
+    assert "sm_103a" in lib.version()
+    assert lib.last_error() == ""
+
+
+FAKE_A = 0x7F0000000000
+FAKE_B = 0x7F0100000000
+
+
+def call(lib, name, *args):
+    return getattr(lib.lib(), name)(*args)
+
+
+def c3(*v):
+    arr = (ctypes.c_double * len(v))(*v)
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), arr
+
+
+@pytest.mark.parametrize("nx,ny,nz,r,iters,why", [
+    (0, 4, 4, 1, 1, "extents"), (4, -1, 4, 1, 1, "extents"), (4, 4, 4, 3, 1, "radius"),
+    (4, 4, 4, 0, 1, "radius"), (4, 4, 4, 1, -1, "iters"), (1 << 29, 4, 4, 1, 1, "too large")])
+def test_sweep_rejects_bad_arguments(lib, nx, ny, nz, r, iters, why):
+    cp, _k = c3(0.0, 1 / 6, 0.0)
+    for name in ("stencil_sweep_f64", "stencil_sweep_f32"):
+        rc = call(lib, name, FAKE_A, FAKE_B, nx, ny, nz, cp, r, iters, None)
+        assert rc == lib.STN_EINVAL, (name, why)
+        assert "invalid argument" in lib.last_error()
+
+
+def test_sweep_rejects_null_and_aliasing(lib):
+    cp, _k = c3(0.0, 1 / 6)
+    f = lib.lib().stencil_sweep_f64
+    assert f(None, FAKE_B, 4, 4, 4, cp, 1, 1, None) == lib.STN_EINVAL
+    assert f(FAKE_A, None, 4, 4, 4, cp, 1, 1, None) == lib.STN_EINVAL
+    assert f(FAKE_A, FAKE_B, 4, 4, 4, None, 1, 1, None) == lib.STN_EINVAL
+    assert f(FAKE_A, FAKE_A, 4, 4, 4, cp, 1, 1, None) == lib.STN_EINVAL
+    # out starts inside in's 6*6*6 doubles
+    assert f(FAKE_A, FAKE_A + 8 * 100, 4, 4, 4, cp, 1, 1, None) == lib.STN_EINVAL
+    assert "overlap" in lib.last_error()
+
+
+def test_residual_and_solvers_reject_bad_arguments(lib):
+    cp, _k = c3(0.0, 1 / 6)
+    out = ctypes.c_double()
+    L = lib.lib()
+    assert L.residual_norm_f64(None, None, 4, 4, 4, cp, 1, ctypes.byref(out), None) == lib.STN_EINVAL
+    assert L.residual_norm_f64(FAKE_A, None, 4, 4, 4, cp, 1, None, None) == lib.STN_EINVAL
+    assert L.residual_norm_f32(FAKE_A, None, 4, 4, 4, cp, 5, ctypes.byref(out), None) == lib.STN_EINVAL
+    info = lib.SolveInfo()
+    J = L.jacobi_solve_f64
+    assert J(None, FAKE_A, 4, 4, 4, cp, 1, -1.0, 10, 1, ctypes.byref(info), None) == lib.STN_EINVAL
+    assert J(None, FAKE_A, 4, 4, 4, cp, 1, 1e-6, -1, 1, ctypes.byref(info), None) == lib.STN_EINVAL
+    assert J(None, FAKE_A, 4, 4, 4, cp, 1, 1e-6, 10, 0, ctypes.byref(info), None) == lib.STN_EINVAL
+    assert J(None, FAKE_A, 4, 4, 4, cp, 1, float("nan"), 10, 1, ctypes.byref(info), None) == lib.STN_EINVAL
+    assert J(FAKE_A, FAKE_A, 4, 4, 4, cp, 1, 1e-6, 10, 1, ctypes.byref(info), None) == lib.STN_EINVAL
+    wp, _w = c3(0.0, 1.0, 0.25)
+    assert L.varcoef_sweep_f64(FAKE_A, FAKE_B, None, FAKE_B + 4096, 4, 4, 4, wp, 2, 1, None) == lib.STN_EINVAL
+    assert L.varcoef_sweep_f32(FAKE_A, FAKE_B, FAKE_B + (1 << 20), FAKE_A, 4, 4, 4, wp, 2, 1, None) == lib.STN_EINVAL
+    assert L.varcoef_apply_f64(FAKE_A, FAKE_B, FAKE_A, 4, 4, 4, wp, 2, None) == lib.STN_EINVAL
+    assert L.jacobi_solve_varcoef_refined(FAKE_A, FAKE_B, FAKE_B + (1 << 30), 4, 4, 4, wp, 2, 1e-10, -1, 3,
+                                          ctypes.byref(info), None) == lib.STN_EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    """The package refuses to import when libstencil.so is absent (no fallback)."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2409_18824_gb300")
+    dst = tmp_path / "paper_2409_18824_gb300"
+    shutil.copytree(pkg, dst, ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_2409_18824_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True)
+    assert r.returncode != 0 and "libstencil.so is missing" in r.stderr

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Double sweeps follow the same canonical operation order on both sides, so they
+are compared BITWISE; float sweeps likewise against the float oracle.  Norms,
+whose reduction order differs, are compared at 1e-12 relative.  Grids are
+non-cubic and ragged against the 32 x 8 tile so that partial tiles, partial
+k-chunks and every halo duty are exercised.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import stencil_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+L7 = si.LAPLACE7
+NORM_RTOL = 1e-12
+
+
+def to_dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def to_host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def assert_bitwise(got, ref):
+    assert got.shape == ref.shape and got.dtype == ref.dtype
+    bad = np.argwhere(got.view(np.uint8 if got.itemsize == 1 else f"u{got.itemsize}") !=
+                      ref.view(f"u{ref.itemsize}"))
+    assert bad.size == 0, f"{len(bad)} mismatches, first at {bad[0]}: {got[tuple(bad[0])]} vs {ref[tuple(bad[0])]}"
+
+
+SHAPES = [(64, 64, 64), (37, 19, 11), (33, 9, 70), (1, 1, 1), (1, 50, 3), (65, 8, 5), (31, 17, 4)]
+
+
+# ------------------------------------------------------------------ sweeps --
+def test_c1_config_64cubed_100_sweeps_and_norm(lib, cuda):
+    """64^3 FP64, U[0,1) interior (seed 1), zero halo, c = {0, 1/6}, 100 sweeps,
+    then the L2 norm of the residual."""
+    u0 = si.uniform_interior(64, 64, 64, 1, seed=1)
+    ref = oracle.stencil_sweep(u0, L7, 1, 100)
+    d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+    lib.stencil_sweep_f64(d_in, d_out, L7, 1, 100)
+    got = to_host(d_out)
+    assert_bitwise(got, ref)
+    n_ref = oracle.residual_norm(ref, L7, 1)
+    n_gpu = lib.residual_norm_f64(d_out, L7, 1)
+    assert abs(n_gpu - n_ref) <= NORM_RTOL * n_ref
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (1, (0.25, 0.125)), (2, (0.0, 0.125, 1 / 24)),
+                                 (2, (0.2, 0.1, 0.0333))])
+@pytest.mark.parametrize("iters", [1, 2, 5])
+def test_sweep_f64_bitwise(lib, cuda, shape, r, c, iters):
+    nx, ny, nz = shape
+    u0 = si.uniform_interior(nx, ny, nz, r, seed=7, lo=-1, hi=1)
+    # non-zero halo: it must be read and carried to out unchanged
+    halo = np.ones_like(u0, dtype=bool)
+    halo[r:r + nz, r:r + ny, r:r + nx] = False
+    u0[halo] = si.rng(8).random(int(halo.sum()))
+    ref = oracle.stencil_sweep(u0, c, r, iters)
+    d_in, d_out = to_dev(u0), to_dev(np.full_like(u0, np.nan))
+    lib.stencil_sweep_f64(d_in, d_out, c, r, iters)
+    assert_bitwise(to_host(d_out), ref)
+    if iters == 1:
+        assert_bitwise(to_host(d_in), u0)  # in untouched for a single sweep
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.1, 0.1, 0.05))])
+def test_sweep_f32_bitwise(lib, cuda, shape, r, c):
+    nx, ny, nz = shape
+    u0 = si.uniform_interior(nx, ny, nz, r, seed=17, dtype=np.float32)
+    ref = oracle.stencil_sweep(u0, c, r, 3)
+    d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+    lib.stencil_sweep_f32(d_in, d_out, c, r, 3)
+    assert_bitwise(to_host(d_out), ref)
+
+
+def test_sweep_iters_zero_copies(lib, cuda):
+    u0 = si.uniform_interior(9, 8, 7, 1, seed=3)
+    d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+    lib.stencil_sweep_f64(d_in, d_out, L7, 1, 0)
+    assert_bitwise(to_host(d_out), u0)
+
+
+def test_sweep_host_buffers(lib, cuda):
+    """Host (numpy) grids are staged through device memory by the library."""
+    u0 = si.uniform_interior(40, 21, 13, 1, seed=5)
+    ref = oracle.stencil_sweep(u0, L7, 1, 4)
+    h_in, h_out = u0.copy(), np.zeros_like(u0)
+    lib.stencil_sweep_f64(h_in, h_out, L7, 1, 4)
+    assert_bitwise(h_out, ref)
+
+
+def test_eigenmode_decay_1000_sweeps_128(lib, cuda):
+    """Property that holds at any size: the (1,1,1) sine mode decays by exactly
+    lambda = (cos tx + cos ty + cos tz)/3 per sweep."""
+    nx, ny, nz = 128, 96, 80
+    u0 = si.sine_mode(nx, ny, nz, 1)
+    lam = sum(math.cos(math.pi / (n + 1)) for n in (nx, ny, nz)) / 3
+    d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+    lib.stencil_sweep_f64(d_in, d_out, L7, 1, 1000)
+    got = to_host(d_out)
+    expect = lam ** 1000 * u0
+    assert np.max(np.abs(got - expect)) / np.max(np.abs(expect)) < 1e-12
+
+
+# -------------------------------------------------------------- residuals --
+@pytest.mark.parametrize("shape", SHAPES[:5])
+@pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
+def test_residual_norm_with_source(lib, cuda, shape, r, c):
+    nx, ny, nz = shape
+    u = si.uniform_interior(nx, ny, nz, r, seed=23)
+    b = si.normal_interior(nx, ny, nz, r, seed=24)
+    for bb in (None, b):
+        ref = oracle.residual_norm(u, c, r, bb)
+        got = lib.residual_norm_f64(to_dev(u), c, r, b=None if bb is None else to_dev(bb))
+        assert abs(got - ref) <= NORM_RTOL * ref
+    u32, b32 = u.astype(np.float32), b.astype(np.float32)
+    ref32 = oracle.residual_norm(u32, c, r, b32)
+    got32 = lib.residual_norm_f32(to_dev(u32), c, r, b=to_dev(b32))
+    assert abs(got32 - ref32) <= NORM_RTOL * ref32
+
+
+def test_residual_norm_deterministic(lib, cuda):
+    u = to_dev(si.uniform_interior(130, 70, 90, 1, seed=29))
+    vals = {lib.residual_norm_f64(u, L7, 1) for _ in range(5)}
+    assert len(vals) == 1
+
+
+# ------------------------------------------------------------------ solves --
+@pytest.mark.parametrize("shape,K", [((12, 9, 7), 5), ((33, 17, 9), 20), ((5, 4, 6), 1)])
+def test_jacobi_solve_matches_oracle(lib, cuda, shape, K):
+    nx, ny, nz = shape
+    b = si.normal_interior(nx, ny, nz, 1, seed=5)
+    u0 = np.zeros_like(b)
+    tol = 1e-8
+    u_ref, it_ref, rel_ref, st_ref = oracle.jacobi_solve(b, u0, L7, 1, tol, 20000, K)
+    d_u = to_dev(u0)
+    rc, info = lib.jacobi_solve_f64(to_dev(b), d_u, L7, 1, tol, 20000, K)
+    assert rc == st_ref == 0
+    assert info["iters"] == it_ref
+    assert abs(info["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
+    assert_bitwise(to_host(d_u), u_ref)
+
+
+def test_jacobi_solve_not_converged_and_zero_iters(lib, cuda):
+    b = si.normal_interior(10, 10, 10, 1, seed=6)
+    d_u = to_dev(np.zeros_like(b))
+    rc, info = lib.jacobi_solve_f64(to_dev(b), d_u, L7, 1, 1e-14, 30, 7)
+    assert rc == lib.STN_NOT_CONVERGED and info["iters"] == 30
+    u_ref, it_ref, rel_ref, _ = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, 1e-14, 30, 7)
+    assert_bitwise(to_host(d_u), u_ref)
+    assert abs(info["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
+    rc0, info0 = lib.jacobi_solve_f64(to_dev(b), to_dev(np.zeros_like(b)), L7, 1, 1e-3, 0, 7)
+    assert rc0 == lib.STN_NOT_CONVERGED and info0["iters"] == 0
+    assert abs(info0["rel_res"] - 1.0) < 1e-12  # u = 0: rho = b
+
+
+# ---------------------------------------------------- variable coefficient --
+VW = si.VARCOEF_W
+
+
+@pytest.mark.parametrize("shape", [(21, 13, 9), (40, 7, 12), (1, 3, 2)])
+@pytest.mark.parametrize("R", [1, 2])
+def test_varcoef_apply_sweep_residual(lib, cuda, shape, R):
+    nx, ny, nz = shape
+    a = si.uniform_full(nx, ny, nz, R, seed=3)
+    f = si.normal_interior(nx, ny, nz, R, seed=5)
+    u = si.uniform_interior(nx, ny, nz, R, seed=6)
+    w = VW[:R + 1]
+    # apply
+    d_out = to_dev(np.zeros_like(u))
+    lib.varcoef_apply_f64(to_dev(u), to_dev(a), d_out, w, R)
+    assert_bitwise(to_host(d_out), oracle.varcoef_apply(u, a, w, R))
+    # sweeps (double and float)
+    ref = u
+    for _ in range(3):
+        ref = oracle.varcoef_sweep(ref, a, f, w, R)
+    d_in, d_out = to_dev(u), to_dev(np.zeros_like(u))
+    lib.varcoef_sweep_f64(d_in, d_out, to_dev(a), to_dev(f), w, R, 3)
+    assert_bitwise(to_host(d_out), ref)
+    u32, a32, f32 = u.astype(np.float32), a.astype(np.float32), f.astype(np.float32)
+    ref32 = u32
+    for _ in range(3):
+        ref32 = oracle.varcoef_sweep(ref32, a32, f32, w, R)
+    d_in, d_out = to_dev(u32), to_dev(np.zeros_like(u32))
+    lib.varcoef_sweep_f32(d_in, d_out, to_dev(a32), to_dev(f32), w, R, 3)
+    assert_bitwise(to_host(d_out), ref32)
+    # residual
+    nref = oracle.varcoef_residual_norm(u, a, f, w, R)
+    assert abs(lib.varcoef_residual_norm_f64(to_dev(u), to_dev(a), to_dev(f), w, R) - nref) <= NORM_RTOL * nref
+
+
+def test_varcoef_jacobi_solve_matches_oracle(lib, cuda):
+    nx, ny, nz, R = 14, 9, 11, 2
+    a = si.uniform_full(nx, ny, nz, R, seed=3)
+    f = si.normal_interior(nx, ny, nz, R, seed=5)
+    u_ref, it_ref, rel_ref, st = oracle.varcoef_jacobi_solve(a, f, np.zeros_like(f), VW, R, 1e-9, 50000, 25)
+    d_u = to_dev(np.zeros_like(f))
+    rc, info = lib.jacobi_solve_varcoef_f64(to_dev(a), to_dev(f), d_u, VW, R, 1e-9, 50000, 25)
+    assert rc == st == 0 and info["iters"] == it_ref
+    assert abs(info["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
+    assert_bitwise(to_host(d_u), u_ref)
+
+
+def test_refined_solve_matches_oracle(lib, cuda):
+    """Manufactured (1,1,1) sine-mode solution: f = A u* by the oracle.  The float
+    inner sweeps and the double residual/update are bitwise on both sides, so
+    the refined iterate must agree bitwise while the outer-step counts agree."""
+    nx, ny, nz, R = 24, 20, 12, 2
+    a = si.uniform_full(nx, ny, nz, R, seed=3)
+    ustar = si.sine_mode(nx, ny, nz, R)
+    f = oracle.varcoef_apply(ustar, a, VW, R)
+    tol, inner, outer = 1e-10, 400, 30
+    u_ref, o_ref, rel_ref, st_ref = oracle.varcoef_refined_solve(a, f, np.zeros_like(f), VW, R, tol, inner, outer)
+    d_u = to_dev(np.zeros_like(f))
+    rc, info = lib.jacobi_solve_varcoef_refined(to_dev(a), to_dev(f), d_u, VW, R, tol, inner, outer)
+    assert rc == st_ref == 0 and info["outer"] == o_ref
+    got = to_host(d_u)
+    assert_bitwise(got, u_ref)
+    # independent double residual of the returned u
+    assert oracle.varcoef_residual_norm(got, a, f, VW, R) / oracle.interior_norm(f, R) <= tol
