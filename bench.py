@@ -49,6 +49,10 @@ WORKLOADS = {
     "sweep64": dict(nx=64, ny=64, nz=64, r=1, sweeps=100, dtype="f64", seed=1,
                     desc="7-point Jacobi, 64^3 FP64, zero halo, interior U[0,1) seed 1, "
                          "100 sweeps + residual L2 norm"),
+    "sweep320": dict(nx=320, ny=320, nz=320, r=1, sweeps=100, dtype="f64", seed=2,
+                     desc="7-point Jacobi, 320^3 FP64 (268 MB per grid, profiling size), 100 sweeps"),
+    "sweep320f32": dict(nx=320, ny=320, nz=320, r=1, sweeps=100, dtype="f32", seed=2,
+                        desc="7-point Jacobi, 320^3 FP32 (134 MB per grid, profiling size), 100 sweeps"),
     "sweep512f32": dict(nx=512, ny=512, nz=512, r=1, sweeps=1000, dtype="f32", seed=2,
                         desc="7-point Jacobi, 512^3 FP32, zero halo, interior U[0,1) seed 2, "
                              "1000 sweeps + residual L2 norm"),
@@ -156,11 +160,21 @@ def run_cuda(args, wl):
     coeffs = si.LAPLACE7
     u0 = si.uniform_interior(nx, ny, nz, r, seed=wl["seed"] + rank, dtype=npdt)
     d_in = torch.from_numpy(u0).to(dev)
-    d_out = torch.empty_like(d_in)
+    d_out = d_in.clone()
     sweep = stn.stencil_sweep_f64 if f64 else stn.stencil_sweep_f32
     resid = stn.residual_norm_f64 if f64 else stn.residual_norm_f32
     apply_ = stn.stencil_apply_f64 if f64 else stn.stencil_apply_f32
     stream = torch.cuda.current_stream(dev)
+
+    if args.kernel_only:
+        # a few launches of the dominant kernel alone (for profilers)
+        for i in range(args.kernel_only):
+            if i % 2 == 0:
+                apply_(d_in, d_out, coeffs, r)
+            else:
+                apply_(d_out, d_in, coeffs, r)
+        torch.cuda.synchronize(dev)
+        return
 
     def step():
         sweep(d_in, d_out, coeffs, r, sweeps)
@@ -346,6 +360,8 @@ def main():
     ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", type=int, default=0,
+                    help="run only this many single-sweep launches (for profilers), print nothing")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("steps >= 1, warmup >= 0")
