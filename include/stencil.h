@@ -148,6 +148,34 @@ int residual_norm_f32(const float* u, const float* b, int64_t nx, int64_t ny, in
                       const double* coeffs, int radius, double* norm_out, void* stream);
 
 /*
+ * residual_norm_f64_noalloc -- residual_norm_f64 for callers that may not let
+ * the library allocate memory (the paper has no counterpart: this is a
+ * deployment variant).  Such callers include serving processes that have
+ * already given their whole device-memory budget to their own pools, code
+ * that must not call cudaMalloc because it can synchronise the device and
+ * stall the process's other streams, and loops that have no way to report an
+ * allocation failure.  This call allocates nothing: its scratch (up to 65536
+ * per-block partial sums plus a few result slots, 512 KiB in all) is a fixed
+ * array in the library's device image, which every GPU that loads the library
+ * holds until the process exits.
+ *   u, b      DEVICE grids only (host grids: STN_EINVAL, no staging).
+ *   norm_out  HOST double receiving the norm; the call synchronises `stream`.
+ * Same result as residual_norm_f64 (same kernels, same fixed reduction
+ * order).  Grids whose launch plan needs more than 65536 partial sums (one
+ * per 32 x 8 tile of the (i, j) plane once the plane has enough tiles to fill
+ * the GPU: nx*ny above about 16.7 million, e.g. 4096 x 4096) are rejected
+ * with STN_EINVAL before any GPU work.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Every call on a device shares the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * ordered by the caller.  Each call writes every scratch slot it reads, so no
+ * state carries over from one call to the next.
+ */
+int residual_norm_f64_noalloc(const double* u, const double* b, int64_t nx, int64_t ny,
+                              int64_t nz, const double* coeffs, int radius, double* norm_out,
+                              void* stream);
+
+/*
  * jacobi_solve_f64 -- solve u = S u + rhs by Jacobi iteration (Sec. 4).
  * Sweeps run in groups of `check_every` (>= 1); the last sweep of each group
  * is fused with the residual reduction of the iterate it starts from.  The

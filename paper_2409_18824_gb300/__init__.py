@@ -67,6 +67,7 @@ SIGNATURES = {
     "stencil_apply_f32": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
     "residual_norm_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
+    "residual_norm_f64_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "jacobi_solve_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _i64, _info_p, _vp]),
     "varcoef_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
     "varcoef_sweep_f64": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
@@ -189,6 +190,16 @@ def residual_norm_f32(u, coeffs, radius, b=None, nx=None, ny=None, nz=None, stre
     out = ctypes.c_double(0.0)
     _check(_lib.residual_norm_f32(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
                                   _stream(stream, u, b)))
+    return out.value
+
+
+def residual_norm_f64_noalloc(u, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None) -> float:
+    """residual_norm_f64 without any allocation (device grids only; see include/stencil.h)."""
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    out = ctypes.c_double(0.0)
+    _check(_lib.residual_norm_f64_noalloc(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
+                                          _stream(stream, u, b)))
     return out.value
 
 
