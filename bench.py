@@ -165,6 +165,8 @@ def run_cuda(args, wl):
     resid = stn.residual_norm_f64 if f64 else stn.residual_norm_f32
     apply_ = stn.stencil_apply_f64 if f64 else stn.stencil_apply_f32
     stream = torch.cuda.current_stream(dev)
+    stn.stencil_tune_set("star_variant", args.variant)
+    stn.stencil_tune_set("temporal_depth", args.temporal)
 
     if args.kernel_only:
         # a few launches of the dominant kernel alone (for profilers)
@@ -284,7 +286,8 @@ def run_cuda(args, wl):
         "dtype": wl["dtype"],
         "data": "synthetic",
         "config": {"workload": wl["desc"], "nx": nx, "ny": ny, "nz": nz, "radius": r,
-                   "sweeps_per_step": sweeps, "l2": "inputs larger than L2 (1 GiB per grid), no flush",
+                   "sweeps_per_step": sweeps, "kernel_variant": args.variant,
+                   "temporal_depth": args.temporal, "l2": "inputs larger than L2 (1 GiB per grid), no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_val, "unit": "GLUP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * (1 + sweeps + 2),
@@ -360,6 +363,10 @@ def main():
     ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="star-kernel variant (-1 automatic, 0 one point/thread, 1/2 register-blocked)")
+    ap.add_argument("--temporal", type=int, default=0,
+                    help="sweeps fused per HBM pass (0 automatic, 1 off, 2..4)")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="run only this many single-sweep launches (for profilers), print nothing")
     args = ap.parse_args()

@@ -95,6 +95,22 @@ const char* stencil_version(void);
 int stencil_release_workspace(void);
 
 /*
+ * stencil_tune_set / stencil_tune_get -- process-wide kernel-selection knobs
+ * (no paper counterpart; the paper's own tuning is compile-time, Sec. 6).
+ *   "star_variant": -1 automatic (default: 1 for float, 0 for double),
+ *                   0 shared-memory plane kernel (one point per thread),
+ *                   1 register/shuffle column kernel (8 j rows per thread,
+ *                   no shared memory).
+ *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
+ *                   (temporal blocking): 0 automatic (currently 1), 1 off,
+ *                   2..4 (double radius 2: at most 3).
+ * Every variant and depth computes bitwise the same result.  Not thread-safe against
+ * concurrent launches.  Unknown knob or value: STN_EINVAL.
+ */
+int stencil_tune_set(const char* knob, int64_t value);
+int stencil_tune_get(const char* knob, int64_t* value);
+
+/*
  * stencil_sweep_f64 / _f32 -- `iters` Jacobi sweeps of the constant-
  * coefficient star stencil (no source term).  Sec. 4 (the benchmark repeats
  * the sweep a fixed number of iterations).
@@ -162,9 +178,9 @@ int residual_norm_f32(const float* u, const float* b, int64_t nx, int64_t ny, in
  *   norm_out  HOST double receiving the norm; the call synchronises `stream`.
  * Same result as residual_norm_f64 (same kernels, same fixed reduction
  * order).  Grids whose launch plan needs more than 65536 partial sums (one
- * per 32 x 8 tile of the (i, j) plane once the plane has enough tiles to fill
- * the GPU: nx*ny above about 16.7 million, e.g. 4096 x 4096) are rejected
- * with STN_EINVAL before any GPU work.  The first call on a device looks up the array's device address
+ * per 64 x 8 or 32 x 8 tile of the (i, j) plane once the plane has enough
+ * tiles to fill the GPU: nx*ny above roughly 17 to 34 million, e.g.
+ * 8192 x 8192) are rejected with STN_EINVAL before any GPU work.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) for that device; make that first call before any
  * stream capture.  Every call on a device shares the one array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be

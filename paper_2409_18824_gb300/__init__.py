@@ -61,6 +61,8 @@ SIGNATURES = {
     "stencil_last_error": (ctypes.c_char_p, []),
     "stencil_version": (ctypes.c_char_p, []),
     "stencil_release_workspace": (_int, []),
+    "stencil_tune_set": (_int, [ctypes.c_char_p, _i64]),
+    "stencil_tune_get": (_int, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
     "stencil_sweep_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_sweep_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
@@ -264,6 +266,16 @@ def jacobi_solve_varcoef_refined(a, f, u, w, radius, tol, inner_sweeps, max_oute
                                                   inner_sweeps, max_outer, ctypes.byref(info),
                                                   _stream(stream, u, a, f)))
     return rc, info.as_dict()
+
+
+def stencil_tune_set(knob: str, value: int):
+    return _check(_lib.stencil_tune_set(knob.encode(), value))
+
+
+def stencil_tune_get(knob: str) -> int:
+    v = _i64(0)
+    _check(_lib.stencil_tune_get(knob.encode(), ctypes.byref(v)))
+    return v.value
 
 
 def release_workspace():

@@ -42,6 +42,7 @@ struct Grid {
 struct ZPlan {
   int tiles_x, tiles_y, chunks;
   int kchunk;
+  int variant = 0;
   i64 blocks() const { return (i64)tiles_x * tiles_y * chunks; }
 };
 
@@ -68,7 +69,16 @@ int ensure_grid3(Workspace* ws, size_t bytes);
 // ---- constant-coefficient star stencil (sweep.cu) --------------------------
 enum SweepMode { kSweep = 0, kSweepResidual = 1, kResidualOnly = 2 };
 
-ZPlan plan_star(const Grid& g);
+// Star-kernel variants: the shared-memory plane kernel (one point per
+// thread) and the shuffle/register column kernel.
+enum StarVariant { kStarScalar = 0, kStarColumn = 1 };
+ZPlan plan_star(const Grid& g, int variant, size_t esize);
+int star_variant(const Grid& g, size_t esize, const void* a, const void* b, const void* c);
+// Tuning override of the variant choice (-1 = automatic).
+int tune_set_star_variant(int v);
+int tune_get_star_variant();
+// Number of per-block partials launch_star writes for these arguments.
+i64 star_blocks(const Grid& g, size_t esize, const void* u, const void* b, const void* out);
 // One launch: out = S u + b over the interior; in residual modes also the
 // per-block partial sums of rho^2 into `partials` (ZPlan::blocks() entries).
 template <typename T>
@@ -77,6 +87,19 @@ int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coe
 // Copies the halo cells of `src` into `dst` (same geometry).
 template <typename T>
 int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s);
+
+// ---- temporal blocking (temporal.cu) -----------------------------------------
+// `depth` sweeps of the star stencil (no source term) in one pass: out =
+// S^depth(u) on the interior; bitwise equal to depth separate sweeps.
+template <typename T>
+int launch_temporal(const T* u, T* out, const Grid& g, const double* coeffs, int depth,
+                    cudaStream_t s);
+// The depth actually used for a request (1 = no temporal blocking).
+int temporal_depth_supported(int depth, size_t esize, int radius);
+ZPlan plan_temporal(const Grid& g, int depth, int resident);
+// Tuning: temporal depth for stencil_sweep (0 = automatic).
+int tune_set_temporal_depth(int d);
+int tune_get_temporal_depth();
 
 // ---- reductions (reduce.cu) -------------------------------------------------
 // Sums partials[0..n) in a fixed order into dst[0] = sum, dst[1] = sqrt(sum),

@@ -79,8 +79,8 @@ static int noalloc_residual(const double* u, const double* b, i64 nx, i64 ny, i6
     return STN_EINVAL;
   }
   const Grid g{nx, ny, nz, radius};
-  const ZPlan p = plan_star(g);
-  if (p.blocks() > kNoAllocPartials) {
+  const i64 nb = star_blocks(g, sizeof(double), u, b, nullptr);
+  if (nb > kNoAllocPartials) {
     set_error("invalid argument: grid needs more than 65536 partial sums, the size of the "
               "no-allocation scratch (use residual_norm_f64)");
     return STN_EINVAL;
@@ -100,7 +100,7 @@ static int noalloc_residual(const double* u, const double* b, i64 nx, i64 ny, i6
   double* slots = scratch + kNoAllocPartials;
   cudaStream_t s = (cudaStream_t)stream;
   if (int rc = launch_star<double>(u, b, nullptr, g, coeffs, kResidualOnly, partials, s)) return rc;
-  if (int rc = launch_finalize(partials, p.blocks(), slots, nullptr, 0.0, s)) return rc;
+  if (int rc = launch_finalize(partials, nb, slots, nullptr, 0.0, s)) return rc;
   STN_CUDA_TRY(cudaMemcpyAsync(norm_out, slots + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   STN_CUDA_TRY(cudaStreamSynchronize(s));
   return STN_OK;

@@ -1,0 +1,344 @@
+// Constant-coefficient star-stencil sweep (radius 1 or 2) with an optional
+// fused residual reduction -- the Jacobi update of arXiv 2409.18824 Sec. 4
+// (Laplace's equation), in the stencil form of Sec. 2.2, with the sum
+// reduction of Sec. 5.3 / Listing 8 fused into the same pass.
+//
+// Design (z-streaming, "2.5D" blocking):
+//   * a block owns a TX x TY tile of (i, j) columns and streams a chunk of k
+//     planes; i is the contiguous Fortran index, so a warp reads 32
+//     consecutive elements of one row (fully coalesced).
+//   * each thread keeps its column's k-2R..k+R values in a register queue; the
+//     in-plane neighbours (i +- d, j +- d) come from a shared-memory copy of
+//     plane k with an R-wide halo;  the next plane's values are loaded before
+//     the current plane is computed, so loads overlap arithmetic.
+//   * every product and sum is rounded separately in the canonical order (see
+//     include/stencil.h and arith.cuh) so double results are bitwise
+//     reproducible.
+//   * residual modes accumulate rho^2 per thread in double, reduce each block
+//     in a fixed shuffle/shared-memory order and write one partial per block;
+//     reduce.cu adds the partials in index order, so the norm is deterministic
+//     for given extents.
+#pragma once
+#include "arith.cuh"
+#include "internal.h"
+
+namespace stn {
+
+namespace {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+
+template <typename T, int R>
+struct StarCoeffs {
+  T c[R + 1];
+};
+
+// Block-wide sum of a per-thread double in a fixed order; result valid in
+// thread (0, 0).
+template <int NT>
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < NT / 32 ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
+__global__ void __launch_bounds__(TX* TY)
+    star_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
+                int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
+                double* __restrict__ partials) {
+  using A = Arith<T>;
+  __shared__ T tile[TY + 2 * R][TX + 2 * R];
+  __shared__ double red[TX * TY / 32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int gi = blockIdx.x * TX + tx + R;  // padded 0-based column index
+  const int gj = blockIdx.y * TY + ty + R;
+  const i64 sy = NX, sz = (i64)NX * NY;
+  const int k0 = R + blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, nz + R);
+  const bool inx = gi < NX, iny = gj < NY;
+  const bool active = (gi < nx + R) && (gj < ny + R);
+
+  // halo duties: x halo for the first/last R lanes, y halo for the first/last R rows
+  const bool hx = (tx < R) || (tx >= TX - R);
+  const int hx_i = (tx < R) ? gi - R : gi + R;
+  const int hx_lx = (tx < R) ? tx : tx + 2 * R;
+  const bool hx_ok = hx && hx_i < NX && iny;
+  const bool hy = (ty < R) || (ty >= TY - R);
+  const int hy_j = (ty < R) ? gj - R : gj + R;
+  const int hy_ly = (ty < R) ? ty : ty + 2 * R;
+  const bool hy_ok = hy && hy_j < NY && inx;
+
+  const T* pc = u + gi + gj * sy;        // this column
+  const T* px = u + hx_i + gj * sy;      // x-halo column
+  const T* py = u + gi + (i64)hy_j * sy;  // y-halo column
+  const bool ld_c = inx && iny;
+
+  T q[2 * R + 1];
+#pragma unroll
+  for (int m = 0; m < 2 * R + 1; m++) q[m] = ld_c ? pc[(i64)(k0 - R + m) * sz] : T(0);
+  T hxv = hx_ok ? px[(i64)k0 * sz] : T(0);
+  T hyv = hy_ok ? py[(i64)k0 * sz] : T(0);
+  double rsum = 0.0;
+
+  for (int k = k0; k < k1; k++) {
+    const bool more = k + 1 < k1;
+    T qn = T(0), hxn = T(0), hyn = T(0);
+    if (more) {
+      if (ld_c) qn = pc[(i64)(k + 1 + R) * sz];
+      if (hx_ok) hxn = px[(i64)(k + 1) * sz];
+      if (hy_ok) hyn = py[(i64)(k + 1) * sz];
+    }
+    __syncthreads();
+    tile[ty + R][tx + R] = q[R];
+    if (hx) tile[ty + R][hx_lx] = hxv;
+    if (hy) tile[hy_ly][tx + R] = hyv;
+    __syncthreads();
+    if (active) {
+      T acc = T(0);
+#pragma unroll
+      for (int d = R; d >= 1; d--) {
+        T sx = A::add(tile[ty + R][tx + R - d], tile[ty + R][tx + R + d]);
+        T sy_ = A::add(tile[ty + R - d][tx + R], tile[ty + R + d][tx + R]);
+        T szz = A::add(q[R - d], q[R + d]);
+        T s = A::add(A::add(sx, sy_), szz);
+        T t = A::mul(cf.c[d], s);
+        acc = (d == R) ? t : A::add(acc, t);
+      }
+      if (HAS_C0) acc = A::add(acc, A::mul(cf.c[0], q[R]));
+      if (HAS_B) acc = A::add(acc, b[gi + gj * sy + (i64)k * sz]);
+      if (MODE != kResidualOnly) out[gi + gj * sy + (i64)k * sz] = acc;
+      if (MODE != kSweep) {
+        const double rho = (double)acc - (double)q[R];
+        rsum = __fma_rn(rho, rho, rsum);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 2 * R; m++) q[m] = q[m + 1];
+    q[2 * R] = qn;
+    hxv = hxn;
+    hyv = hyn;
+  }
+  if (MODE != kSweep) {
+    const double t = block_sum_fixed<TX * TY>(rsum, red);
+    if (tx == 0 && ty == 0)
+      partials[blockIdx.x + gridDim.x * ((i64)blockIdx.y + (i64)gridDim.y * blockIdx.z)] = t;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Column variant: no shared memory and no barriers.  A warp covers 32
+// consecutive i (the 32 - 2R middle lanes compute, the R lanes at each end
+// only load the halo columns); the i neighbours come from the adjacent lanes
+// by warp shuffle.  Each thread owns SC_TJ consecutive j rows of its column,
+// so the j neighbours are its own registers except for R extra rows above and
+// below, which it loads too.  The k neighbours come from a ring of
+// Q = 2R+1+PF register planes; the k loop is unrolled Q times so the ring
+// rotates by renaming, and plane k+R+PF is loaded before plane k is computed.
+// Addresses are 32-bit offsets from a per-plane base.  Arithmetic and its
+// order are those of star_kernel.
+// ---------------------------------------------------------------------------
+constexpr int SC_WARPS = 4;
+constexpr int SC_TJ = 8;
+
+template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE, int TJ, int PF>
+__global__ void __launch_bounds__(32 * SC_WARPS)
+    star_col_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
+                    int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
+                    double* __restrict__ partials) {
+  using A = Arith<T>;
+  constexpr int Q = 2 * R + 1 + PF;
+  constexpr int CW = 32 - 2 * R;  // computing lanes per warp
+  __shared__ double red[SC_WARPS];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int gi = blockIdx.x * CW + lane;  // padded i of this lane (lane R <-> interior column)
+  const int j0 = R + (blockIdx.y * SC_WARPS + w) * TJ;
+  const i64 sz = (i64)NX * NY;
+  const int k0 = R + blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, nz + R);
+  const bool col_ok = gi < NX;
+  const bool lane_c = lane >= R && lane < 32 - R && gi < nx + R;
+  // row offsets (elements, 32-bit) from this column's top halo row j0-R
+  // rows: 0..R-1 top halo, R..R+TJ-1 own, R+TJ..TJ+2R-1 bottom halo
+  constexpr int NR = TJ + 2 * R;
+  unsigned roff[NR];
+  bool rok[NR];
+#pragma unroll
+  for (int r2 = 0; r2 < NR; r2++) {
+    const int j = j0 - R + r2;
+    rok[r2] = col_ok && j < NY;
+    roff[r2] = (unsigned)r2 * (unsigned)NX;
+  }
+  bool act[TJ];
+#pragma unroll
+  for (int t = 0; t < TJ; t++) act[t] = lane_c && j0 + t < ny + R;
+  const T* ubase = u + gi + (i64)(j0 - R) * NX;
+  T* obase = out ? out + gi + (i64)(j0 - R) * NX : nullptr;
+  const T* bbase = b ? b + gi + (i64)(j0 - R) * NX : nullptr;
+
+  T q[Q][TJ];     // own rows, planes k-R .. k+R+PF
+  T hq[Q][2 * R];  // halo rows (R above, R below), planes k .. k+PF (same ring indexing)
+
+  auto load_own = [&](int slot, int kk) {
+    const T* p = ubase + (i64)kk * sz;
+#pragma unroll
+    for (int t = 0; t < TJ; t++) q[slot][t] = rok[R + t] ? p[roff[R + t]] : T(0);
+  };
+  auto load_halo = [&](int slot, int kk) {
+    const T* p = ubase + (i64)kk * sz;
+#pragma unroll
+    for (int h = 0; h < R; h++) {
+      hq[slot][h] = rok[h] ? p[roff[h]] : T(0);
+      hq[slot][R + h] = rok[R + TJ + h] ? p[roff[R + TJ + h]] : T(0);
+    }
+  };
+#pragma unroll
+  for (int m = 0; m < Q - 1; m++) {
+    const int kk = k0 - R + m;
+    if (kk <= k1 - 1 + R) load_own(m, kk);
+  }
+#pragma unroll
+  for (int m = 0; m < PF; m++)
+    if (k0 + m < k1) load_halo(m, k0 + m);
+  double rsum = 0.0;
+
+  for (int kb = k0; kb < k1; kb += Q) {
+#pragma unroll
+    for (int J = 0; J < Q; J++) {
+      const int k = kb + J;
+      if (k >= k1) break;
+      if (k + PF < k1) {
+        load_own((J + Q - 1) % Q, k + R + PF);
+        load_halo((J + PF) % Q, k + PF);
+      }
+      const T* qc = q[(J + R) % Q];
+      const T* hc = hq[J % Q];
+      const i64 ko = (i64)k * sz;
+      T* op = MODE != kResidualOnly ? obase + ko : nullptr;
+      const T* bp = HAS_B ? bbase + ko : nullptr;
+#pragma unroll
+      for (int t = 0; t < TJ; t++) {
+        const T c = qc[t];
+        T acc = T(0);
+#pragma unroll
+        for (int d = R; d >= 1; d--) {
+          const T xm = __shfl_up_sync(0xffffffffu, c, d);
+          const T xp = __shfl_down_sync(0xffffffffu, c, d);
+          const T ym = t - d >= 0 ? qc[t - d] : hc[t - d + R];
+          const T yp = t + d < TJ ? qc[t + d] : hc[R + t + d - TJ];
+          const T zm = q[(J + R - d) % Q][t], zp = q[(J + R + d) % Q][t];
+          const T s = A::add(A::add(A::add(xm, xp), A::add(ym, yp)), A::add(zm, zp));
+          const T tt = A::mul(cf.c[d], s);
+          acc = (d == R) ? tt : A::add(acc, tt);
+        }
+        if (HAS_C0) acc = A::add(acc, A::mul(cf.c[0], c));
+        if (act[t]) {
+          if (HAS_B) acc = A::add(acc, bp[roff[R + t]]);
+          if (MODE != kResidualOnly) op[roff[R + t]] = acc;
+          if (MODE != kSweep) {
+            const double rho = (double)acc - (double)c;
+            rsum = __fma_rn(rho, rho, rsum);
+          }
+        }
+      }
+    }
+  }
+  if (MODE != kSweep) {
+    const double t = block_sum_fixed<32 * SC_WARPS>(rsum, red);
+    if (lane == 0 && w == 0)
+      partials[blockIdx.x + gridDim.x * ((i64)blockIdx.y + (i64)gridDim.y * blockIdx.z)] = t;
+  }
+}
+
+template <typename T>
+__global__ void copy_halo_kernel(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny,
+                                 int nz, int r) {
+  const int NX = nx + 2 * r, NY = ny + 2 * r, NZ = nz + 2 * r;
+  const i64 rows = (i64)NY * NZ;
+  const int lane = threadIdx.x & 31;
+  const i64 warp0 = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const i64 nwarps = ((i64)gridDim.x * blockDim.x) >> 5;
+  for (i64 row = warp0; row < rows; row += nwarps) {
+    const int j = (int)(row % NY), k = (int)(row / NY);
+    const i64 base = row * NX;
+    if (k < r || k >= nz + r || j < r || j >= ny + r) {
+      for (int i = lane; i < NX; i += 32) dst[base + i] = src[base + i];
+    } else if (lane < 2 * r) {
+      const int i = lane < r ? lane : nx + lane;  // lanes r..2r-1 -> nx+r .. nx+2r-1
+      dst[base + i] = src[base + i];
+    }
+  }
+}
+
+template <typename T, int R, bool HAS_B, bool HAS_C0>
+int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
+                  SweepMode mode, double* partials, cudaStream_t s, int variant) {
+  const ZPlan p = plan_star(g, variant, sizeof(T));
+  StarCoeffs<T, R> cf;
+  for (int d = 0; d <= R; d++) cf.c[d] = (T)coeffs[d];
+  dim3 grid(p.tiles_x, p.tiles_y, p.chunks);
+  const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz, NX = (int)g.NX(), NY = (int)g.NY();
+  constexpr int PF = 1;
+#define STN_LAUNCH_MODES(KERNEL_EXPR, BLOCK)                                                     \
+  switch (mode) {                                                                                \
+    case kSweep: KERNEL_EXPR(kSweep)<<<grid, BLOCK, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials); break; \
+    case kSweepResidual: KERNEL_EXPR(kSweepResidual)<<<grid, BLOCK, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials); break; \
+    default: KERNEL_EXPR(kResidualOnly)<<<grid, BLOCK, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials); break; \
+  }
+#define STN_SCALAR(M) star_kernel<T, R, HAS_B, HAS_C0, M>
+#define STN_COL(M) star_col_kernel<T, R, HAS_B, HAS_C0, M, SC_TJ, PF>
+  if (variant == kStarColumn) {
+    STN_LAUNCH_MODES(STN_COL, dim3(32, SC_WARPS))
+  } else {
+    STN_LAUNCH_MODES(STN_SCALAR, dim3(TX, TY))
+  }
+#undef STN_SCALAR
+#undef STN_COL
+#undef STN_LAUNCH_MODES
+  STN_CUDA_TRY(cudaGetLastError());
+  return STN_OK;
+}
+
+}  // namespace
+
+template <typename T>
+int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
+                SweepMode mode, double* partials, cudaStream_t s) {
+  const bool hb = b != nullptr, hc0 = coeffs[0] != 0.0;
+  const int v = star_variant(g, sizeof(T), u, b, out);
+  if (g.r == 1) {
+    if (hb) return hc0 ? launch_star_t<T, 1, true, true>(u, b, out, g, coeffs, mode, partials, s, v)
+                       : launch_star_t<T, 1, true, false>(u, b, out, g, coeffs, mode, partials, s, v);
+    return hc0 ? launch_star_t<T, 1, false, true>(u, b, out, g, coeffs, mode, partials, s, v)
+               : launch_star_t<T, 1, false, false>(u, b, out, g, coeffs, mode, partials, s, v);
+  }
+  if (hb) return hc0 ? launch_star_t<T, 2, true, true>(u, b, out, g, coeffs, mode, partials, s, v)
+                     : launch_star_t<T, 2, true, false>(u, b, out, g, coeffs, mode, partials, s, v);
+  return hc0 ? launch_star_t<T, 2, false, true>(u, b, out, g, coeffs, mode, partials, s, v)
+             : launch_star_t<T, 2, false, false>(u, b, out, g, coeffs, mode, partials, s, v);
+}
+
+template <typename T>
+int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s) {
+  const i64 rows = g.NY() * g.NZ();
+  i64 blocks = (rows + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  copy_halo_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, (int)g.nx, (int)g.ny, (int)g.nz, g.r);
+  STN_CUDA_TRY(cudaGetLastError());
+  return STN_OK;
+}
+
+
+}  // namespace stn

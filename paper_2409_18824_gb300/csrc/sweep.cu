@@ -1,236 +1,69 @@
-// Constant-coefficient star-stencil sweep (radius 1 or 2) with an optional
-// fused residual reduction -- the Jacobi update of arXiv 2409.18824 Sec. 4
-// (Laplace's equation), in the stencil form of Sec. 2.2, with the sum
-// reduction of Sec. 5.3 / Listing 8 fused into the same pass.
-//
-// Design (z-streaming, "2.5D" blocking):
-//   * a block owns a TX x TY tile of (i, j) columns and streams a chunk of k
-//     planes; i is the contiguous Fortran index, so a warp reads 32
-//     consecutive elements of one row (fully coalesced).
-//   * each thread keeps its column's k-2R..k+R values in a register queue; the
-//     in-plane neighbours (i +- d, j +- d) come from a shared-memory copy of
-//     plane k with an R-wide halo;  the next plane's values are loaded before
-//     the current plane is computed, so loads overlap arithmetic.
-//   * every product and sum is rounded separately in the canonical order (see
-//     include/stencil.h and arith.cuh) so double results are bitwise
-//     reproducible.
-//   * residual modes accumulate rho^2 per thread in double, reduce each block
-//     in a fixed shuffle/shared-memory order and write one partial per block;
-//     reduce.cu adds the partials in index order, so the norm is deterministic
-//     for given extents.
-#include "arith.cuh"
-#include "internal.h"
+// Host-side planning of the star-stencil kernels (star.cuh) and the tuning
+// override; the kernels themselves are instantiated per element type in
+// sweep_f64.cu and sweep_f32.cu so that the two compile in parallel.
+#include "star.cuh"
 
 namespace stn {
 
-namespace {
+static int g_star_variant_override = -1;
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-
-template <typename T, int R>
-struct StarCoeffs {
-  T c[R + 1];
-};
-
-// Block-wide sum of a per-thread double in a fixed order; result valid in
-// thread (0, 0).
-template <int NT>
-__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
-  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (warp == 0) {
-    t = lane < NT / 32 ? red[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  }
-  return t;
-}
-
-template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
-__global__ void __launch_bounds__(TX* TY)
-    star_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
-                int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
-                double* __restrict__ partials) {
-  using A = Arith<T>;
-  __shared__ T tile[TY + 2 * R][TX + 2 * R];
-  __shared__ double red[TX * TY / 32];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int gi = blockIdx.x * TX + tx + R;  // padded 0-based column index
-  const int gj = blockIdx.y * TY + ty + R;
-  const i64 sy = NX, sz = (i64)NX * NY;
-  const int k0 = R + blockIdx.z * kchunk;
-  const int k1 = min(k0 + kchunk, nz + R);
-  const bool inx = gi < NX, iny = gj < NY;
-  const bool active = (gi < nx + R) && (gj < ny + R);
-
-  // halo duties: x halo for the first/last R lanes, y halo for the first/last R rows
-  const bool hx = (tx < R) || (tx >= TX - R);
-  const int hx_i = (tx < R) ? gi - R : gi + R;
-  const int hx_lx = (tx < R) ? tx : tx + 2 * R;
-  const bool hx_ok = hx && hx_i < NX && iny;
-  const bool hy = (ty < R) || (ty >= TY - R);
-  const int hy_j = (ty < R) ? gj - R : gj + R;
-  const int hy_ly = (ty < R) ? ty : ty + 2 * R;
-  const bool hy_ok = hy && hy_j < NY && inx;
-
-  const T* pc = u + gi + gj * sy;        // this column
-  const T* px = u + hx_i + gj * sy;      // x-halo column
-  const T* py = u + gi + (i64)hy_j * sy;  // y-halo column
-  const bool ld_c = inx && iny;
-
-  T q[2 * R + 1];
-#pragma unroll
-  for (int m = 0; m < 2 * R + 1; m++) q[m] = ld_c ? pc[(i64)(k0 - R + m) * sz] : T(0);
-  T hxv = hx_ok ? px[(i64)k0 * sz] : T(0);
-  T hyv = hy_ok ? py[(i64)k0 * sz] : T(0);
-  double rsum = 0.0;
-
-  for (int k = k0; k < k1; k++) {
-    const bool more = k + 1 < k1;
-    T qn = T(0), hxn = T(0), hyn = T(0);
-    if (more) {
-      if (ld_c) qn = pc[(i64)(k + 1 + R) * sz];
-      if (hx_ok) hxn = px[(i64)(k + 1) * sz];
-      if (hy_ok) hyn = py[(i64)(k + 1) * sz];
-    }
-    __syncthreads();
-    tile[ty + R][tx + R] = q[R];
-    if (hx) tile[ty + R][hx_lx] = hxv;
-    if (hy) tile[hy_ly][tx + R] = hyv;
-    __syncthreads();
-    if (active) {
-      T acc = T(0);
-#pragma unroll
-      for (int d = R; d >= 1; d--) {
-        T sx = A::add(tile[ty + R][tx + R - d], tile[ty + R][tx + R + d]);
-        T sy_ = A::add(tile[ty + R - d][tx + R], tile[ty + R + d][tx + R]);
-        T szz = A::add(q[R - d], q[R + d]);
-        T s = A::add(A::add(sx, sy_), szz);
-        T t = A::mul(cf.c[d], s);
-        acc = (d == R) ? t : A::add(acc, t);
-      }
-      if (HAS_C0) acc = A::add(acc, A::mul(cf.c[0], q[R]));
-      if (HAS_B) acc = A::add(acc, b[gi + gj * sy + (i64)k * sz]);
-      if (MODE != kResidualOnly) out[gi + gj * sy + (i64)k * sz] = acc;
-      if (MODE != kSweep) {
-        const double rho = (double)acc - (double)q[R];
-        rsum = __fma_rn(rho, rho, rsum);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 2 * R; m++) q[m] = q[m + 1];
-    q[2 * R] = qn;
-    hxv = hxn;
-    hyv = hyn;
-  }
-  if (MODE != kSweep) {
-    const double t = block_sum_fixed<TX * TY>(rsum, red);
-    if (tx == 0 && ty == 0)
-      partials[blockIdx.x + gridDim.x * ((i64)blockIdx.y + (i64)gridDim.y * blockIdx.z)] = t;
-  }
-}
-
-template <typename T>
-__global__ void copy_halo_kernel(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny,
-                                 int nz, int r) {
-  const int NX = nx + 2 * r, NY = ny + 2 * r, NZ = nz + 2 * r;
-  const i64 rows = (i64)NY * NZ;
-  const int lane = threadIdx.x & 31;
-  const i64 warp0 = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const i64 nwarps = ((i64)gridDim.x * blockDim.x) >> 5;
-  for (i64 row = warp0; row < rows; row += nwarps) {
-    const int j = (int)(row % NY), k = (int)(row / NY);
-    const i64 base = row * NX;
-    if (k < r || k >= nz + r || j < r || j >= ny + r) {
-      for (int i = lane; i < NX; i += 32) dst[base + i] = src[base + i];
-    } else if (lane < 2 * r) {
-      const int i = lane < r ? lane : nx + lane;  // lanes r..2r-1 -> nx+r .. nx+2r-1
-      dst[base + i] = src[base + i];
-    }
-  }
-}
-
-template <typename T, int R, bool HAS_B, bool HAS_C0>
-int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
-                  SweepMode mode, double* partials, cudaStream_t s) {
-  const ZPlan p = plan_star(g);
-  StarCoeffs<T, R> cf;
-  for (int d = 0; d <= R; d++) cf.c[d] = (T)coeffs[d];
-  dim3 grid(p.tiles_x, p.tiles_y, p.chunks), block(TX, TY);
-  const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz, NX = (int)g.NX(), NY = (int)g.NY();
-  switch (mode) {
-    case kSweep:
-      star_kernel<T, R, HAS_B, HAS_C0, kSweep>
-          <<<grid, block, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials);
-      break;
-    case kSweepResidual:
-      star_kernel<T, R, HAS_B, HAS_C0, kSweepResidual>
-          <<<grid, block, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials);
-      break;
-    default:
-      star_kernel<T, R, HAS_B, HAS_C0, kResidualOnly>
-          <<<grid, block, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials);
-      break;
-  }
-  STN_CUDA_TRY(cudaGetLastError());
+int tune_set_star_variant(int v) {
+  if (v < -1 || v > 1) return STN_EINVAL;
+  g_star_variant_override = v;
   return STN_OK;
 }
+int tune_get_star_variant() { return g_star_variant_override; }
 
-}  // namespace
+static int g_temporal_depth = 0;
+int tune_set_temporal_depth(int d) {
+  if (d < 0 || d > 4) return STN_EINVAL;
+  g_temporal_depth = d;
+  return STN_OK;
+}
+int tune_get_temporal_depth() { return g_temporal_depth; }
 
-ZPlan plan_star(const Grid& g) {
+ZPlan plan_star(const Grid& g, int variant, size_t esize) {
   ZPlan p;
-  p.tiles_x = (int)((g.nx + TX - 1) / TX);
-  p.tiles_y = (int)((g.ny + TY - 1) / TY);
-  // enough blocks to fill every SM several times; chunks of >= 4 planes
+  // blocks resident per SM for each variant (register-limited)
+  i64 resident;
+  if (variant == kStarColumn) {
+    p.tiles_x = (int)((g.nx + (32 - 2 * g.r) - 1) / (32 - 2 * g.r));
+    p.tiles_y = (int)((g.ny + SC_WARPS * SC_TJ - 1) / (SC_WARPS * SC_TJ));
+    resident = esize == 4 ? 8 : 5;
+  } else {
+    p.tiles_x = (int)((g.nx + TX - 1) / TX);
+    p.tiles_y = (int)((g.ny + TY - 1) / TY);
+    resident = esize == 4 ? 8 : 5;
+  }
+  const i64 want = 152 * resident;
+  // enough blocks to fill every SM; chunks of >= 4 planes
   const i64 tiles = (i64)p.tiles_x * p.tiles_y;
-  const i64 want = 152 * 8;
   i64 chunks = (want + tiles - 1) / tiles;
   const i64 max_chunks = (g.nz + 3) / 4;
   if (chunks > max_chunks) chunks = max_chunks;
   if (chunks < 1) chunks = 1;
   p.kchunk = (int)((g.nz + chunks - 1) / chunks);
   p.chunks = (int)((g.nz + p.kchunk - 1) / p.kchunk);
+  p.variant = variant;
   return p;
 }
 
-template <typename T>
-int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
-                SweepMode mode, double* partials, cudaStream_t s) {
-  const bool hb = b != nullptr, hc0 = coeffs[0] != 0.0;
-  if (g.r == 1) {
-    if (hb) return hc0 ? launch_star_t<T, 1, true, true>(u, b, out, g, coeffs, mode, partials, s)
-                       : launch_star_t<T, 1, true, false>(u, b, out, g, coeffs, mode, partials, s);
-    return hc0 ? launch_star_t<T, 1, false, true>(u, b, out, g, coeffs, mode, partials, s)
-               : launch_star_t<T, 1, false, false>(u, b, out, g, coeffs, mode, partials, s);
-  }
-  if (hb) return hc0 ? launch_star_t<T, 2, true, true>(u, b, out, g, coeffs, mode, partials, s)
-                     : launch_star_t<T, 2, true, false>(u, b, out, g, coeffs, mode, partials, s);
-  return hc0 ? launch_star_t<T, 2, false, true>(u, b, out, g, coeffs, mode, partials, s)
-             : launch_star_t<T, 2, false, false>(u, b, out, g, coeffs, mode, partials, s);
+int star_variant(const Grid& g, size_t esize, const void* a, const void* b, const void* c) {
+  (void)a;
+  (void)b;
+  (void)c;
+  // the column kernel addresses rows with 32-bit offsets: TJ + 2R rows of NX
+  if ((i64)(SC_TJ + 4) * g.NX() >= ((i64)1 << 31)) return kStarScalar;
+  const int ov = g_star_variant_override;
+  if (ov >= 0) return ov;
+  // float sweeps are memory-bound: the column kernel issues the fewest
+  // instructions per update.  Double sweeps are bound by the FP64 pipe: the
+  // plane kernel keeps every lane of every FP64 instruction useful.
+  return esize == 4 ? kStarColumn : kStarScalar;
 }
 
-template <typename T>
-int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s) {
-  const i64 rows = g.NY() * g.NZ();
-  i64 blocks = (rows + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  copy_halo_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, (int)g.nx, (int)g.ny, (int)g.nz, g.r);
-  STN_CUDA_TRY(cudaGetLastError());
-  return STN_OK;
+i64 star_blocks(const Grid& g, size_t esize, const void* u, const void* b, const void* out) {
+  return plan_star(g, star_variant(g, esize, u, b, out), esize).blocks();
 }
-
-template int launch_star<double>(const double*, const double*, double*, const Grid&,
-                                 const double*, SweepMode, double*, cudaStream_t);
-template int launch_star<float>(const float*, const float*, float*, const Grid&, const double*,
-                                SweepMode, double*, cudaStream_t);
-template int launch_copy_halo<double>(const double*, double*, const Grid&, cudaStream_t);
-template int launch_copy_halo<float>(const float*, float*, const Grid&, cudaStream_t);
 
 }  // namespace stn

@@ -1,0 +1,10 @@
+// float instantiations of the star-stencil launchers (kernels in star.cuh).
+#include "star.cuh"
+
+namespace stn {
+
+template int launch_star<float>(const float*, const float*, float*, const Grid&, const double*, SweepMode,
+                             double*, cudaStream_t);
+template int launch_copy_halo<float>(const float*, float*, const Grid&, cudaStream_t);
+
+}  // namespace stn

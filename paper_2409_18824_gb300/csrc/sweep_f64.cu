@@ -1,0 +1,10 @@
+// double instantiations of the star-stencil launchers (kernels in star.cuh).
+#include "star.cuh"
+
+namespace stn {
+
+template int launch_star<double>(const double*, const double*, double*, const Grid&, const double*, SweepMode,
+                             double*, cudaStream_t);
+template int launch_copy_halo<double>(const double*, double*, const Grid&, cudaStream_t);
+
+}  // namespace stn

@@ -192,7 +192,7 @@ int launch_var_t(const T* u, const T* a, const T* f, T* out, const Grid& g, cons
 
 }  // namespace
 
-ZPlan plan_var(const Grid& g) { return plan_star(g); }
+ZPlan plan_var(const Grid& g) { return plan_star(g, kStarScalar, 8); }
 
 template <typename T>
 int launch_var(const T* u, const T* a, const T* f, T* out, const Grid& g, const double* w,

@@ -106,3 +106,15 @@ def test_binding_fails_loudly_without_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", "import paper_2409_18824_gb300"], cwd=tmp_path,
                        capture_output=True, text=True)
     assert r.returncode != 0 and "libstencil.so is missing" in r.stderr
+
+
+def test_tuning_knobs(lib):
+    assert lib.stencil_tune_get("star_variant") == -1
+    for bad in (-2, 2, 99):
+        with pytest.raises(lib.StencilError):
+            lib.stencil_tune_set("star_variant", bad)
+    with pytest.raises(lib.StencilError):
+        lib.stencil_tune_set("no_such_knob", 0)
+    lib.stencil_tune_set("star_variant", 1)
+    assert lib.stencil_tune_get("star_variant") == 1
+    lib.stencil_tune_set("star_variant", -1)

@@ -38,7 +38,9 @@ def assert_bitwise(got, ref):
     assert bad.size == 0, f"{len(bad)} mismatches, first at {bad[0]}: {got[tuple(bad[0])]} vs {ref[tuple(bad[0])]}"
 
 
-SHAPES = [(64, 64, 64), (37, 19, 11), (33, 9, 70), (1, 1, 1), (1, 50, 3), (65, 8, 5), (31, 17, 4)]
+# odd NX (scalar kernel) and even NX (two-points-per-lane kernel), partial tiles in i and j
+SHAPES = [(64, 64, 64), (37, 19, 11), (33, 9, 70), (1, 1, 1), (1, 50, 3), (65, 8, 5), (31, 17, 4),
+          (36, 19, 11), (62, 9, 70), (2, 3, 2), (130, 7, 9), (126, 17, 5)]
 
 
 # ------------------------------------------------------------------ sweeps --
@@ -86,6 +88,84 @@ def test_sweep_f32_bitwise(lib, cuda, shape, r, c):
     assert_bitwise(to_host(d_out), ref)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sweep_misaligned_grids_use_scalar_path(lib, cuda, dtype):
+    """Grids that start one element past an aligned address cannot take the
+    vector kernel; the scalar kernel must give the same bitwise result."""
+    import torch
+    nx, ny, nz, r = 62, 9, 13, 1
+    u0 = si.uniform_interior(nx, ny, nz, r, seed=41, dtype=dtype)
+    ref = oracle.stencil_sweep(u0, L7, r, 3)
+    n = u0.size
+    base_in = torch.zeros(n + 1, dtype=torch.from_numpy(u0).dtype, device="cuda")
+    base_out = torch.zeros(n + 1, dtype=base_in.dtype, device="cuda")
+    d_in = base_in[1:].view(u0.shape)
+    d_out = base_out[1:].view(u0.shape)
+    d_in.copy_(torch.from_numpy(u0))
+    (lib.stencil_sweep_f64 if dtype == np.float64 else lib.stencil_sweep_f32)(d_in, d_out, L7, r, 3)
+    assert_bitwise(to_host(d_out), ref)
+    if dtype == np.float64:
+        nref = oracle.residual_norm(ref, L7, r)
+        assert abs(lib.residual_norm_f64(d_out, L7, r) - nref) <= NORM_RTOL * nref
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
+def test_every_kernel_variant_bitwise(lib, cuda, variant, r, c):
+    """The one-point-per-thread kernel and both register-blocked kernels give the
+    same bits (forced through the tuning knob), for sweeps, residuals and a
+    solve, on shapes ragged against every tile size."""
+    try:
+        lib.stencil_tune_set("star_variant", variant)
+        for shape in [(64, 64, 64), (37, 19, 11), (130, 33, 9), (62, 70, 5), (2, 1, 3)]:
+            nx, ny, nz = shape
+            u0 = si.uniform_interior(nx, ny, nz, r, seed=nx, lo=-1, hi=1)
+            b = si.normal_interior(nx, ny, nz, r, seed=ny)
+            ref = oracle.stencil_sweep(u0, c, r, 3)
+            d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+            lib.stencil_sweep_f64(d_in, d_out, c, r, 3)
+            assert_bitwise(to_host(d_out), ref)
+            u32 = u0.astype(np.float32)
+            d_in, d_out = to_dev(u32), to_dev(np.zeros_like(u32))
+            lib.stencil_sweep_f32(d_in, d_out, c, r, 3)
+            assert_bitwise(to_host(d_out), oracle.stencil_sweep(u32, c, r, 3))
+            nref = oracle.residual_norm(u0, c, r, b)
+            assert abs(lib.residual_norm_f64(to_dev(u0), c, r, b=to_dev(b)) - nref) <= NORM_RTOL * nref
+        b = si.normal_interior(33, 17, 9, 1, seed=5)
+        u_ref, it_ref, _, _ = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, 1e-8, 20000, 20)
+        d_u = to_dev(np.zeros_like(b))
+        rc, info = lib.jacobi_solve_f64(to_dev(b), d_u, L7, 1, 1e-8, 20000, 20)
+        assert rc == 0 and info["iters"] == it_ref
+        assert_bitwise(to_host(d_u), u_ref)
+    finally:
+        lib.stencil_tune_set("star_variant", -1)
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
+def test_temporal_blocking_bitwise(lib, cuda, depth, dtype, r, c):
+    """depth sweeps fused per pass (temporal blocking) equal depth separate
+    sweeps bit for bit, including a remainder of single sweeps, non-zero halos,
+    ragged tiles (62 x 16 output tiles) and grids thinner than the fused depth."""
+    try:
+        lib.stencil_tune_set("temporal_depth", depth)
+        for shape, iters in [((64, 64, 64), 2 * depth + 1), ((37, 19, 11), depth), ((125, 33, 40), 7),
+                             ((3, 2, 1), depth + 2), ((62, 16, 2), 2 * depth)]:
+            nx, ny, nz = shape
+            u0 = si.uniform_interior(nx, ny, nz, r, seed=nx + 3, lo=-1, hi=1, dtype=dtype)
+            halo = np.ones_like(u0, dtype=bool)
+            halo[r:r + nz, r:r + ny, r:r + nx] = False
+            u0[halo] = si.rng(9).random(int(halo.sum())).astype(dtype)
+            ref = oracle.stencil_sweep(u0, c, r, iters)
+            d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+            fn = lib.stencil_sweep_f64 if dtype == np.float64 else lib.stencil_sweep_f32
+            fn(d_in, d_out, c, r, iters)
+            assert_bitwise(to_host(d_out), ref)
+    finally:
+        lib.stencil_tune_set("temporal_depth", 0)
+
+
 def test_sweep_iters_zero_copies(lib, cuda):
     u0 = si.uniform_interior(9, 8, 7, 1, seed=3)
     d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
@@ -116,7 +196,7 @@ def test_eigenmode_decay_1000_sweeps_128(lib, cuda):
 
 
 # -------------------------------------------------------------- residuals --
-@pytest.mark.parametrize("shape", SHAPES[:5])
+@pytest.mark.parametrize("shape", SHAPES[:5] + SHAPES[7:9])
 @pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
 def test_residual_norm_with_source(lib, cuda, shape, r, c):
     nx, ny, nz = shape

@@ -45,6 +45,6 @@ def test_noalloc_rejects_host_grids_and_oversize(lib, cuda):
     u = si.uniform_interior(8, 8, 8, 1, seed=1)
     rc, _ = _abi_call(lib, u.ctypes.data, None, 8, 8, 8, si.LAPLACE7, 1)
     assert rc == lib.STN_EINVAL and "device grids only" in lib.last_error()
-    # 4096 x 4100 plane: more partial sums than the scratch holds; rejected before any GPU work
-    rc, _ = _abi_call(lib, 0x7F0000000000, None, 4096, 4100, 4, si.LAPLACE7, 1)
+    # 8192 x 8200 plane: more partial sums than the scratch holds; rejected before any GPU work
+    rc, _ = _abi_call(lib, 0x7F0000000000, None, 8192, 8200, 4, si.LAPLACE7, 1)
     assert rc == lib.STN_EINVAL and "65536" in lib.last_error()
