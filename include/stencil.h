@@ -210,6 +210,58 @@ int jacobi_solve_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64
                      int64_t check_every, stn_solve_info* info, void* stream);
 
 /*
+ * jacobi_solve_refined_f64 -- mixed-precision iterative refinement of
+ * u = S u + rhs (not in the paper; double only for the residual and the
+ * update):
+ *   outer (double): t = S u + rhs, rho = t - u; stop if ||rho|| <= tol*||rhs||
+ *                   (absolute if ||rhs|| = 0); s = max|rho|; r32 = float(rho/s)
+ *   inner (float) : sweeps of e = S e + r32 from e = 0 (coefficients rounded to
+ *                   float), in groups of check_every; stop after a group whose
+ *                   last sweep changed e by <= inner_tol*||r32|| (inner_tol = 0:
+ *                   never), or after inner_sweeps sweeps
+ *   update(double): u = u + s * double(e)
+ * up to max_outer outer steps.  Device grids only.  info->outer = outer
+ * steps, info->iters = float sweeps, info->rel_res = last double relative
+ * residual.  Synchronises.  Returns STN_OK or STN_NOT_CONVERGED.
+ */
+int jacobi_solve_refined_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64_t nz,
+                             const double* coeffs, int radius, double tol, int64_t inner_sweeps,
+                             double inner_tol, int64_t check_every, int64_t max_outer,
+                             stn_solve_info* info, void* stream);
+
+/*
+ * Batched solves: many independent problems of different extents (a C4-style
+ * batch) in ONE persistent kernel launch of thread-block clusters.  Each
+ * cluster takes the next problem (largest estimated work first) from a
+ * device-side queue and iterates it to convergence; sweeps are separated by
+ * the cluster's hardware barrier and convergence checks are reduced in a
+ * fixed order, so every result is bitwise independent of the rest of the
+ * batch and its sweeps are those of the single-problem path.
+ *   probs   HOST array of `count` problems; their grids are DEVICE memory, each
+ *           its own (problems must not share or overlap grids).
+ *   infos   HOST array of `count` results (may be NULL).
+ * The library allocates the scratch grids of the batch (stream-ordered) and
+ * frees them before returning.  Synchronises `stream`.  Returns STN_OK when
+ * every problem converged, STN_NOT_CONVERGED when one did not, or an error.
+ */
+typedef struct stn_problem {
+  int64_t nx, ny, nz;  /* interior extents */
+  const double* rhs;   /* source term grid (device), or NULL */
+  double* u;           /* initial guess in, last iterate out (device) */
+} stn_problem;
+
+/* Plain double Jacobi for each problem; same stopping rule as jacobi_solve_f64. */
+int jacobi_solve_batched_f64(const stn_problem* probs, int64_t count, const double* coeffs,
+                             int radius, double tol, int64_t max_iters, int64_t check_every,
+                             stn_solve_info* infos, void* stream);
+
+/* Refinement of jacobi_solve_refined_f64 for each problem. */
+int jacobi_solve_batched_refined(const stn_problem* probs, int64_t count, const double* coeffs,
+                                 int radius, double tol, int64_t inner_sweeps, double inner_tol,
+                                 int64_t check_every, int64_t max_outer, stn_solve_info* infos,
+                                 void* stream);
+
+/*
  * Variable-coefficient operator, radius R in {1, 2}, weights w[0..R] (HOST;
  * w[0] unused), per-point coefficient field a on the full padded grid:
  *   (A u)(p) = sum_{d=1..R} w_d sum_{q = p +- d e_x, e_y, e_z} kappa(p,q) (u(p) - u(q)),

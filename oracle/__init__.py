@@ -81,6 +81,8 @@ def _load():
                                                             ctypes.c_int, ctypes.c_double, _i64, _i64,
                                                             ctypes.POINTER(_i64), _dp]),
             "oracle_dense_solve": (ctypes.c_int, [_dp, _dp, _i64]),
+            "oracle_refined_solve_f64": (ctypes.c_int, [_dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int,
+                                                        ctypes.c_double, _i64, _i64, ctypes.POINTER(_i64), _dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -253,6 +255,21 @@ def varcoef_refined_solve(a, f, u0, w, R, tol, inner_sweeps, max_outer):
                                           _ptr(u, ctypes.c_double), *interior_shape(u, R),
                                           _ptr(ww, ctypes.c_double), R, tol, inner_sweeps, max_outer,
                                           ctypes.byref(outer), ctypes.byref(rel))
+    if st < 0:
+        raise MemoryError("oracle allocation failed")
+    return u, outer.value, rel.value, st
+
+
+def refined_solve(b, u0, coeffs, r, tol, inner_sweeps, max_outer):
+    """Constant-coefficient refinement; returns (u, outer, rel_res, status)."""
+    lib = _load()
+    u = _grid(u0, np.float64).copy()
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    outer = _i64(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.oracle_refined_solve_f64(_ptr(b, ctypes.c_double), _ptr(u, ctypes.c_double), *interior_shape(u, r),
+                                      _ptr(c, ctypes.c_double), r, tol, inner_sweeps, max_outer,
+                                      ctypes.byref(outer), ctypes.byref(rel))
     if st < 0:
         raise MemoryError("oracle allocation failed")
     return u, outer.value, rel.value, st

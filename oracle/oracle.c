@@ -435,6 +435,77 @@ int oracle_varcoef_refined_solve(const double* a, const double* f, double* u, i6
 }
 
 /* ---------------------------------------------------------------------------
+ * Mixed-precision iterative refinement for u = S u + b (constant
+ * coefficients).  Not in the paper; steps in order:
+ *   outer (double): t = S u + b; rho = t - u; stop if ||rho|| <= tol*||b||
+ *                   (absolute when b = 0); s = max|rho|; r32 = float(rho / s)
+ *   inner (float) : `inner_sweeps` sweeps of e = S e + r32 from e = 0, with
+ *                   the coefficients rounded to float
+ *   update(double): u = u + s * double(e)
+ * Returns 0 if converged within max_outer steps, 1 if not.
+ * ------------------------------------------------------------------------- */
+int oracle_refined_solve_f64(const double* b, double* u, i64 nx, i64 ny, i64 nz, const double* c,
+                             int r, double tol, i64 inner_sweeps, i64 max_outer, i64* outer_out,
+                             double* rel_res_out) {
+  const i64 NX = nx + 2 * r, NY = ny + 2 * r, NZ = nz + 2 * r;
+  const i64 n = NX * NY * NZ;
+  double* t = (double*)calloc((size_t)n, sizeof(double));
+  float* r32 = (float*)calloc((size_t)n, sizeof(float));
+  float* e = (float*)calloc((size_t)n, sizeof(float));
+  float* e2 = (float*)calloc((size_t)n, sizeof(float));
+  if (!t || !r32 || !e || !e2) {
+    free(t); free(r32); free(e); free(e2);
+    return -2;
+  }
+  float c32[3] = {0.0f, 0.0f, 0.0f};
+  for (int d = 0; d <= r; d++) c32[d] = (float)c[d];
+  const double bnorm = b ? oracle_interior_norm_f64(b, nx, ny, nz, r) : 0.0;
+  const double scale = bnorm > 0.0 ? bnorm : 1.0;
+  double rel = INFINITY;
+  i64 outer = 0;
+  int status = 1;
+  for (;;) {
+    oracle_sweep_f64(u, b, t, nx, ny, nz, c, r);
+    double ss = 0.0, amax = 0.0;
+    for (i64 k = r; k < nz + r; k++)
+      for (i64 j = r; j < ny + r; j++)
+        for (i64 i = r; i < nx + r; i++) {
+          const i64 p = off3(i, j, k, NX, NY);
+          double rho = t[p] - u[p];
+          ss = ss + rho * rho;
+          if (fabs(rho) > amax) amax = fabs(rho);
+        }
+    rel = sqrt(ss) / scale;
+    if (rel <= tol) { status = 0; break; }
+    if (outer >= max_outer || amax == 0.0) break;
+    for (i64 k = r; k < nz + r; k++)
+      for (i64 j = r; j < ny + r; j++)
+        for (i64 i = r; i < nx + r; i++) {
+          const i64 p = off3(i, j, k, NX, NY);
+          r32[p] = (float)((t[p] - u[p]) / amax);
+          e[p] = 0.0f;
+        }
+    float* cur = e;
+    float* nxt = e2;
+    for (i64 s = 0; s < inner_sweeps; s++) {
+      oracle_sweep_f32(cur, r32, nxt, nx, ny, nz, c32, r);
+      float* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    for (i64 k = r; k < nz + r; k++)
+      for (i64 j = r; j < ny + r; j++)
+        for (i64 i = r; i < nx + r; i++) {
+          const i64 p = off3(i, j, k, NX, NY);
+          u[p] = u[p] + amax * (double)cur[p];
+        }
+    outer++;
+  }
+  free(t); free(r32); free(e); free(e2);
+  *outer_out = outer;
+  *rel_res_out = rel;
+  return status;
+}
+
+/* ---------------------------------------------------------------------------
  * Dense Gaussian elimination with partial pivoting (textbook), A is n x n
  * row-major and overwritten; b is overwritten with the solution.  Used to
  * solve tiny systems exactly as a pin for the iterative solves.

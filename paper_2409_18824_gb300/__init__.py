@@ -36,6 +36,11 @@ class StencilError(RuntimeError):
         self.code = code
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("rhs", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("outer", ctypes.c_int64), ("rel_res", ctypes.c_double),
                 ("res_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double), ("status", ctypes.c_int)]
@@ -71,6 +76,12 @@ SIGNATURES = {
     "residual_norm_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f64_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "jacobi_solve_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _i64, _info_p, _vp]),
+    "jacobi_solve_refined_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _dbl, _i64, _i64,
+                                        _info_p, _vp]),
+    "jacobi_solve_batched_f64": (_int, [ctypes.POINTER(Problem), _i64, _dp, _int, _dbl, _i64, _i64, _info_p,
+                                        _vp]),
+    "jacobi_solve_batched_refined": (_int, [ctypes.POINTER(Problem), _i64, _dp, _int, _dbl, _i64, _dbl, _i64,
+                                            _i64, _info_p, _vp]),
     "varcoef_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
     "varcoef_sweep_f64": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "varcoef_sweep_f32": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
@@ -214,6 +225,49 @@ def jacobi_solve_f64(rhs, u, coeffs, radius, tol, max_iters, check_every=50, nx=
     rc = _check(_lib.jacobi_solve_f64(_addr(rhs), _addr(u), nx, ny, nz, cp, radius, tol, max_iters,
                                       check_every, ctypes.byref(info), _stream(stream, u, rhs)))
     return rc, info.as_dict()
+
+
+def jacobi_solve_refined_f64(rhs, u, coeffs, radius, tol, inner_sweeps, inner_tol=0.0, check_every=50,
+                             max_outer=50, nx=None, ny=None, nz=None, stream=None):
+    """Returns (status, info dict)."""
+    nx, ny, nz = _extents(u, radius, nx, ny, nz)
+    cp, _keep = _coeffs(coeffs)
+    info = SolveInfo()
+    rc = _check(_lib.jacobi_solve_refined_f64(_addr(rhs), _addr(u), nx, ny, nz, cp, radius, tol, inner_sweeps,
+                                              inner_tol, check_every, max_outer, ctypes.byref(info),
+                                              _stream(stream, u, rhs)))
+    return rc, info.as_dict()
+
+
+def _problems(us, rhss, radius):
+    n = len(us)
+    arr = (Problem * max(n, 1))()
+    for i, (u, b) in enumerate(zip(us, rhss)):
+        nx, ny, nz = _extents(u, radius, None, None, None)
+        arr[i].nx, arr[i].ny, arr[i].nz = nx, ny, nz
+        arr[i].rhs = _addr(b)
+        arr[i].u = _addr(u)
+    return arr, n
+
+
+def jacobi_solve_batched_f64(us, rhss, coeffs, radius, tol, max_iters, check_every=50, stream=None):
+    """Solves every (u, rhs) pair in one persistent launch; returns (status, [info dicts])."""
+    arr, n = _problems(us, rhss, radius)
+    cp, _keep = _coeffs(coeffs)
+    infos = (SolveInfo * max(n, 1))()
+    rc = _check(_lib.jacobi_solve_batched_f64(arr, n, cp, radius, tol, max_iters, check_every, infos,
+                                              _stream(stream, *us)))
+    return rc, [infos[i].as_dict() for i in range(n)]
+
+
+def jacobi_solve_batched_refined(us, rhss, coeffs, radius, tol, inner_sweeps, inner_tol=0.0, check_every=50,
+                                 max_outer=50, stream=None):
+    arr, n = _problems(us, rhss, radius)
+    cp, _keep = _coeffs(coeffs)
+    infos = (SolveInfo * max(n, 1))()
+    rc = _check(_lib.jacobi_solve_batched_refined(arr, n, cp, radius, tol, inner_sweeps, inner_tol,
+                                                  check_every, max_outer, infos, _stream(stream, *us)))
+    return rc, [infos[i].as_dict() for i in range(n)]
 
 
 def varcoef_apply_f64(u, a, out, w, radius, nx=None, ny=None, nz=None, stream=None):

@@ -604,6 +604,40 @@ static int refined_impl(const double* a, const double* f, double* u, i64 nx, i64
   return status;
 }
 
+static int batch_impl(const stn_problem* probs, i64 count, const double* coeffs, int radius,
+                      double tol, i64 iters, i64 check_every, double inner_tol, i64 max_outer,
+                      bool refined, stn_solve_info* infos, void* stream) {
+  clear_error();
+  if (count < 0) return einval("count < 0");
+  if (count > 0 && !probs) return einval("NULL problem array");
+  if (!coeffs) return einval("NULL coeffs");
+  if (!(tol >= 0.0)) return einval("tol must be >= 0");
+  if (iters < 0) return einval("iteration limit < 0");
+  if (check_every < 1) return einval("check_every < 1");
+  if (!(inner_tol >= 0.0)) return einval("inner_tol must be >= 0");
+  if (max_outer < 0) return einval("max_outer < 0");
+  if (count > (1 << 30)) return einval("too many problems");
+  for (i64 i = 0; i < count; i++) {
+    const stn_problem& p = probs[i];
+    if (int rc = check_grid(p.nx, p.ny, p.nz, radius)) return rc;
+    if (p.nx > (1 << 20) || p.ny > (1 << 20) || p.nz > (1 << 20))
+      return einval("batched problem extent too large");
+    if (!p.u) return einval("NULL problem grid");
+    const size_t bytes = (size_t)Grid{p.nx, p.ny, p.nz, radius}.count() * sizeof(double);
+    if (p.rhs && overlap(p.rhs, p.u, bytes)) return einval("problem rhs overlaps its u");
+  }
+  if (count == 0) return STN_OK;
+  for (i64 i = 0; i < count; i++) {
+    bool h = false;
+    if (int rc = classify(probs[i].u, &h)) return rc;
+    if (!h && probs[i].rhs)
+      if (int rc = classify(probs[i].rhs, &h)) return rc;
+    if (h) return einval("batched problems take device grids only");
+  }
+  return batched_solve(probs, count, coeffs, radius, tol, iters, check_every, inner_tol, max_outer,
+                       refined, infos, (cudaStream_t)stream);
+}
+
 }  // namespace stn
 
 // ===================================================================== ABI ==
@@ -682,6 +716,37 @@ int jacobi_solve_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64
                      const double* coeffs, int radius, double tol, int64_t max_iters,
                      int64_t check_every, stn_solve_info* info, void* stream) {
   return jacobi_impl(rhs, u, nx, ny, nz, coeffs, radius, tol, max_iters, check_every, info, stream);
+}
+
+int jacobi_solve_refined_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64_t nz,
+                             const double* coeffs, int radius, double tol, int64_t inner_sweeps,
+                             double inner_tol, int64_t check_every, int64_t max_outer,
+                             stn_solve_info* info, void* stream) {
+  clear_error();
+  if (!u) return einval("NULL grid");
+  stn_problem p;
+  p.nx = nx;
+  p.ny = ny;
+  p.nz = nz;
+  p.rhs = rhs;
+  p.u = u;
+  return batch_impl(&p, 1, coeffs, radius, tol, inner_sweeps, check_every, inner_tol, max_outer, true,
+                    info, stream);
+}
+
+int jacobi_solve_batched_f64(const stn_problem* probs, int64_t count, const double* coeffs,
+                             int radius, double tol, int64_t max_iters, int64_t check_every,
+                             stn_solve_info* infos, void* stream) {
+  return batch_impl(probs, count, coeffs, radius, tol, max_iters, check_every, 0.0, 0, false, infos,
+                    stream);
+}
+
+int jacobi_solve_batched_refined(const stn_problem* probs, int64_t count, const double* coeffs,
+                                 int radius, double tol, int64_t inner_sweeps, double inner_tol,
+                                 int64_t check_every, int64_t max_outer, stn_solve_info* infos,
+                                 void* stream) {
+  return batch_impl(probs, count, coeffs, radius, tol, inner_sweeps, check_every, inner_tol,
+                    max_outer, true, infos, stream);
 }
 
 int varcoef_apply_f64(const double* u, const double* a, double* out, int64_t nx, int64_t ny,

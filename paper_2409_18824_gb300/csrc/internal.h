@@ -101,6 +101,15 @@ ZPlan plan_temporal(const Grid& g, int depth, int resident);
 int tune_set_temporal_depth(int d);
 int tune_get_temporal_depth();
 
+// ---- batched solves (batched.cu) --------------------------------------------
+// One persistent cluster launch over `count` problems (device grids).
+// refined = false: plain double Jacobi, `iters` = max sweeps per problem.
+// refined = true: `iters` = max float sweeps per outer step, inner_tol the
+// inner stop, max_outer the outer steps.  Synchronises `s`.
+int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int radius, double tol,
+                  i64 iters, i64 check_every, double inner_tol, i64 max_outer, bool refined,
+                  stn_solve_info* infos, cudaStream_t s);
+
 // ---- reductions (reduce.cu) -------------------------------------------------
 // Sums partials[0..n) in a fixed order into dst[0] = sum, dst[1] = sqrt(sum),
 // and, if scale_src is not NULL, dst[2] = sqrt(sum) / scale with

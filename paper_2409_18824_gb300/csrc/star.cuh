@@ -53,20 +53,23 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
   return t;
 }
 
+// One 32 x 8 tile of columns (tile_x, tile_y) over planes [k0, k1): the body
+// of star_kernel, also called in loops by the persistent batched solver.
+// Accumulates rho^2 of its points into *rsum in residual modes.  Every thread
+// of the block must call it (it uses __syncthreads); `tile` is the block's
+// TY+2R x TX+2R shared plane.  The pointers carry no __restrict__: the
+// batched solver reads grids that other CTAs of its launch wrote, which must
+// go through the coherent load path.
 template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
-__global__ void __launch_bounds__(TX* TY)
-    star_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
-                int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
-                double* __restrict__ partials) {
+__device__ __forceinline__ void star_tile(const T* u, const T* b, T* out, int nx, int ny, int NX, int NY,
+                                          int tile_x, int tile_y, int k0, int k1,
+                                          const StarCoeffs<T, R>& cf, T (*tile)[TX + 2 * R],
+                                          double* rsum_io) {
   using A = Arith<T>;
-  __shared__ T tile[TY + 2 * R][TX + 2 * R];
-  __shared__ double red[TX * TY / 32];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int gi = blockIdx.x * TX + tx + R;  // padded 0-based column index
-  const int gj = blockIdx.y * TY + ty + R;
+  const int gi = tile_x * TX + tx + R;  // padded 0-based column index
+  const int gj = tile_y * TY + ty + R;
   const i64 sy = NX, sz = (i64)NX * NY;
-  const int k0 = R + blockIdx.z * kchunk;
-  const int k1 = min(k0 + kchunk, nz + R);
   const bool inx = gi < NX, iny = gj < NY;
   const bool active = (gi < nx + R) && (gj < ny + R);
 
@@ -80,8 +83,8 @@ __global__ void __launch_bounds__(TX* TY)
   const int hy_ly = (ty < R) ? ty : ty + 2 * R;
   const bool hy_ok = hy && hy_j < NY && inx;
 
-  const T* pc = u + gi + gj * sy;        // this column
-  const T* px = u + hx_i + gj * sy;      // x-halo column
+  const T* pc = u + gi + gj * sy;         // this column
+  const T* px = u + hx_i + gj * sy;       // x-halo column
   const T* py = u + gi + (i64)hy_j * sy;  // y-halo column
   const bool ld_c = inx && iny;
 
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(TX* TY)
   for (int m = 0; m < 2 * R + 1; m++) q[m] = ld_c ? pc[(i64)(k0 - R + m) * sz] : T(0);
   T hxv = hx_ok ? px[(i64)k0 * sz] : T(0);
   T hyv = hy_ok ? py[(i64)k0 * sz] : T(0);
-  double rsum = 0.0;
+  double rsum = *rsum_io;
 
   for (int k = k0; k < k1; k++) {
     const bool more = k + 1 < k1;
@@ -130,13 +133,28 @@ __global__ void __launch_bounds__(TX* TY)
     hxv = hxn;
     hyv = hyn;
   }
+  __syncthreads();  // the tile buffer is free again when this returns
+  *rsum_io = rsum;
+}
+
+template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
+__global__ void __launch_bounds__(TX* TY)
+    star_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
+                int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
+                double* __restrict__ partials) {
+  __shared__ T tile[TY + 2 * R][TX + 2 * R];
+  __shared__ double red[TX * TY / 32];
+  const int k0 = R + blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, nz + R);
+  double rsum = 0.0;
+  star_tile<T, R, HAS_B, HAS_C0, MODE>(u, b, out, nx, ny, NX, NY, blockIdx.x, blockIdx.y, k0, k1, cf,
+                                        tile, &rsum);
   if (MODE != kSweep) {
     const double t = block_sum_fixed<TX * TY>(rsum, red);
-    if (tx == 0 && ty == 0)
+    if (threadIdx.x == 0 && threadIdx.y == 0)
       partials[blockIdx.x + gridDim.x * ((i64)blockIdx.y + (i64)gridDim.y * blockIdx.z)] = t;
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Column variant: no shared memory and no barriers.  A warp covers 32

@@ -1,0 +1,127 @@
+"""Batched persistent solves (one cluster launch over many problems) and the
+mixed-precision refinement, against the CPU oracle.
+
+A batched problem's sweeps are the single-problem path's sweeps (same tile
+code, same canonical order), so its iterate must agree bitwise with the
+oracle's Jacobi solve whenever the iteration counts agree; and a problem's
+result must not depend on which other problems share the launch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import stencil_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+L7 = si.LAPLACE7
+NORM_RTOL = 1e-12
+
+
+def to_dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def to_host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def bitwise(a, b):
+    return a.shape == b.shape and np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+SIZES = [(16, 16, 16), (23, 17, 40), (40, 9, 11), (8, 30, 12), (33, 33, 5), (5, 6, 7), (1, 1, 1), (64, 20, 9)]
+
+
+def make_batch(sizes, seed0=5):
+    rhs = [si.normal_interior(nx, ny, nz, 1, seed=seed0 + i) for i, (nx, ny, nz) in enumerate(sizes)]
+    return rhs
+
+
+def test_batched_f64_matches_oracle_and_is_composition_independent(lib, cuda):
+    rhs = make_batch(SIZES)
+    tol, K, maxit = 1e-8, 10, 40000
+    d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+    d_b = [to_dev(b) for b in rhs]
+    rc, infos = lib.jacobi_solve_batched_f64(d_u, d_b, L7, 1, tol, maxit, K)
+    assert rc == 0
+    got = [to_host(u) for u in d_u]
+    for i, b in enumerate(rhs):
+        u_ref, it_ref, rel_ref, st = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, tol, maxit, K)
+        assert st == 0 and infos[i]["status"] == 0
+        assert infos[i]["iters"] == it_ref, (i, infos[i], it_ref)
+        assert abs(infos[i]["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
+        assert bitwise(got[i], u_ref), i
+    # the same problem alone, and in a different mix, gives the same bits
+    for pick in ([3], [6, 3, 0]):
+        d_u2 = [to_dev(np.zeros_like(rhs[i])) for i in pick]
+        d_b2 = [to_dev(rhs[i]) for i in pick]
+        rc2, infos2 = lib.jacobi_solve_batched_f64(d_u2, d_b2, L7, 1, tol, maxit, K)
+        assert rc2 == 0
+        for j, i in enumerate(pick):
+            assert bitwise(to_host(d_u2[j]), got[i])
+            assert infos2[j]["iters"] == infos[i]["iters"] and infos2[j]["rel_res"] == infos[i]["rel_res"]
+
+
+def test_batched_not_converged_and_empty(lib, cuda):
+    rhs = make_batch(SIZES[:3])
+    d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+    rc, infos = lib.jacobi_solve_batched_f64(d_u, [to_dev(b) for b in rhs], L7, 1, 1e-14, 25, 10)
+    assert rc == lib.STN_NOT_CONVERGED and all(i["iters"] == 25 and i["status"] == 1 for i in infos)
+    for i, b in enumerate(rhs):
+        u_ref, _, rel_ref, _ = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, 1e-14, 25, 10)
+        assert bitwise(to_host(d_u[i]), u_ref)
+    assert lib.jacobi_solve_batched_f64([], [], L7, 1, 1e-8, 10, 10) == (0, [])
+
+
+def test_batched_rejects_host_grids(lib, cuda):
+    b = si.normal_interior(4, 4, 4, 1, seed=1)
+    with pytest.raises(lib.StencilError):
+        lib.jacobi_solve_batched_f64([np.zeros_like(b)], [b], L7, 1, 1e-8, 10, 10)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_refined_fixed_inner_matches_oracle(lib, cuda, batched):
+    """With a fixed number of float sweeps per outer step the refinement is a
+    fixed sequence of roundings: bitwise equal to the oracle's refinement."""
+    sizes = [(20, 14, 9), (9, 9, 9), (31, 7, 12)]
+    rhs = make_batch(sizes, seed0=11)
+    tol, inner, outer_max = 1e-10, 150, 40
+    refs = [oracle.refined_solve(b, np.zeros_like(b), L7, 1, tol, inner, outer_max) for b in rhs]
+    if batched:
+        d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+        rc, infos = lib.jacobi_solve_batched_refined(d_u, [to_dev(b) for b in rhs], L7, 1, tol, inner, 0.0, 50,
+                                                     outer_max)
+        assert rc == 0
+    else:
+        d_u, infos = [], []
+        for b in rhs:
+            u = to_dev(np.zeros_like(b))
+            rc, info = lib.jacobi_solve_refined_f64(to_dev(b), u, L7, 1, tol, inner, 0.0, 50, outer_max)
+            assert rc == 0
+            d_u.append(u)
+            infos.append(info)
+    for i, (u_ref, o_ref, rel_ref, st) in enumerate(refs):
+        assert st == 0 and infos[i]["outer"] == o_ref and infos[i]["iters"] == o_ref * inner
+        got = to_host(d_u[i])
+        assert bitwise(got, u_ref), i
+        # independent double residual of the returned iterate
+        assert oracle.residual_norm(got, L7, 1, rhs[i]) / oracle.interior_norm(rhs[i], 1) <= tol
+
+
+def test_refined_adaptive_inner_reaches_tolerance(lib, cuda):
+    sizes = [(40, 30, 20), (16, 16, 16), (12, 50, 7)]
+    rhs = make_batch(sizes, seed0=21)
+    tol = 1e-10
+    d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+    rc, infos = lib.jacobi_solve_batched_refined(d_u, [to_dev(b) for b in rhs], L7, 1, tol, 20000, 1e-3, 25, 50)
+    assert rc == 0
+    for i, b in enumerate(rhs):
+        got = to_host(d_u[i])
+        rel = oracle.residual_norm(got, L7, 1, b) / oracle.interior_norm(b, 1)
+        assert rel <= tol and abs(rel - infos[i]["rel_res"]) <= 1e-6 * tol
+        u_ref, _, _, _ = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, 1e-13, 200000, 100)
+        assert np.max(np.abs(got - u_ref)) / np.max(np.abs(u_ref)) < 1e-6

@@ -314,3 +314,21 @@ def test_refined_solve_reaches_tolerance():
     assert res <= tol and abs(res - rel) <= 1e-3 * tol
     x = np.linalg.solve(Ai, f.ravel()[mask])
     assert np.max(np.abs(u.ravel()[mask] - x)) / np.max(np.abs(x)) < 10 * np.linalg.cond(Ai) * tol
+
+
+def test_constant_refined_solve_reaches_tolerance():
+    """Constant-coefficient refinement end state: its reported double residual is
+    recomputed from the dense operator, and u matches the direct solve of
+    (I - S) u = b."""
+    nx, ny, nz, r = 5, 4, 6, 1
+    b = si.normal_interior(nx, ny, nz, r, seed=5)
+    mask = interior_mask(nx, ny, nz, r)
+    S = dense_sweep_operator(nx, ny, nz, r, L7)[:, mask]
+    M = np.eye(mask.sum()) - S
+    tol = 1e-12
+    u, outer, rel, st = oracle.refined_solve(b, np.zeros_like(b), L7, r, tol, 300, 40)
+    assert st == 0 and outer >= 2
+    res = np.linalg.norm(b.ravel()[mask] - M @ u.ravel()[mask]) / np.linalg.norm(b.ravel()[mask])
+    assert res <= tol and abs(res - rel) <= 1e-3 * tol
+    x = np.linalg.solve(M, b.ravel()[mask])
+    assert np.max(np.abs(u.ravel()[mask] - x)) / np.max(np.abs(x)) < 10 * np.linalg.cond(M) * tol
