@@ -304,6 +304,107 @@ def run_cuda(args, wl):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------- batched solves ----
+def batch_problems(count, seed_sizes=4, seed_rhs=5):
+    """Per-axis sizes log-uniform in [16, 128] (PCG64 seed 4); right-hand sides
+    N(0,1), problem i drawn from PCG64 seed 5 * 1000003 + i; zero halo."""
+    sizes = si.log_uniform_sizes(count, 16, 128, seed_sizes)
+    return [tuple(int(v) for v in s) for s in sizes], [seed_rhs * 1000003 + i for i in range(count)]
+
+
+def run_batched(args):
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sizes, seeds = batch_problems(args.batch)
+    tol = 1e-8
+    # one allocation per array kind; problems are views into it
+    counts = [(nx + 2) * (ny + 2) * (nz + 2) for nx, ny, nz in sizes]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    total = int(offs[-1])
+    h_rhs = torch.empty(total, dtype=torch.float64).pin_memory()
+    hr = h_rhs.numpy()
+    for i, (nx, ny, nz) in enumerate(sizes):
+        hr[offs[i]:offs[i + 1]] = si.normal_interior(nx, ny, nz, 1, seed=seeds[i]).ravel()
+    d_rhs = h_rhs.to(dev)
+    d_u = torch.zeros(total, dtype=torch.float64, device=dev)
+    us = [d_u[offs[i]:offs[i + 1]].view(nz + 2, ny + 2, nx + 2) for i, (nx, ny, nz) in enumerate(sizes)]
+    bs = [d_rhs[offs[i]:offs[i + 1]].view(nz + 2, ny + 2, nx + 2) for i, (nx, ny, nz) in enumerate(sizes)]
+    refined = args.refined
+
+    def step():
+        d_u.zero_()
+        if refined:
+            rc, infos = stn.jacobi_solve_batched_refined(us, bs, si.LAPLACE7, 1, tol, args.inner_max,
+                                                         args.inner_tol, 50, 40)
+        else:
+            rc, infos = stn.jacobi_solve_batched_f64(us, bs, si.LAPLACE7, 1, tol, 10 ** 7, 100)
+        return rc, infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    times, lups, all_infos = [], 0.0, None
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, infos = step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+            all_infos = infos
+    ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    pts = np.array([nx * ny * nz for nx, ny, nz in sizes], dtype=np.float64)
+    iters = np.array([i["iters"] for i in all_infos], dtype=np.float64)
+    lups = float((pts * iters).sum())
+    conv = sum(1 for i in all_infos if i["status"] == 0)
+    value = args.batch * ws * args.steps / (ms * 1e-3)
+    # e2e: right-hand sides from pinned host memory in, solutions out, inside the timed region
+    h_u = torch.empty(total, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d_rhs.copy_(h_rhs, non_blocking=True)
+    step()
+    h_u.copy_(d_u, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    out = {
+        "metric": "batched solves/s (2048 Jacobi/Poisson solves, sizes log-U[16,128], tol 1e-8)",
+        "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 refined" if refined else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.batch} independent 7-point Poisson solves u = S u + b, per-axis sizes "
+                               f"log-uniform in [16,128] (seed 4), b ~ N(0,1), tol 1e-8, one persistent "
+                               f"cluster launch" + (", FP32 sweeps with FP64 refinement" if refined else ", FP64"),
+                   "batch": args.batch, "points": int(pts.sum()), "l2": "no flush (each solve re-reads its grid)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": {"value": args.batch / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": total * 8,
+                "d2h_bytes_per_step": total * 8},
+        "gpu_launches": args.steps * 1,
+        "aggregate_glups": lups / (ms / args.steps * 1e-3) / 1e9,
+        "converged": conv,
+        "sweeps_max": int(iters.max()), "sweeps_median": float(np.median(iters)),
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 # ------------------------------------------------------------ oracle (CPU) --
 def cpu_sample(wl, sweeps):
     import oracle
@@ -360,7 +461,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--batch", type=int, default=2048, help="problems in the batched workload")
+    ap.add_argument("--refined", action="store_true", help="batched workload: FP32 sweeps + FP64 refinement")
+    ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--inner-max", type=int, default=200000)
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=-1,
@@ -372,6 +477,13 @@ def main():
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("steps >= 1, warmup >= 0")
+    if args.workload == "batch":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "batched workload: CPU oracle arm only "
+                              "implemented for the sweep workloads"}))
+            return
+        run_batched(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

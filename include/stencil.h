@@ -104,7 +104,10 @@ int stencil_release_workspace(void);
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
  *                   (temporal blocking): 0 automatic (currently 1), 1 off,
  *                   2..4 (double radius 2: at most 3).
- * Every variant and depth computes bitwise the same result.  Not thread-safe against
+ *   "batch_engine": batched solvers: 0 dynamic work-unit scheduler (default:
+ *                   any CTA may take any unit of any problem in flight),
+ *                   1 one thread-block cluster per problem.
+ * Every variant, depth and engine computes bitwise the same iterates.  Not thread-safe against
  * concurrent launches.  Unknown knob or value: STN_EINVAL.
  */
 int stencil_tune_set(const char* knob, int64_t value);

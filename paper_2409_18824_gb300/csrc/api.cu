@@ -660,6 +660,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_temporal_depth((int)value) != STN_OK) return einval("temporal_depth must be 0..4");
     return STN_OK;
   }
+  if (strcmp(knob, "batch_engine") == 0) {
+    if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0 or 1");
+    return STN_OK;
+  }
   return einval("unknown knob");
 }
 
@@ -672,6 +676,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "temporal_depth") == 0) {
     *value = tune_get_temporal_depth();
+    return STN_OK;
+  }
+  if (strcmp(knob, "batch_engine") == 0) {
+    *value = tune_get_batch_engine();
     return STN_OK;
   }
   return einval("unknown knob");

@@ -18,10 +18,13 @@
 // runs the sweeps of the correction equation e = S e + rho/s in float.
 #include <cooperative_groups.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "work_sched.h"
 #include "star.cuh"
 
 namespace cg = cooperative_groups;
@@ -379,9 +382,9 @@ static double est_work(i64 nx, i64 ny, i64 nz) {
   return (double)nx * ny * nz / g;
 }
 
-int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int radius, double tol,
-                  i64 iters, i64 check_every, double inner_tol, i64 max_outer, bool refined,
-                  stn_solve_info* infos, cudaStream_t s) {
+static int batched_clusters(const stn_problem* probs, i64 count, const double* coeffs, int radius,
+                            double tol, i64 iters, i64 check_every, double inner_tol, i64 max_outer,
+                            bool refined, stn_solve_info* infos, cudaStream_t s) {
   std::vector<BatchProblem> hp((size_t)count);
   std::vector<int> order((size_t)count);
   size_t pool64 = 0, pool32 = 0;
@@ -526,6 +529,176 @@ int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int
     if (r.status != STN_OK) worst = STN_NOT_CONVERGED;
   }
   return worst;
+}
+
+// Scheduler engine: one persistent launch of the dynamic unit scheduler
+// (sched.cu) over all problems, queued largest estimated work first.
+static int batched_sched(const stn_problem* probs, i64 count, const double* coeffs, int radius,
+                         double tol, i64 iters, i64 check_every, double inner_tol, i64 max_outer,
+                         bool refined, stn_solve_info* infos, cudaStream_t s) {
+  const bool hc0 = coeffs[0] != 0.0;
+  const int ctas = sched_ctas(radius, hc0);
+  if (ctas < 1) {
+    set_error("scheduler kernel does not fit on an SM");
+    return STN_ECUDA;
+  }
+  const int nslots = (int)std::min<i64>(count, 96);
+  // layout of one device allocation
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_probs = take(sizeof(SchedProblem) * count);
+  const size_t o_slots = take(sizeof(SchedSlot) * nslots);
+  const size_t o_words = take(sizeof(unsigned long long) * nslots);
+  const size_t o_queue = take(sizeof(int) * count);
+  const size_t o_ctr = take(sizeof(int) * 8);
+  const size_t o_res = take(sizeof(SchedResult) * count);
+  const size_t o_flags = take(sizeof(int) * count);
+  std::vector<size_t> o_t((size_t)count), o_part((size_t)count), o_e((size_t)count);
+  std::vector<size_t> npts((size_t)count);
+  std::vector<int> nunits((size_t)count);
+  for (i64 i = 0; i < count; i++) {
+    const stn_problem& p = probs[i];
+    npts[i] = (size_t)((p.nx + 2 * radius) * (p.ny + 2 * radius) * (p.nz + 2 * radius));
+    nunits[i] = (int)sched_units(p.nx, p.ny, p.nz);
+    o_t[i] = take(sizeof(double) * npts[i]);
+    o_part[i] = take(sizeof(double) * nunits[i]);
+  }
+  const size_t o_f32 = off;
+  for (i64 i = 0; i < count && refined; i++) o_e[i] = take(3 * sizeof(float) * ((npts[i] + 63) / 64 * 64));
+  const size_t total = off + 256;
+  char* base = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&base, total, s);
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    set_error("batched solver: device allocation of scratch failed");
+    return STN_ENOMEM;
+  }
+  STN_CUDA_TRY(e);
+  std::vector<SchedProblem> hp((size_t)count);
+  std::vector<double> work((size_t)count);
+  std::vector<int> order((size_t)count);
+  for (i64 i = 0; i < count; i++) {
+    const stn_problem& p = probs[i];
+    SchedProblem& q = hp[i];
+    q.nx = (int)p.nx;
+    q.ny = (int)p.ny;
+    q.nz = (int)p.nz;
+    q.nunits = nunits[i];
+    q.u = p.u;
+    q.b = p.rhs;
+    q.t = (double*)(base + o_t[i]);
+    q.partials = (double*)(base + o_part[i]);
+    q.e = q.e2 = q.r32 = nullptr;
+    if (refined) {
+      const size_t n32 = (npts[i] + 63) / 64 * 64;
+      q.e = (float*)(base + o_e[i]);
+      q.e2 = q.e + n32;
+      q.r32 = q.e2 + n32;
+    }
+    order[i] = (int)i;
+    work[i] = est_work(p.nx, p.ny, p.nz);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+  std::vector<SchedSlot> hs((size_t)nslots);
+  for (auto& sl : hs) {
+    memset(&sl, 0, sizeof(sl));
+    sl.claim_free = 1;
+  }
+  std::vector<SchedResult> hres((size_t)count);
+  int herr = 0;
+  int rc = STN_OK;
+  do {
+    if ((e = cudaMemcpyAsync(base + o_probs, hp.data(), sizeof(SchedProblem) * count, cudaMemcpyHostToDevice, s))) break;
+    if ((e = cudaMemcpyAsync(base + o_slots, hs.data(), sizeof(SchedSlot) * nslots, cudaMemcpyHostToDevice, s))) break;
+    if ((e = cudaMemsetAsync(base + o_words, 0, sizeof(unsigned long long) * nslots, s))) break;
+    if ((e = cudaMemcpyAsync(base + o_queue, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s))) break;
+    if ((e = cudaMemsetAsync(base + o_ctr, 0, sizeof(int) * 8, s))) break;
+    if ((e = cudaMemsetAsync(base + o_flags, 0, sizeof(int) * count, s))) break;
+    const int free0 = nslots;
+    if ((e = cudaMemcpyAsync(base + o_ctr + 3 * sizeof(int), &free0, sizeof(int), cudaMemcpyHostToDevice, s))) break;
+    if (refined && (e = cudaMemsetAsync(base + o_f32, 0, off - o_f32, s))) break;
+    bool bad = false;
+    for (i64 i = 0; i < count; i++)
+      if ((e = cudaMemcpyAsync(hp[i].t, hp[i].u, sizeof(double) * npts[i], cudaMemcpyDeviceToDevice, s))) {
+        bad = true;
+        break;
+      }
+    if (bad) break;
+    SchedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.probs = (SchedProblem*)(base + o_probs);
+    a.slots = (SchedSlot*)(base + o_slots);
+    a.words = (unsigned long long*)(base + o_words);
+    a.nslots = nslots;
+    a.count = (int)count;
+    a.queue = (const int*)(base + o_queue);
+    a.qcap = (int)count;
+    int* ctr = (int*)(base + o_ctr);
+    a.qhead = ctr + 0;
+    a.finished = ctr + 1;
+    a.error = ctr + 2;
+    a.free_slots = ctr + 3;
+    a.qtail = nullptr;
+    a.serving = 0;
+    a.results = (SchedResult*)(base + o_res);
+    a.done_flags = (int*)(base + o_flags);
+    for (int d = 0; d < 3; d++) a.coeffs[d] = d <= radius ? coeffs[d] : 0.0;
+    a.tol = tol;
+    a.max_iters = iters;
+    a.check_every = check_every;
+    a.inner_tol = inner_tol;
+    a.max_outer = max_outer;
+    a.refined = refined ? 1 : 0;
+    a.idle_cycles = 4000000000ll;  // about 2 s at GB300 clocks without any claimable unit
+    if ((rc = sched_launch(a, radius, hc0, ctas, s)) != STN_OK) break;
+    if ((e = cudaMemcpyAsync(hres.data(), base + o_res, sizeof(SchedResult) * count, cudaMemcpyDeviceToHost, s))) break;
+    if ((e = cudaMemcpyAsync(&herr, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
+    if ((e = cudaStreamSynchronize(s))) break;
+  } while (false);
+  cudaFreeAsync(base, s);
+  if (rc != STN_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "batched scheduler");
+  if (herr != 0) {
+    set_error(herr == STN_ETIMEOUT ? "batched scheduler: a CTA found no work for 2 s (stalled)"
+                                   : "batched scheduler: device error");
+    return herr;
+  }
+  int worst = STN_OK;
+  for (i64 i = 0; i < count; i++) {
+    const SchedResult& r = hres[i];
+    if (infos) {
+      infos[i].iters = r.iters;
+      infos[i].outer = r.outer;
+      infos[i].rel_res = r.rel_res;
+      infos[i].res_norm = r.res_norm;
+      infos[i].rhs_norm = r.rhs_norm;
+      infos[i].status = r.status;
+    }
+    if (r.status != STN_OK) worst = STN_NOT_CONVERGED;
+  }
+  return worst;
+}
+
+static int g_batch_engine = 0;
+int tune_set_batch_engine(int v) {
+  if (v < 0 || v > 1) return STN_EINVAL;
+  g_batch_engine = v;
+  return STN_OK;
+}
+int tune_get_batch_engine() { return g_batch_engine; }
+
+int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int radius, double tol,
+                  i64 iters, i64 check_every, double inner_tol, i64 max_outer, bool refined,
+                  stn_solve_info* infos, cudaStream_t s) {
+  if (g_batch_engine == 1)
+    return batched_clusters(probs, count, coeffs, radius, tol, iters, check_every, inner_tol, max_outer,
+                            refined, infos, s);
+  return batched_sched(probs, count, coeffs, radius, tol, iters, check_every, inner_tol, max_outer,
+                       refined, infos, s);
 }
 
 }  // namespace stn

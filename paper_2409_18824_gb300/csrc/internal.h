@@ -110,6 +110,10 @@ int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int
                   i64 iters, i64 check_every, double inner_tol, i64 max_outer, bool refined,
                   stn_solve_info* infos, cudaStream_t s);
 
+// Tuning: batched engine (0 = dynamic unit scheduler, 1 = one cluster per problem).
+int tune_set_batch_engine(int v);
+int tune_get_batch_engine();
+
 // ---- reductions (reduce.cu) -------------------------------------------------
 // Sums partials[0..n) in a fixed order into dst[0] = sum, dst[1] = sqrt(sum),
 // and, if scale_src is not NULL, dst[2] = sqrt(sum) / scale with

@@ -1,0 +1,555 @@
+// Dynamic persistent scheduler for many Jacobi solves (batched and served).
+//
+// One persistent kernel runs one wave of CTAs.  Every active problem advances
+// pass by pass (a pass = one data-parallel step: a sweep, a residual sweep, an
+// element-wise refinement step).  A pass is split into work units (32 x 8
+// column tiles x a chunk of k planes) that any CTA may claim, so a large
+// problem soaks up every CTA the small ones leave idle, and a problem's
+// critical path shrinks to its own work divided by the whole GPU.
+//
+//   claim     : 64-bit word per slot = (pass id << 32) | next unit; one
+//               atomicAdd claims a unit AND names the pass it belongs to.
+//   complete  : per-unit partial results are written to the problem's
+//               partials array, then a release fence and an atomicAdd on the
+//               slot's done counter; the CTA that completes the last unit
+//               runs the pass epilogue.
+//   epilogue  : reduces the partials in unit order (a fixed tree: results do
+//               not depend on which CTA did what), advances the problem's
+//               state machine, resets the counters and publishes the next
+//               pass with an atomic exchange of the claim word (release).
+// Sweeps are computed by star_tile, the code of the single-problem kernels,
+// so every sweep is bitwise the single-problem sweep.  There is no device
+// wait on another CTA's progress except the bounded idle back-off of a CTA
+// that found no work; it gives up after `idle_ns` and records STN_ETIMEOUT
+// (batch) or simply returns (serving, where the host relaunches on demand).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "work_sched.h"
+#include "star.cuh"
+
+namespace stn {
+
+namespace {
+
+constexpr int BT = TX * TY;
+
+enum Phase : int {
+  PH_IDLE = 0,
+  PH_INIT = 1,    // sum b^2 (rhs norm)
+  PH_SWEEP = 2,   // plain double sweep cur -> nxt (residual on a group's last)
+  PH_COPY = 3,    // u <- t (interior)
+  PH_RES = 4,     // refined: t = S u + b, sum rho^2
+  PH_MAX = 5,     // refined: max |t - u|
+  PH_SCALE = 6,   // refined: r32 = float((t-u)/s), e = 0, sum r32^2
+  PH_INNER = 7,   // refined: float sweep e -> e' (residual on a group's last)
+  PH_UPDATE = 8,  // refined: u += s * e
+};
+
+struct Geo {
+  int tiles_x, tiles_y, kc, klen, n;
+};
+
+__host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
+  Geo g;
+  g.tiles_x = (nx + TX - 1) / TX;
+  g.tiles_y = (ny + TY - 1) / TY;
+  // chunks of at most 64 planes, at least enough units to spread a big
+  // problem over the GPU
+  int kc = (nz + 63) / 64;
+  if (kc < 1) kc = 1;
+  g.klen = (nz + kc - 1) / kc;
+  g.kc = (nz + g.klen - 1) / g.klen;
+  g.n = g.tiles_x * g.tiles_y * g.kc;
+  return g;
+}
+
+__device__ __forceinline__ int tid_flat() { return threadIdx.x + TX * threadIdx.y; }
+
+__device__ __forceinline__ double bmax(double v, double* red) {
+  const int lane = tid_flat() & 31, warp = tid_flat() >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < BT / 32 ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+  }
+  __syncthreads();
+  return t;
+}
+
+// Fixed-order reduction of n partials by the whole CTA (tree shape depends
+// on n only); result valid in thread 0.
+__device__ __forceinline__ double reduce_parts(const double* p, int n, bool is_max, double* red) {
+  double v = 0.0;
+  for (int i = tid_flat(); i < n; i += BT) v = is_max ? fmax(v, p[i]) : v + p[i];
+  if (is_max) return bmax(v, red);
+  const double s = block_sum_fixed<BT>(v, red);
+  __syncthreads();
+  return s;
+}
+
+// Calls f(p) for every interior point of unit q, k outer; thread (tx, ty)
+// owns one column of the unit's tile.
+template <int R, typename F>
+__device__ __forceinline__ void for_unit_points(const SchedProblem& P, const Geo& g, int q, F&& f) {
+  const int tiles = g.tiles_x * g.tiles_y;
+  const int kci = q / tiles, tq = q - kci * tiles;
+  const int tyi = tq / g.tiles_x, txi = tq - tyi * g.tiles_x;
+  const int i = txi * TX + threadIdx.x + R, j = tyi * TY + threadIdx.y + R;
+  if (i >= P.nx + R || j >= P.ny + R) return;
+  const i64 NX = P.nx + 2 * R, NY = P.ny + 2 * R;
+  const int k0 = R + kci * g.klen, k1 = min(k0 + g.klen, P.nz + R);
+  for (int k = k0; k < k1; k++) f((i64)i + NX * ((i64)j + NY * k));
+}
+
+template <typename T, int R, bool HAS_C0, int MODE>
+__device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, const SchedProblem& P,
+                                             const Geo& g, int q, const StarCoeffs<T, R>& cf,
+                                             T (*tile)[TX + 2 * R]) {
+  const int tiles = g.tiles_x * g.tiles_y;
+  const int kci = q / tiles, tq = q - kci * tiles;
+  const int tyi = tq / g.tiles_x, txi = tq - tyi * g.tiles_x;
+  const int k0 = R + kci * g.klen, k1 = min(k0 + g.klen, P.nz + R);
+  const int NX = P.nx + 2 * R, NY = P.ny + 2 * R;
+  double rs = 0.0;
+  if (b)
+    star_tile<T, R, true, HAS_C0, MODE>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tile, &rs);
+  else
+    star_tile<T, R, false, HAS_C0, MODE>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf,
+                                         tile, &rs);
+  return rs;
+}
+
+struct SmemPlanes {
+  double d[TY + 4][TX + 4];
+  float f[TY + 4][TX + 4];
+};
+
+// Processes unit q of the slot's current pass; returns the partial (valid in
+// thread 0) to store at partials[q].
+template <int R, bool HAS_C0>
+__device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedProblem& P, int q,
+                           SmemPlanes& sp, double* red) {
+  const Geo g = make_geo(P.nx, P.ny, P.nz);
+  StarCoeffs<double, R> c64;
+  StarCoeffs<float, R> c32;
+#pragma unroll
+  for (int d = 0; d <= R; d++) {
+    c64.c[d] = a.coeffs[d];
+    c32.c[d] = (float)a.coeffs[d];
+  }
+  auto* t64 = reinterpret_cast<double(*)[TX + 2 * R]>(&sp.d[0][0]);
+  auto* t32 = reinterpret_cast<float(*)[TX + 2 * R]>(&sp.f[0][0]);
+  double v = 0.0;
+  switch (S.phase) {
+    case PH_INIT: {
+      if (P.b) for_unit_points<R>(P, g, q, [&](i64 p) {
+          const double x = P.b[p];
+          v = __fma_rn(x, x, v);
+        });
+      return block_sum_fixed<BT>(v, red);
+    }
+    case PH_SWEEP: {
+      double* cur = S.parity ? P.t : P.u;
+      double* nxt = S.parity ? P.u : P.t;
+      if (S.resid)
+        v = unit_sweep<double, R, HAS_C0, kSweepResidual>(cur, P.b, nxt, P, g, q, c64, t64);
+      else
+        unit_sweep<double, R, HAS_C0, kSweep>(cur, P.b, nxt, P, g, q, c64, t64);
+      return block_sum_fixed<BT>(v, red);
+    }
+    case PH_COPY: {
+      for_unit_points<R>(P, g, q, [&](i64 p) { P.u[p] = P.t[p]; });
+      return 0.0;
+    }
+    case PH_RES: {
+      v = unit_sweep<double, R, HAS_C0, kSweepResidual>(P.u, P.b, P.t, P, g, q, c64, t64);
+      return block_sum_fixed<BT>(v, red);
+    }
+    case PH_MAX: {
+      for_unit_points<R>(P, g, q, [&](i64 p) { v = fmax(v, fabs(__dsub_rn(P.t[p], P.u[p]))); });
+      return bmax(v, red);
+    }
+    case PH_SCALE: {
+      const double s = S.smax;
+      for_unit_points<R>(P, g, q, [&](i64 p) {
+        const float x = __double2float_rn(__ddiv_rn(__dsub_rn(P.t[p], P.u[p]), s));
+        P.r32[p] = x;
+        P.e[p] = 0.0f;
+        v = __fma_rn((double)x, (double)x, v);
+      });
+      return block_sum_fixed<BT>(v, red);
+    }
+    case PH_INNER: {
+      float* cur = S.parity ? P.e2 : P.e;
+      float* nxt = S.parity ? P.e : P.e2;
+      if (S.resid)
+        v = unit_sweep<float, R, HAS_C0, kSweepResidual>(cur, P.r32, nxt, P, g, q, c32, t32);
+      else
+        unit_sweep<float, R, HAS_C0, kSweep>(cur, P.r32, nxt, P, g, q, c32, t32);
+      return block_sum_fixed<BT>(v, red);
+    }
+    case PH_UPDATE: {
+      const double s = S.smax;
+      const float* e = S.parity ? P.e2 : P.e;
+      for_unit_points<R>(P, g, q, [&](i64 p) { P.u[p] = __dadd_rn(P.u[p], __dmul_rn(s, (double)e[p])); });
+      return 0.0;
+    }
+    default:
+      return 0.0;
+  }
+}
+
+// Sets up a group of sweeps of the slot (counts are set; the caller publishes).
+__device__ __forceinline__ void start_group(const SchedArgs& a, SchedSlot& S, long long done_so_far,
+                                            long long limit) {
+  long long left = limit - done_so_far;
+  S.group = a.check_every < left ? a.check_every : left;
+  S.group_pos = 0;
+  S.resid = S.group == 1 ? 1 : 0;
+}
+
+// Advances the slot's state machine after a completed pass.  `red_val` is
+// the reduced partial of that pass.  Returns true when the problem finished.
+__device__ bool advance(const SchedArgs& a, SchedSlot& S, const SchedProblem& P, double red_val) {
+  switch (S.phase) {
+    case PH_INIT: {
+      S.bnorm = sqrt(red_val);
+      S.scale = S.bnorm > 0.0 ? S.bnorm : 1.0;
+      S.iters = 0;
+      S.outer = 0;
+      S.sweeps = 0;
+      S.parity = 0;
+      if (a.refined) {
+        S.phase = PH_RES;
+        S.resid = 1;
+        return false;
+      }
+      if (a.max_iters <= 0) {
+        S.status = STN_NOT_CONVERGED;
+        return true;
+      }
+      S.phase = PH_SWEEP;
+      start_group(a, S, 0, a.max_iters);
+      return false;
+    }
+    case PH_SWEEP: {
+      S.iters++;
+      S.parity ^= 1;
+      S.group_pos++;
+      if (S.group_pos == S.group) {
+        S.res = sqrt(red_val);
+        S.rel = S.res / S.scale;
+        if (S.rel <= a.tol) S.status = STN_OK;
+        else if (S.iters >= a.max_iters) S.status = STN_NOT_CONVERGED;
+        else {
+          start_group(a, S, S.iters, a.max_iters);
+          return false;
+        }
+        if (S.parity) {  // the last iterate is in t
+          S.phase = PH_COPY;
+          return false;
+        }
+        return true;
+      }
+      S.resid = S.group_pos == S.group - 1 ? 1 : 0;
+      return false;
+    }
+    case PH_COPY:
+      return true;
+    case PH_RES: {
+      S.res = sqrt(red_val);
+      S.rel = S.res / S.scale;
+      if (S.rel <= a.tol) {
+        S.status = STN_OK;
+        return true;
+      }
+      if (S.outer >= a.max_outer) {
+        S.status = STN_NOT_CONVERGED;
+        return true;
+      }
+      S.phase = PH_MAX;
+      return false;
+    }
+    case PH_MAX: {
+      S.smax = red_val;
+      if (!(S.smax > 0.0)) {
+        S.status = STN_NOT_CONVERGED;
+        return true;
+      }
+      S.phase = PH_SCALE;
+      return false;
+    }
+    case PH_SCALE: {
+      S.r32norm = sqrt(red_val);
+      S.inner = 0;
+      S.parity = 0;
+      if (a.max_iters <= 0) {
+        S.phase = PH_UPDATE;
+        return false;
+      }
+      S.phase = PH_INNER;
+      start_group(a, S, 0, a.max_iters);
+      if (!(a.inner_tol > 0.0)) S.resid = 0;
+      return false;
+    }
+    case PH_INNER: {
+      S.inner++;
+      S.parity ^= 1;
+      S.group_pos++;
+      bool stop = false;
+      if (S.group_pos == S.group) {
+        if (a.inner_tol > 0.0 && sqrt(red_val) <= a.inner_tol * S.r32norm) stop = true;
+        if (S.inner >= a.max_iters) stop = true;
+        if (!stop) start_group(a, S, S.inner, a.max_iters);
+      } else {
+        S.resid = S.group_pos == S.group - 1 ? 1 : 0;
+      }
+      if (!(a.inner_tol > 0.0)) S.resid = 0;
+      if (stop) S.phase = PH_UPDATE;
+      return false;
+    }
+    case PH_UPDATE: {
+      S.sweeps += S.inner;
+      S.outer++;
+      S.phase = PH_RES;
+      S.resid = 1;
+      return false;
+    }
+    default:
+      return true;
+  }
+}
+
+__device__ __forceinline__ int ld_acquire_sys_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Publishes the next pass of slot si (one thread; the slot state for that
+// pass has been written).  Release: state writes before the word exchange.
+__device__ __forceinline__ void publish(const SchedArgs& a, int si) {
+  SchedSlot& S = a.slots[si];
+  const unsigned pass = S.pass + 1;
+  S.pass = pass;
+  S.done = 0;
+  __threadfence();
+  atomicExch(&a.words[si], (unsigned long long)pass << 32);
+}
+
+// Loads problem `pi` into slot `si` (one thread) and publishes its first pass.
+__device__ void admit(const SchedArgs& a, int si, int pi) {
+  SchedSlot& S = a.slots[si];
+  const SchedProblem& P = a.probs[pi];
+  S.problem = pi;
+  S.phase = PH_INIT;
+  S.status = STN_NOT_CONVERGED;
+  S.parity = 0;
+  S.resid = 0;
+  S.rel = INFINITY;
+  S.res = INFINITY;
+  S.nunits = P.nunits;
+  S.claim_free = 0;
+  S.start_clock = clock64();
+  publish(a, si);
+}
+
+// Takes the next queued problem index, or -1.  For serving the host appends
+// entries and then advances *qtail (system-scope release).
+__device__ int pop_queue(const SchedArgs& a) {
+  const int tail = a.serving ? ld_acquire_sys_s32(a.qtail) : a.count;
+  int h = atomicAdd(a.qhead, 0);
+  while (h < tail) {
+    const int got = atomicCAS(a.qhead, h, h + 1);
+    if (got == h) return a.queue[h % a.qcap];
+    h = got;
+  }
+  return -1;
+}
+
+// Tries to start a queued problem in a free slot (one thread).  The slot is
+// claimed first, so a popped problem always has a home.
+__device__ bool try_admit(const SchedArgs& a) {
+  if (*(volatile int*)a.free_slots <= 0) return false;
+  for (int k = 0; k < a.nslots; k++) {
+    if (*(volatile int*)&a.slots[k].claim_free != 1) continue;
+    if (atomicCAS(&a.slots[k].claim_free, 1, 2) != 1) continue;  // 2 = being filled
+    const int pi = pop_queue(a);
+    if (pi < 0) {
+      atomicExch(&a.slots[k].claim_free, 1);
+      return false;
+    }
+    atomicSub(a.free_slots, 1);
+    admit(a, k, pi);
+    return true;
+  }
+  return false;
+}
+
+// The CTA that completed the last unit of slot si's pass: reduce the unit
+// partials in order, advance the state machine, publish the next pass or
+// finish the problem and start the next queued one in this slot.
+template <int R, bool HAS_C0>
+__device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, const SchedSlot& S0,
+                         double* red) {
+  const bool is_max = S0.phase == PH_MAX;
+  const double v = reduce_parts(P.partials, S0.nunits, is_max, red);
+  if (tid_flat() == 0) {
+    SchedSlot& S = a.slots[si];
+    const bool finished = advance(a, S, P, v);
+    if (finished) {
+      SchedResult r;
+      r.iters = a.refined ? S.sweeps : S.iters;
+      r.outer = S.outer;
+      r.rel_res = S.rel;
+      r.res_norm = S.res;
+      r.rhs_norm = S.bnorm;
+      r.clocks = clock64() - S.start_clock;
+      r.status = S.status;
+      r.pad = 0;
+      a.results[S.problem] = r;
+      __threadfence_system();
+      atomicExch(&a.done_flags[S.problem], 1);
+      __threadfence_system();
+      atomicAdd(a.finished, 1);
+      S.phase = PH_IDLE;
+      S.nunits = 0;
+      const int nxt = pop_queue(a);
+      if (nxt >= 0) {
+        admit(a, si, nxt);
+      } else {
+        publish(a, si);  // an empty pass: nothing to claim
+        S.claim_free = 1;
+        __threadfence();
+        atomicAdd(a.free_slots, 1);
+      }
+    } else {
+      publish(a, si);
+    }
+  }
+  __syncthreads();
+}
+
+template <int R, bool HAS_C0>
+__global__ void __launch_bounds__(BT) sched_kernel(SchedArgs a) {
+  __shared__ SmemPlanes sp;
+  __shared__ double red[BT / 32];
+  __shared__ SchedSlot s_state;
+  __shared__ SchedProblem s_prob;
+  __shared__ int s_slot, s_unit, s_last, s_flag;
+  const int nslots = a.nslots;
+  int cursor = (int)(blockIdx.x % (unsigned)(nslots > 0 ? nslots : 1));
+  long long idle_since = -1;
+  for (;;) {
+    if (tid_flat() == 0) {
+      s_slot = -1;
+      if (*(volatile int*)a.error != 0) {
+        s_slot = -3;
+      } else {
+        for (int probe = 0; probe < nslots; probe++) {
+          const int si = (cursor + probe) % nslots;
+          const unsigned long long w0 = *(volatile unsigned long long*)&a.words[si];
+          const int nu = *(volatile int*)&a.slots[si].nunits;
+          if ((int)(w0 & 0xffffffffu) >= nu) continue;
+          const unsigned long long w = atomicAdd(&a.words[si], 1ull);
+          __threadfence();
+          const unsigned pass = (unsigned)(w >> 32);
+          const int q = (int)(w & 0xffffffffu);
+          const SchedSlot S = a.slots[si];
+          if (S.pass == pass && q < S.nunits && S.nunits > 0) {
+            s_state = S;
+            s_prob = a.probs[S.problem];
+            s_slot = si;
+            s_unit = q;
+            cursor = si;
+            break;
+          }
+        }
+        if (s_slot == -1) {
+          if (try_admit(a)) s_slot = -2;
+          else if (!a.serving && *(volatile int*)a.finished >= a.count) s_slot = -3;
+        }
+      }
+    }
+    __syncthreads();
+    const int si = s_slot;
+    if (si == -3) break;
+    if (si == -2) continue;
+    if (si < 0) {
+      // no work anywhere: bounded back-off, then give up
+      if (tid_flat() == 0) {
+        const long long now = clock64();
+        if (idle_since < 0) idle_since = now;
+        s_flag = (now - idle_since) > a.idle_cycles ? 1 : 0;
+        if (!s_flag) __nanosleep(1000);
+      }
+      __syncthreads();
+      if (s_flag) {
+        if (tid_flat() == 0 && !a.serving) atomicCAS(a.error, 0, STN_ETIMEOUT);
+        break;
+      }
+      continue;
+    }
+    idle_since = -1;
+    __threadfence();  // acquire for every thread: the previous pass's grids
+    const SchedSlot S = s_state;
+    const SchedProblem P = s_prob;
+    const double part = run_unit<R, HAS_C0>(a, S, P, s_unit, sp, red);
+    __syncthreads();  // every thread's writes of this unit precede the release
+    if (tid_flat() == 0) {
+      P.partials[s_unit] = part;
+      __threadfence();
+      const int prev = atomicAdd(&a.slots[si].done, 1);
+      s_last = prev == S.nunits - 1 ? 1 : 0;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();  // acquire for every thread: the other units' partials
+      epilogue<R, HAS_C0>(a, si, P, S, red);
+    }
+  }
+}
+
+}  // namespace
+
+int sched_launch(const SchedArgs& a, int radius, bool has_c0, int ctas, cudaStream_t s) {
+#define STN_SCHED(R_, C0_) sched_kernel<R_, C0_><<<ctas, dim3(TX, TY), 0, s>>>(a)
+  if (radius == 1) {
+    if (has_c0) STN_SCHED(1, true);
+    else STN_SCHED(1, false);
+  } else {
+    if (has_c0) STN_SCHED(2, true);
+    else STN_SCHED(2, false);
+  }
+#undef STN_SCHED
+  STN_CUDA_TRY(cudaGetLastError());
+  return STN_OK;
+}
+
+int sched_ctas(int radius, bool has_c0) {
+  int per_sm = 0;
+  cudaError_t e;
+  if (radius == 1)
+    e = has_c0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sched_kernel<1, true>, BT, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sched_kernel<1, false>, BT, 0);
+  else
+    e = has_c0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sched_kernel<2, true>, BT, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sched_kernel<2, false>, BT, 0);
+  if (e != cudaSuccess || per_sm < 1) return -1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+i64 sched_units(i64 nx, i64 ny, i64 nz) { return make_geo((int)nx, (int)ny, (int)nz).n; }
+
+}  // namespace stn

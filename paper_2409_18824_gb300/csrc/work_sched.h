@@ -1,0 +1,82 @@
+// Shared declarations of the persistent scheduler (sched.cu) and its hosts
+// (batched solves in batched.cu, the serving loop in server.cpp).
+#pragma once
+
+#include "internal.h"
+
+namespace stn {
+
+// One problem: u = S u + b on a padded grid, with its scratch.
+struct SchedProblem {
+  int nx, ny, nz, nunits;
+  double* u;         // iterate (in/out)
+  const double* b;   // source term (may be null)
+  double* t;         // double scratch grid; its halo must equal u's halo
+  float* e;          // refined: correction grids (zeroed, halo included)
+  float* e2;
+  float* r32;
+  double* partials;  // one per work unit
+};
+
+// Scheduler state of one slot (one problem in flight).
+struct SchedSlot {
+  int problem;          // index into the problem / result arrays
+  int phase;            // pass kind (sched.cu Phase)
+  int status;
+  int parity;           // which grid of a ping-pong pair holds the iterate
+  int resid;            // the current sweep also reduces its residual
+  int nunits;           // units of the current pass (0 when idle)
+  int done;             // units completed in the current pass
+  int claim_free;       // 1 when the slot holds no problem
+  unsigned pass;        // id of the published pass (high word of the claim word)
+  int pad;
+  long long group, group_pos;
+  long long iters, outer, sweeps, inner;
+  long long start_clock;
+  double bnorm, scale, res, rel, smax, r32norm;
+};
+
+struct SchedResult {
+  long long iters;
+  long long outer;
+  double rel_res;
+  double res_norm;
+  double rhs_norm;
+  long long clocks;  // device clock cycles from admission to completion
+  int status;
+  int pad;
+};
+
+struct SchedArgs {
+  SchedProblem* probs;
+  SchedSlot* slots;
+  unsigned long long* words;  // per slot: (pass << 32) | next unit
+  int nslots;
+  int count;                  // problems in total (batch) / queue capacity bound (serving)
+  const int* queue;           // problem indices in admission order (ring of qcap)
+  int qcap;
+  int* qhead;                 // device counter of taken queue entries
+  const int* qtail;           // serving: host-advanced count of queued entries
+  int serving;
+  SchedResult* results;       // per problem
+  int* done_flags;            // per problem: 1 once its result is written
+  int* finished;              // problems finished
+  int* free_slots;            // slots holding no problem
+  int* error;                 // first error (STN_ETIMEOUT, ...), 0 if none
+  double coeffs[3];
+  double tol;
+  long long max_iters;        // plain: sweeps; refined: float sweeps per outer step
+  long long check_every;
+  double inner_tol;
+  long long max_outer;
+  int refined;
+  long long idle_cycles;      // give up after this many clock cycles without work
+};
+
+int sched_launch(const SchedArgs& a, int radius, bool has_c0, int ctas, cudaStream_t s);
+// CTAs of one full wave of the scheduler kernel (-1 on error).
+int sched_ctas(int radius, bool has_c0);
+// Work units of a problem's pass.
+i64 sched_units(i64 nx, i64 ny, i64 nz);
+
+}  // namespace stn

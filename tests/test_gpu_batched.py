@@ -14,6 +14,15 @@ import stencil_inputs as si
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(params=[0, 1], ids=["scheduler", "clusters"])
+def engine(request, lib):
+    """Both batched engines: the dynamic work-unit scheduler and one cluster
+    per problem; they must give the same bits."""
+    lib.stencil_tune_set("batch_engine", request.param)
+    yield request.param
+    lib.stencil_tune_set("batch_engine", 0)
+
 L7 = si.LAPLACE7
 NORM_RTOL = 1e-12
 
@@ -41,7 +50,7 @@ def make_batch(sizes, seed0=5):
     return rhs
 
 
-def test_batched_f64_matches_oracle_and_is_composition_independent(lib, cuda):
+def test_batched_f64_matches_oracle_and_is_composition_independent(lib, cuda, engine):
     rhs = make_batch(SIZES)
     tol, K, maxit = 1e-8, 10, 40000
     d_u = [to_dev(np.zeros_like(b)) for b in rhs]
@@ -66,7 +75,7 @@ def test_batched_f64_matches_oracle_and_is_composition_independent(lib, cuda):
             assert infos2[j]["iters"] == infos[i]["iters"] and infos2[j]["rel_res"] == infos[i]["rel_res"]
 
 
-def test_batched_not_converged_and_empty(lib, cuda):
+def test_batched_not_converged_and_empty(lib, cuda, engine):
     rhs = make_batch(SIZES[:3])
     d_u = [to_dev(np.zeros_like(b)) for b in rhs]
     rc, infos = lib.jacobi_solve_batched_f64(d_u, [to_dev(b) for b in rhs], L7, 1, 1e-14, 25, 10)
@@ -84,7 +93,7 @@ def test_batched_rejects_host_grids(lib, cuda):
 
 
 @pytest.mark.parametrize("batched", [False, True])
-def test_refined_fixed_inner_matches_oracle(lib, cuda, batched):
+def test_refined_fixed_inner_matches_oracle(lib, cuda, engine, batched):
     """With a fixed number of float sweeps per outer step the refinement is a
     fixed sequence of roundings: bitwise equal to the oracle's refinement."""
     sizes = [(20, 14, 9), (9, 9, 9), (31, 7, 12)]
@@ -112,7 +121,7 @@ def test_refined_fixed_inner_matches_oracle(lib, cuda, batched):
         assert oracle.residual_norm(got, L7, 1, rhs[i]) / oracle.interior_norm(rhs[i], 1) <= tol
 
 
-def test_refined_adaptive_inner_reaches_tolerance(lib, cuda):
+def test_refined_adaptive_inner_reaches_tolerance(lib, cuda, engine):
     sizes = [(40, 30, 20), (16, 16, 16), (12, 50, 7)]
     rhs = make_batch(sizes, seed0=21)
     tol = 1e-10
