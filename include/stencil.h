@@ -71,7 +71,8 @@ enum {
   STN_ENOMEM = -2,        /* device or host allocation failed */
   STN_ECUDA = -3,         /* a CUDA runtime call failed (message in stencil_last_error) */
   STN_ETIMEOUT = -4,      /* a device-side wait reached its spin limit */
-  STN_EBUSY = -5          /* admission refused (server over its memory budget) */
+  STN_EBUSY = -5,         /* admission refused (server over its memory budget) */
+  STN_PENDING = 2         /* server: request not finished yet */
 };
 
 /* Result of a solve (host struct filled by the solvers). */
@@ -263,6 +264,72 @@ int jacobi_solve_batched_refined(const stn_problem* probs, int64_t count, const 
                                  int radius, double tol, int64_t inner_sweeps, double inner_tol,
                                  int64_t check_every, int64_t max_outer, stn_solve_info* infos,
                                  void* stream);
+
+/*
+ * Serving loop (continuous batching; not in the paper).  A server owns a
+ * device-memory budget and a persistent scheduler kernel.  Requests (one
+ * Poisson/Jacobi solve u = S u + rhs each, extents per request) are submitted
+ * at any time from any thread; the server admits them in arrival order as
+ * their grids fit in the budget, runs every admitted request concurrently on
+ * the GPU (requests admitted while others run join the running kernel), and
+ * hands back the solution.  A result depends only on its request: it is the
+ * same alone and in any mix of concurrent requests.
+ */
+typedef struct stn_server stn_server;
+
+typedef struct stn_server_opts {
+  size_t hbm_budget;       /* bytes of device memory for request grids and scratch */
+  int radius;              /* 1 or 2 */
+  double coeffs[3];        /* {c0, c1, c2}; entries beyond radius ignored */
+  double tol;              /* stop at ||rho|| <= tol*||rhs|| (as jacobi_solve_f64) */
+  int refined;             /* 1: float sweeps + double refinement; 0: double Jacobi */
+  int64_t max_iters;       /* plain: sweep limit */
+  int64_t inner_sweeps;    /* refined: float sweep limit per outer step */
+  double inner_tol;        /* refined: inner stop (0 = run inner_sweeps) */
+  int64_t check_every;     /* sweeps per convergence check */
+  int64_t max_outer;       /* refined: outer step limit */
+  int max_inflight;        /* requests on the GPU at once */
+  int queue_capacity;      /* admitted-but-unfinished requests the device queue holds */
+} stn_server_opts;
+
+typedef struct stn_request {
+  int64_t nx, ny, nz;      /* interior extents */
+  const double* rhs;       /* HOST padded grid (copied at submit) */
+  const double* u0;        /* HOST padded initial guess and halo, or NULL for zeros */
+} stn_request;
+
+typedef struct stn_result {
+  stn_solve_info info;
+  double latency_s;        /* submit -> result ready */
+  double queue_s;          /* submit -> admitted to the GPU */
+  int rc;                  /* STN_OK, STN_NOT_CONVERGED or an error */
+} stn_result;
+
+typedef struct stn_server_stats_t {
+  int64_t submitted, completed, pending, running;
+  size_t bytes_in_use;
+  int status;              /* STN_OK, or the error that stopped the server */
+} stn_server_stats_t;
+
+/* Creates a server on the current device (NULL on error; see
+ * stencil_last_error). */
+stn_server* stn_server_create(const stn_server_opts* opts);
+/* Submits a request; *ticket identifies it.  STN_EBUSY if it can never fit in
+ * the budget or the server is stopping. */
+int stn_submit(stn_server* s, const stn_request* req, uint64_t* ticket);
+/* STN_PENDING while the request runs; else fills *res (may be NULL) and returns
+ * STN_OK (the solve's own status is in res->info.status / res->rc). */
+int stn_poll(stn_server* s, uint64_t ticket, stn_result* res);
+/* Waits up to timeout_s seconds (negative: forever); STN_ETIMEOUT if it did not
+ * finish in time. */
+int stn_wait(stn_server* s, uint64_t ticket, double timeout_s, stn_result* res);
+/* Copies a finished request's solution (padded grid) to HOST memory u_out. */
+int stn_result_copy(stn_server* s, uint64_t ticket, double* u_out);
+/* Forgets a finished request (frees its host copy). */
+int stn_release(stn_server* s, uint64_t ticket);
+int stn_server_stats(stn_server* s, stn_server_stats_t* stats);
+/* Stops accepting requests, finishes the ones submitted, frees everything. */
+void stn_server_destroy(stn_server* s);
 
 /*
  * Variable-coefficient operator, radius R in {1, 2}, weights w[0..R] (HOST;

@@ -28,6 +28,7 @@ STN_ENOMEM = -2
 STN_ECUDA = -3
 STN_ETIMEOUT = -4
 STN_EBUSY = -5
+STN_PENDING = 2
 
 
 class StencilError(RuntimeError):
@@ -47,6 +48,33 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("radius", ctypes.c_int), ("coeffs", ctypes.c_double * 3),
+                ("tol", ctypes.c_double), ("refined", ctypes.c_int), ("max_iters", ctypes.c_int64),
+                ("inner_sweeps", ctypes.c_int64), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int64),
+                ("max_outer", ctypes.c_int64), ("max_inflight", ctypes.c_int), ("queue_capacity", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("rhs", ctypes.c_void_p), ("u0", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("info", SolveInfo), ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("rc", ctypes.c_int)]
+
+    def as_dict(self):
+        d = self.info.as_dict()
+        d.update(latency_s=self.latency_s, queue_s=self.queue_s, rc=self.rc)
+        return d
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t), ("status", ctypes.c_int)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -82,6 +110,14 @@ SIGNATURES = {
                                         _vp]),
     "jacobi_solve_batched_refined": (_int, [ctypes.POINTER(Problem), _i64, _dp, _int, _dbl, _i64, _dbl, _i64,
                                             _i64, _info_p, _vp]),
+    "stn_server_create": (_vp, [ctypes.POINTER(ServerOpts)]),
+    "stn_submit": (_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "stn_poll": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "stn_wait": (_int, [_vp, ctypes.c_uint64, _dbl, ctypes.POINTER(Result)]),
+    "stn_result_copy": (_int, [_vp, ctypes.c_uint64, _vp]),
+    "stn_release": (_int, [_vp, ctypes.c_uint64]),
+    "stn_server_stats": (_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "stn_server_destroy": (None, [_vp]),
     "varcoef_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
     "varcoef_sweep_f64": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "varcoef_sweep_f32": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
@@ -330,6 +366,70 @@ def stencil_tune_get(knob: str) -> int:
     v = _i64(0)
     _check(_lib.stencil_tune_get(knob.encode(), ctypes.byref(v)))
     return v.value
+
+
+class Server:
+    """The serving loop of the C ABI (stn_server_*): submit host right-hand
+    sides, get tickets, wait for solutions."""
+
+    def __init__(self, hbm_budget, coeffs=(0.0, 1.0 / 6.0), radius=1, tol=1e-8, refined=True, max_iters=10 ** 7,
+                 inner_sweeps=200000, inner_tol=1e-2, check_every=50, max_outer=40, max_inflight=64,
+                 queue_capacity=4096):
+        o = ServerOpts()
+        o.hbm_budget = int(hbm_budget)
+        o.radius = radius
+        for i in range(3):
+            o.coeffs[i] = float(coeffs[i]) if i < len(coeffs) else 0.0
+        o.tol, o.refined, o.max_iters = tol, int(refined), max_iters
+        o.inner_sweeps, o.inner_tol, o.check_every, o.max_outer = inner_sweeps, inner_tol, check_every, max_outer
+        o.max_inflight, o.queue_capacity = max_inflight, queue_capacity
+        h = _lib.stn_server_create(ctypes.byref(o))
+        if not h:
+            raise StencilError(STN_EINVAL, last_error())
+        self._h = h
+        self.radius = radius
+
+    def submit(self, rhs: np.ndarray, u0: np.ndarray | None = None) -> int:
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        nz, ny, nx = (s - 2 * self.radius for s in rhs.shape)
+        req = Request(nx, ny, nz, rhs.ctypes.data, None if u0 is None else np.ascontiguousarray(u0).ctypes.data)
+        t = ctypes.c_uint64(0)
+        _check(_lib.stn_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        r = Result()
+        rc = _check(_lib.stn_poll(self._h, ticket, ctypes.byref(r)))
+        return None if rc == STN_PENDING else r.as_dict()
+
+    def wait(self, ticket, timeout_s=-1.0):
+        r = Result()
+        _check(_lib.stn_wait(self._h, ticket, timeout_s, ctypes.byref(r)))
+        return r.as_dict()
+
+    def result(self, ticket, shape):
+        out = np.empty(shape, dtype=np.float64)
+        _check(_lib.stn_result_copy(self._h, ticket, out.ctypes.data))
+        return out
+
+    def release(self, ticket):
+        return _check(_lib.stn_release(self._h, ticket))
+
+    def stats(self):
+        st = ServerStats()
+        _check(_lib.stn_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.stn_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def release_workspace():

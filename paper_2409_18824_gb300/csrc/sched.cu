@@ -67,6 +67,20 @@ __host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
 
 __device__ __forceinline__ int tid_flat() { return threadIdx.x + TX * threadIdx.y; }
 
+// Reads a state struct through volatile 8-byte loads (never a stale L1 line):
+// slot and problem records are written by other SMs and, when serving, by
+// the host.
+template <typename S>
+__device__ __forceinline__ S vload(const S* p) {
+  static_assert(sizeof(S) % 8 == 0, "state records are whole 8-byte words");
+  S out;
+  const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(p);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
+#pragma unroll 4
+  for (int i = 0; i < (int)(sizeof(S) / 8); i++) dst[i] = src[i];
+  return out;
+}
+
 __device__ __forceinline__ double bmax(double v, double* red) {
   const int lane = tid_flat() & 31, warp = tid_flat() >> 5;
 #pragma unroll
@@ -87,7 +101,10 @@ __device__ __forceinline__ double bmax(double v, double* red) {
 // on n only); result valid in thread 0.
 __device__ __forceinline__ double reduce_parts(const double* p, int n, bool is_max, double* red) {
   double v = 0.0;
-  for (int i = tid_flat(); i < n; i += BT) v = is_max ? fmax(v, p[i]) : v + p[i];
+  for (int i = tid_flat(); i < n; i += BT) {
+    const double x = __ldcg(p + i);
+    v = is_max ? fmax(v, x) : v + x;
+  }
   if (is_max) return bmax(v, red);
   const double s = block_sum_fixed<BT>(v, red);
   __syncthreads();
@@ -337,7 +354,7 @@ __device__ __forceinline__ int ld_acquire_sys_s32(const int* p) {
 // pass has been written).  Release: state writes before the word exchange.
 __device__ __forceinline__ void publish(const SchedArgs& a, int si) {
   SchedSlot& S = a.slots[si];
-  const unsigned pass = S.pass + 1;
+  const unsigned pass = *(volatile unsigned*)&S.pass + 1;
   S.pass = pass;
   S.done = 0;
   __threadfence();
@@ -347,7 +364,7 @@ __device__ __forceinline__ void publish(const SchedArgs& a, int si) {
 // Loads problem `pi` into slot `si` (one thread) and publishes its first pass.
 __device__ void admit(const SchedArgs& a, int si, int pi) {
   SchedSlot& S = a.slots[si];
-  const SchedProblem& P = a.probs[pi];
+  const SchedProblem P = vload(&a.probs[pi]);
   S.problem = pi;
   S.phase = PH_INIT;
   S.status = STN_NOT_CONVERGED;
@@ -368,7 +385,7 @@ __device__ int pop_queue(const SchedArgs& a) {
   int h = atomicAdd(a.qhead, 0);
   while (h < tail) {
     const int got = atomicCAS(a.qhead, h, h + 1);
-    if (got == h) return a.queue[h % a.qcap];
+    if (got == h) return *(const volatile int*)&a.queue[h % a.qcap];
     h = got;
   }
   return -1;
@@ -402,8 +419,9 @@ __device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, cons
   const bool is_max = S0.phase == PH_MAX;
   const double v = reduce_parts(P.partials, S0.nunits, is_max, red);
   if (tid_flat() == 0) {
-    SchedSlot& S = a.slots[si];
+    SchedSlot S = vload(&a.slots[si]);
     const bool finished = advance(a, S, P, v);
+    a.slots[si] = S;  // written back before anything is published
     if (finished) {
       SchedResult r;
       r.iters = a.refined ? S.sweeps : S.iters;
@@ -419,15 +437,16 @@ __device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, cons
       atomicExch(&a.done_flags[S.problem], 1);
       __threadfence_system();
       atomicAdd(a.finished, 1);
-      S.phase = PH_IDLE;
-      S.nunits = 0;
+      SchedSlot& G = a.slots[si];
+      G.phase = PH_IDLE;
+      G.nunits = 0;
       const int nxt = pop_queue(a);
       if (nxt >= 0) {
         admit(a, si, nxt);
       } else {
         publish(a, si);  // an empty pass: nothing to claim
-        S.claim_free = 1;
         __threadfence();
+        atomicExch(&G.claim_free, 1);
         atomicAdd(a.free_slots, 1);
       }
     } else {
@@ -462,10 +481,10 @@ __global__ void __launch_bounds__(BT) sched_kernel(SchedArgs a) {
           __threadfence();
           const unsigned pass = (unsigned)(w >> 32);
           const int q = (int)(w & 0xffffffffu);
-          const SchedSlot S = a.slots[si];
+          const SchedSlot S = vload(&a.slots[si]);
           if (S.pass == pass && q < S.nunits && S.nunits > 0) {
             s_state = S;
-            s_prob = a.probs[S.problem];
+            s_prob = vload(&a.probs[S.problem]);
             s_slot = si;
             s_unit = q;
             cursor = si;

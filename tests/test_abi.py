@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "stencil.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|const char\s*\*)\s*\**\s*(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char|stn_server)\s*\**\s*(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -125,3 +125,19 @@ def test_tuning_knobs(lib):
         lib.stencil_tune_set(knob, good)
         assert lib.stencil_tune_get(knob) == good
         lib.stencil_tune_set(knob, before)
+
+
+def test_server_rejects_bad_options(lib):
+    o = lib.ServerOpts()
+    o.hbm_budget = 1 << 20
+    o.radius = 3  # invalid
+    o.tol = 1e-8
+    o.check_every = 10
+    o.max_inflight = 4
+    o.queue_capacity = 16
+    assert not lib.lib().stn_server_create(ctypes.byref(o))
+    assert "out of range" in lib.last_error()
+    o.radius = 1
+    o.hbm_budget = 0
+    assert not lib.lib().stn_server_create(ctypes.byref(o))
+    assert not lib.lib().stn_server_create(None)

@@ -1,0 +1,122 @@
+"""Serving loop (stn_server_*): requests arrive while others run, are admitted
+against a device-memory budget and run concurrently in the persistent
+scheduler.  Each result must be the same bits alone and in the mix (compared
+with the batched solver on that request alone) and meet its tolerance on the
+CPU oracle's independent double residual."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import stencil_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+L7 = si.LAPLACE7
+
+
+def bitwise(a, b):
+    return a.shape == b.shape and np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def requests(n, seed=31, lo=6, hi=24):
+    sizes = si.log_uniform_sizes(n, lo, hi, seed)
+    return [si.normal_interior(int(x), int(y), int(z), 1, seed=seed * 1000 + i) for i, (x, y, z) in enumerate(sizes)]
+
+
+def alone(lib, rhs, refined, tol):
+    import torch
+    u = torch.zeros(rhs.shape, dtype=torch.float64, device="cuda")
+    b = torch.from_numpy(rhs).cuda()
+    if refined:
+        rc, infos = lib.jacobi_solve_batched_refined([u], [b], L7, 1, tol, 200000, 1e-2, 50, 40)
+    else:
+        rc, infos = lib.jacobi_solve_batched_f64([u], [b], L7, 1, tol, 10 ** 6, 50)
+    torch.cuda.synchronize()
+    return u.cpu().numpy(), infos[0]
+
+
+@pytest.mark.parametrize("refined", [True, False])
+def test_serving_results_same_alone_and_in_the_mix(lib, cuda, refined):
+    tol = 1e-8
+    rhss = requests(16)
+    got = {}
+    with lib.Server(hbm_budget=1 << 30, tol=tol, refined=refined, check_every=50, max_inflight=8) as srv:
+        tickets = []
+        for i, b in enumerate(rhss):  # arrivals spread over the run
+            tickets.append(srv.submit(b))
+            time.sleep(0.002 * (i % 3))
+        for i, t in enumerate(tickets):
+            res = srv.wait(t, 120.0)
+            assert res["rc"] == 0 and res["status"] == 0, res
+            assert res["latency_s"] >= res["queue_s"] >= 0
+            got[i] = (srv.result(t, rhss[i].shape), res)
+            srv.release(t)
+        st = srv.stats()
+        assert st["completed"] == len(rhss) and st["pending"] == 0 and st["running"] == 0
+        assert st["bytes_in_use"] == 0
+    for i, b in enumerate(rhss):
+        u, res = got[i]
+        ref, info = alone(lib, b, refined, tol)
+        assert bitwise(u, ref), i
+        assert res["iters"] == info["iters"] and res["outer"] == info["outer"]
+        assert oracle.residual_norm(u, L7, 1, b) / oracle.interior_norm(b, 1) <= tol
+
+
+def test_serving_admission_respects_budget(lib, cuda):
+    rhss = requests(10, seed=41, lo=20, hi=28)
+    per = 3 * 8 * max(b.size for b in rhss) + 3 * 4 * max(b.size for b in rhss) + (1 << 16)
+    budget = int(per * 1.5)  # room for the largest request plus a small one
+    with lib.Server(hbm_budget=budget, tol=1e-8, refined=True, max_inflight=8) as srv:
+        tickets = [srv.submit(b) for b in rhss]
+        peak_pending, peak_bytes = 0, 0
+        done = 0
+        deadline = time.time() + 120
+        while done < len(tickets) and time.time() < deadline:
+            st = srv.stats()
+            peak_pending = max(peak_pending, st["pending"])
+            peak_bytes = max(peak_bytes, st["bytes_in_use"])
+            done = st["completed"]
+            time.sleep(0.001)
+        assert done == len(tickets)
+        assert peak_bytes <= budget  # never over the budget
+        assert peak_pending >= len(tickets) - 3  # requests waited for memory
+        for t, b in zip(tickets, rhss):
+            res = srv.wait(t, 10.0)
+            assert res["status"] == 0
+            u = srv.result(t, b.shape)
+            assert oracle.residual_norm(u, L7, 1, b) / oracle.interior_norm(b, 1) <= 1e-8
+
+
+def test_serving_rejects_oversize_and_concurrent_submitters(lib, cuda):
+    big = np.zeros(si.padded_shape(64, 64, 64, 1))
+    with lib.Server(hbm_budget=1 << 20, tol=1e-6, refined=True) as srv:
+        with pytest.raises(lib.StencilError) as ei:
+            srv.submit(big)
+        assert ei.value.code == lib.STN_EBUSY
+    # several host threads submitting at once
+    rhss = requests(12, seed=51, lo=6, hi=14)
+    out = [None] * len(rhss)
+    with lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=False, max_inflight=4) as srv:
+        def worker(k):
+            for i in range(k, len(rhss), 3):
+                t = srv.submit(rhss[i])
+                out[i] = srv.wait(t, 60.0)
+        th = [threading.Thread(target=worker, args=(k,)) for k in range(3)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+    assert all(r is not None and r["status"] == 0 for r in out)
+
+
+def test_serving_shutdown_with_requests_in_flight(lib, cuda):
+    rhss = requests(6, seed=61, lo=10, hi=20)
+    srv = lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=True, max_inflight=2)
+    for b in rhss:
+        srv.submit(b)
+    t0 = time.time()
+    srv.close()  # finishes the submitted requests, then frees everything
+    assert time.time() - t0 < 120
