@@ -68,6 +68,15 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes per lattice update of the default kernels, from one ncu capture
+# each (dram__bytes_read.sum + dram__bytes_write.sum of a 320^3 launch divided
+# by its 32.8 M updates; summaries under profiles/).  Set to None whenever the
+# kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_LUP = {
+    ("f64", 0): 498.2e6 / 320 ** 3,   # plane kernel (star_kernel<double,1>)
+    ("f32", -1): 226.9e6 / 320 ** 3,  # column kernel (star_col_kernel<float,1>)
+}
+
 # FP64 issue rate of this GPU measured with a throughput probe: 2 double
 # fused-multiply-add instructions per clock per SM (every double add and
 # multiply of the sweep is issued as one), 152 SMs.
@@ -254,6 +263,9 @@ def run_cuda(args, wl):
     clocks = clk.summary()
     lups_kernel = float(nx) * ny * nz
     bytes_alg = 2.0 * esize * lups_kernel           # read u, write out: compulsory traffic
+    tkey = (wl["dtype"], 0 if (f64 and args.variant in (-1, 0)) else (-1 if args.variant == -1 else args.variant))
+    tpl = TRAFFIC_BYTES_PER_LUP.get(tkey)
+    traffic = tpl * lups_kernel if (tpl is not None and args.temporal in (0, 1)) else None
     hbm_gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
     hbm_peak = float(peaks["hbm_gbs"])
     if f64:
@@ -263,13 +275,14 @@ def run_cuda(args, wl):
         fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_clock * 1e6 / 1e12  # Tops/s
         achieved = ops / (kern_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": None,
+                    "frac": achieved / fp64_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                     "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
                     "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
                     "hbm_peak_kind": peak_kind, "kernel_ms": kern_ms, "kernel_ms_in_step": launch_ms_in_step}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                    "frac": hbm_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                    "peak_kind": peak_kind,
                     "kernel_ms": kern_ms, "kernel_ms_in_step": launch_ms_in_step}
 
     out = {
@@ -395,6 +408,7 @@ def run_batched(args):
                 "d2h_bytes_per_step": total * 8},
         "gpu_launches": args.steps * 1,
         "aggregate_glups": lups / (ms / args.steps * 1e-3) / 1e9,
+        "scheduler_counters": stn.stencil_sched_stats(),
         "converged": conv,
         "sweeps_max": int(iters.max()), "sweeps_median": float(np.median(iters)),
         "clocks": clk.summary(),
@@ -403,6 +417,77 @@ def run_batched(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------- serving -----
+def serve_requests(count, seed_sizes=6, seed_rhs=7):
+    """Per-axis sizes log-uniform in [32, 256] (PCG64 seed 6); right-hand sides
+    N(0,1), request i from PCG64 seed 7 * 1000003 + i; zero halo and guess."""
+    sizes = si.log_uniform_sizes(count, 32, 256, seed_sizes)
+    return [tuple(int(v) for v in s) for s in sizes], [seed_rhs * 1000003 + i for i in range(count)]
+
+
+def run_serving(args):
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    sizes, seeds = serve_requests(args.requests)
+    rhss = [si.normal_interior(nx, ny, nz, 1, seed=sd) for (nx, ny, nz), sd in zip(sizes, seeds)]
+    budget = 40 << 30
+    refined = not args.plain
+
+    def run_trace(arrivals):
+        """Submits request i at arrivals[i] seconds; returns (makespan, latencies)."""
+        with stn.Server(hbm_budget=budget, tol=1e-8, refined=refined, inner_sweeps=200000, inner_tol=1e-2,
+                        check_every=50, max_outer=40, max_inflight=64) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for i, at in enumerate(arrivals):
+                d = at - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(rhss[i]))
+            lat, status = [], []
+            for t in tickets:
+                r = srv.wait(t, 3600.0)
+                lat.append(r["latency_s"])
+                status.append(r["status"])
+                srv.release(t)
+            return time.perf_counter() - t0, lat, status
+
+    n = len(rhss)
+    # capacity: every request at t = 0
+    with ClockSampler(local) as clk:
+        span, lat, status = run_trace([0.0] * n)
+        capacity = n / span
+        loads = []
+        for frac in args.loads:
+            rate = frac * capacity
+            arr = si.poisson_arrival_times(n, rate, seed=8).tolist()
+            span_l, lat_l, st_l = run_trace(arr)
+            loads.append({"offered_frac": frac, "offered_per_s": rate, "solves_per_s": n / span_l,
+                          "p50_s": float(np.percentile(lat_l, 50)), "p99_s": float(np.percentile(lat_l, 99)),
+                          "converged": int(sum(1 for x in st_l if x == 0))})
+    out = {
+        "metric": "serving solves/s and p50/p99 latency (Poisson arrivals, sizes log-U[32,256], tol 1e-8)",
+        "value": capacity, "unit": "solves/s", "n_gpus": ws, "steps": 1, "warmup": 0,
+        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 refined" if refined else "f64", "data": "synthetic",
+        "config": {"workload": f"{n} Poisson solve requests, per-axis sizes log-uniform in [32,256] (seed 6), "
+                               f"rhs N(0,1), tol 1e-8, 40 GiB admission budget, continuous batching",
+                   "requests": n},
+        "saturation": {"solves_per_s": capacity, "p50_s": float(np.percentile(lat, 50)),
+                       "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(1 for x in status if x == 0))},
+        "loads": loads,
+        "e2e": {"value": capacity, "unit": "solves/s",
+                "h2d_bytes_per_step": int(sum(b.nbytes for b in rhss)) * 2,
+                "d2h_bytes_per_step": int(sum(b.nbytes for b in rhss))},
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------ oracle (CPU) --
@@ -461,7 +546,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--requests", type=int, default=48, help="serving workload: requests per trace")
+    ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8, 1.1],
+                    help="serving workload: offered loads as fractions of the measured capacity")
+    ap.add_argument("--plain", action="store_true", help="serving workload: double Jacobi instead of refinement")
     ap.add_argument("--batch", type=int, default=2048, help="problems in the batched workload")
     ap.add_argument("--refined", action="store_true", help="batched workload: FP32 sweeps + FP64 refinement")
     ap.add_argument("--inner-tol", type=float, default=1e-2)
@@ -477,6 +566,13 @@ def main():
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("steps >= 1, warmup >= 0")
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "serving workload: CPU oracle arm only "
+                              "implemented for the sweep workloads"}))
+            return
+        run_serving(args)
+        return
     if args.workload == "batch":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "batched workload: CPU oracle arm only "

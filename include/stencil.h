@@ -101,7 +101,8 @@ int stencil_release_workspace(void);
  *   "star_variant": -1 automatic (default: 1 for float, 0 for double),
  *                   0 shared-memory plane kernel (one point per thread),
  *                   1 register/shuffle column kernel (8 j rows per thread,
- *                   no shared memory).
+ *                   no shared memory), 2 plane kernel taking two k planes
+ *                   per step (more independent work per thread).
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
  *                   (temporal blocking): 0 automatic (currently 1), 1 off,
  *                   2..4 (double radius 2: at most 3).
@@ -112,6 +113,11 @@ int stencil_release_workspace(void);
  * concurrent launches.  Unknown knob or value: STN_EINVAL.
  */
 int stencil_tune_set(const char* knob, int64_t value);
+/* Counters of the last batched/served scheduler launch in this process
+ * (summed over CTAs): cycles claiming, computing units, completing units, in
+ * pass epilogues, idle; units; epilogues; empty claim scans.  Returns the
+ * number of counters written (at most n). */
+int stencil_sched_stats(uint64_t* out, int n);
 int stencil_tune_get(const char* knob, int64_t* value);
 
 /*

@@ -96,6 +96,7 @@ SIGNATURES = {
     "stencil_release_workspace": (_int, []),
     "stencil_tune_set": (_int, [ctypes.c_char_p, _i64]),
     "stencil_tune_get": (_int, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
+    "stencil_sched_stats": (_int, [ctypes.POINTER(ctypes.c_uint64), _int]),
     "stencil_sweep_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_sweep_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
@@ -430,6 +431,15 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+SCHED_STATS = ("cyc_claim", "cyc_unit", "cyc_done", "cyc_epilogue", "cyc_idle", "units", "epilogues", "misses")
+
+
+def stencil_sched_stats() -> dict:
+    buf = (ctypes.c_uint64 * len(SCHED_STATS))()
+    n = _check(_lib.stencil_sched_stats(buf, len(SCHED_STATS)))
+    return {k: int(buf[i]) for i, k in enumerate(SCHED_STATS[:n])}
 
 
 def release_workspace():

@@ -70,8 +70,9 @@ int ensure_grid3(Workspace* ws, size_t bytes);
 enum SweepMode { kSweep = 0, kSweepResidual = 1, kResidualOnly = 2 };
 
 // Star-kernel variants: the shared-memory plane kernel (one point per
-// thread) and the shuffle/register column kernel.
-enum StarVariant { kStarScalar = 0, kStarColumn = 1 };
+// thread), the shuffle/register column kernel, and the plane kernel taking
+// two planes per step.
+enum StarVariant { kStarScalar = 0, kStarColumn = 1, kStarPlane2 = 2 };
 ZPlan plan_star(const Grid& g, int variant, size_t esize);
 int star_variant(const Grid& g, size_t esize, const void* a, const void* b, const void* c);
 // Tuning override of the variant choice (-1 = automatic).

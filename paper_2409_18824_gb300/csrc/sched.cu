@@ -22,6 +22,8 @@
 // wait on another CTA's progress except the bounded idle back-off of a CTA
 // that found no work; it gives up after `idle_ns` and records STN_ETIMEOUT
 // (batch) or simply returns (serving, where the host relaunches on demand).
+#include <string.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -55,11 +57,15 @@ __host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
   Geo g;
   g.tiles_x = (nx + TX - 1) / TX;
   g.tiles_y = (ny + TY - 1) / TY;
-  // chunks of at most 64 planes, at least enough units to spread a big
-  // problem over the GPU
-  int kc = (nz + 63) / 64;
-  if (kc < 1) kc = 1;
-  g.klen = (nz + kc - 1) / kc;
+  // k chunks sized from the extents alone (the unit split fixes the order of
+  // every reduction): aim at ~1024 units per pass so a large problem can
+  // occupy the whole GPU, with chunks of 16..64 planes.
+  const long long tiles = (long long)g.tiles_x * g.tiles_y;
+  long long klen = ((long long)nz * tiles + 1023) / 1024;
+  if (klen < 32) klen = 32;
+  if (klen > 64) klen = 64;
+  if (klen > nz) klen = nz;
+  g.klen = (int)klen;
   g.kc = (nz + g.klen - 1) / g.klen;
   g.n = g.tiles_x * g.tiles_y * g.kc;
   return g;
@@ -466,6 +472,8 @@ __global__ void __launch_bounds__(BT) sched_kernel(SchedArgs a) {
   const int nslots = a.nslots;
   int cursor = (int)(blockIdx.x % (unsigned)(nslots > 0 ? nslots : 1));
   long long idle_since = -1;
+  unsigned long long st[SCHED_NSTATS] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long t0 = clock64();
   for (;;) {
     if (tid_flat() == 0) {
       s_slot = -1;
@@ -499,10 +507,16 @@ __global__ void __launch_bounds__(BT) sched_kernel(SchedArgs a) {
     }
     __syncthreads();
     const int si = s_slot;
+    long long t1 = clock64();
     if (si == -3) break;
-    if (si == -2) continue;
+    if (si == -2) {
+      st[SCHED_CYC_CLAIM] += t1 - t0;
+      t0 = t1;
+      continue;
+    }
     if (si < 0) {
       // no work anywhere: bounded back-off, then give up
+      st[SCHED_N_MISS]++;
       if (tid_flat() == 0) {
         const long long now = clock64();
         if (idle_since < 0) idle_since = now;
@@ -510,18 +524,25 @@ __global__ void __launch_bounds__(BT) sched_kernel(SchedArgs a) {
         if (!s_flag) __nanosleep(1000);
       }
       __syncthreads();
+      const long long t2 = clock64();
+      st[SCHED_CYC_IDLE] += t2 - t0;
+      t0 = t2;
       if (s_flag) {
         if (tid_flat() == 0 && !a.serving) atomicCAS(a.error, 0, STN_ETIMEOUT);
         break;
       }
       continue;
     }
+    st[SCHED_CYC_CLAIM] += t1 - t0;
     idle_since = -1;
     __threadfence();  // acquire for every thread: the previous pass's grids
     const SchedSlot S = s_state;
     const SchedProblem P = s_prob;
     const double part = run_unit<R, HAS_C0>(a, S, P, s_unit, sp, red);
     __syncthreads();  // every thread's writes of this unit precede the release
+    const long long t2 = clock64();
+    st[SCHED_CYC_UNIT] += t2 - t1;
+    st[SCHED_N_UNITS]++;
     if (tid_flat() == 0) {
       P.partials[s_unit] = part;
       __threadfence();
@@ -530,16 +551,44 @@ __global__ void __launch_bounds__(BT) sched_kernel(SchedArgs a) {
       if (s_last) __threadfence();
     }
     __syncthreads();
+    const long long t3 = clock64();
+    st[SCHED_CYC_DONE] += t3 - t2;
     if (s_last) {
       __threadfence();  // acquire for every thread: the other units' partials
       epilogue<R, HAS_C0>(a, si, P, S, red);
+      st[SCHED_N_EPI]++;
+      const long long t4 = clock64();
+      st[SCHED_CYC_EPI] += t4 - t3;
+      t0 = t4;
+    } else {
+      t0 = t3;
     }
   }
+  if (a.stats && tid_flat() == 0)
+    for (int i = 0; i < SCHED_NSTATS; i++) atomicAdd(&a.stats[i], st[i]);
 }
 
 }  // namespace
 
-int sched_launch(const SchedArgs& a, int radius, bool has_c0, int ctas, cudaStream_t s) {
+static unsigned long long* g_stats_dev = nullptr;
+static unsigned long long g_stats_host[SCHED_NSTATS];
+static cudaStream_t g_stats_stream = nullptr;
+
+void sched_last_stats(unsigned long long* out) {
+  if (g_stats_dev && cudaMemcpyAsync(g_stats_host, g_stats_dev, sizeof(g_stats_host), cudaMemcpyDeviceToHost,
+                                     g_stats_stream) == cudaSuccess &&
+      cudaStreamSynchronize(g_stats_stream) == cudaSuccess)
+    memcpy(out, g_stats_host, sizeof(g_stats_host));
+  else
+    memset(out, 0, sizeof(g_stats_host));
+}
+
+int sched_launch(const SchedArgs& a0, int radius, bool has_c0, int ctas, cudaStream_t s) {
+  SchedArgs a = a0;
+  if (!g_stats_dev) STN_CUDA_TRY(cudaMalloc(&g_stats_dev, sizeof(unsigned long long) * SCHED_NSTATS));
+  STN_CUDA_TRY(cudaMemsetAsync(g_stats_dev, 0, sizeof(unsigned long long) * SCHED_NSTATS, s));
+  g_stats_stream = s;
+  a.stats = g_stats_dev;
 #define STN_SCHED(R_, C0_) sched_kernel<R_, C0_><<<ctas, dim3(TX, TY), 0, s>>>(a)
   if (radius == 1) {
     if (has_c0) STN_SCHED(1, true);

@@ -137,6 +137,143 @@ __device__ __forceinline__ void star_tile(const T* u, const T* b, T* out, int nx
   *rsum_io = rsum;
 }
 
+// Two planes per step: the same tile sweep as star_tile, but planes k and
+// k+1 are staged together (two shared planes, one pair of barriers per two
+// planes) and their two independent updates are interleaved, which doubles
+// the independent double operations each thread has in flight.  Same
+// arithmetic, same order per point.
+template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
+__device__ __forceinline__ void star_tile2(const T* u, const T* b, T* out, int nx, int ny, int NX,
+                                           int NY, int tile_x, int tile_y, int k0, int k1,
+                                           const StarCoeffs<T, R>& cf,
+                                           T (*tile)[TY + 2 * R][TX + 2 * R], double* rsum_io) {
+  using A = Arith<T>;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int gi = tile_x * TX + tx + R;
+  const int gj = tile_y * TY + ty + R;
+  const i64 sy = NX, sz = (i64)NX * NY;
+  const bool inx = gi < NX, iny = gj < NY;
+  const bool active = (gi < nx + R) && (gj < ny + R);
+  const bool hx = (tx < R) || (tx >= TX - R);
+  const int hx_i = (tx < R) ? gi - R : gi + R;
+  const int hx_lx = (tx < R) ? tx : tx + 2 * R;
+  const bool hx_ok = hx && hx_i < NX && iny;
+  const bool hy = (ty < R) || (ty >= TY - R);
+  const int hy_j = (ty < R) ? gj - R : gj + R;
+  const int hy_ly = (ty < R) ? ty : ty + 2 * R;
+  const bool hy_ok = hy && hy_j < NY && inx;
+  const T* pc = u + gi + gj * sy;
+  const T* px = u + hx_i + gj * sy;
+  const T* py = u + gi + (i64)hy_j * sy;
+  const bool ld_c = inx && iny;
+  constexpr int Q = 2 * R + 2;  // planes k-R .. k+1+R
+  T q[Q];
+#pragma unroll
+  for (int m = 0; m < Q; m++) {
+    const int kk = k0 - R + m;
+    q[m] = (ld_c && kk <= k1 - 1 + R) ? pc[(i64)kk * sz] : T(0);
+  }
+  T hx0 = hx_ok ? px[(i64)k0 * sz] : T(0), hy0 = hy_ok ? py[(i64)k0 * sz] : T(0);
+  T hx1 = (hx_ok && k0 + 1 < k1) ? px[(i64)(k0 + 1) * sz] : T(0);
+  T hy1 = (hy_ok && k0 + 1 < k1) ? py[(i64)(k0 + 1) * sz] : T(0);
+  double rsum = *rsum_io;
+  for (int k = k0; k < k1; k += 2) {
+    const bool two = k + 1 < k1;
+    // prefetch the next pair: centre planes k+2+R, k+3+R; halo planes k+2, k+3
+    T qn0 = T(0), qn1 = T(0), hxn0 = T(0), hxn1 = T(0), hyn0 = T(0), hyn1 = T(0);
+    if (k + 2 < k1) {
+      if (ld_c) qn0 = pc[(i64)(k + 2 + R) * sz];
+      if (hx_ok) hxn0 = px[(i64)(k + 2) * sz];
+      if (hy_ok) hyn0 = py[(i64)(k + 2) * sz];
+    }
+    if (k + 3 < k1) {
+      if (ld_c) qn1 = pc[(i64)(k + 3 + R) * sz];
+      if (hx_ok) hxn1 = px[(i64)(k + 3) * sz];
+      if (hy_ok) hyn1 = py[(i64)(k + 3) * sz];
+    }
+    __syncthreads();
+    tile[0][ty + R][tx + R] = q[R];
+    tile[1][ty + R][tx + R] = q[R + 1];
+    if (hx) {
+      tile[0][ty + R][hx_lx] = hx0;
+      tile[1][ty + R][hx_lx] = hx1;
+    }
+    if (hy) {
+      tile[0][hy_ly][tx + R] = hy0;
+      tile[1][hy_ly][tx + R] = hy1;
+    }
+    __syncthreads();
+    if (active) {
+      T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+      for (int d = R; d >= 1; d--) {
+        const T sx0 = A::add(tile[0][ty + R][tx + R - d], tile[0][ty + R][tx + R + d]);
+        const T sx1 = A::add(tile[1][ty + R][tx + R - d], tile[1][ty + R][tx + R + d]);
+        const T sy0 = A::add(tile[0][ty + R - d][tx + R], tile[0][ty + R + d][tx + R]);
+        const T sy1 = A::add(tile[1][ty + R - d][tx + R], tile[1][ty + R + d][tx + R]);
+        const T sz0 = A::add(q[R - d], q[R + d]);
+        const T sz1 = A::add(q[R + 1 - d], q[R + 1 + d]);
+        const T s0 = A::add(A::add(sx0, sy0), sz0);
+        const T s1 = A::add(A::add(sx1, sy1), sz1);
+        const T t0 = A::mul(cf.c[d], s0);
+        const T t1 = A::mul(cf.c[d], s1);
+        acc0 = (d == R) ? t0 : A::add(acc0, t0);
+        acc1 = (d == R) ? t1 : A::add(acc1, t1);
+      }
+      if (HAS_C0) {
+        acc0 = A::add(acc0, A::mul(cf.c[0], q[R]));
+        acc1 = A::add(acc1, A::mul(cf.c[0], q[R + 1]));
+      }
+      const i64 o0 = gi + gj * sy + (i64)k * sz;
+      if (HAS_B) {
+        acc0 = A::add(acc0, b[o0]);
+        if (two) acc1 = A::add(acc1, b[o0 + sz]);
+      }
+      if (MODE != kResidualOnly) {
+        out[o0] = acc0;
+        if (two) out[o0 + sz] = acc1;
+      }
+      if (MODE != kSweep) {
+        const double r0 = (double)acc0 - (double)q[R];
+        rsum = __fma_rn(r0, r0, rsum);
+        if (two) {
+          const double r1 = (double)acc1 - (double)q[R + 1];
+          rsum = __fma_rn(r1, r1, rsum);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < Q - 2; m++) q[m] = q[m + 2];
+    q[Q - 2] = qn0;
+    q[Q - 1] = qn1;
+    hx0 = hxn0;
+    hx1 = hxn1;
+    hy0 = hyn0;
+    hy1 = hyn1;
+  }
+  __syncthreads();
+  *rsum_io = rsum;
+}
+
+template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
+__global__ void __launch_bounds__(TX* TY)
+    star2_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
+                 int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
+                 double* __restrict__ partials) {
+  __shared__ T tile[2][TY + 2 * R][TX + 2 * R];
+  __shared__ double red[TX * TY / 32];
+  const int k0 = R + blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, nz + R);
+  double rsum = 0.0;
+  star_tile2<T, R, HAS_B, HAS_C0, MODE>(u, b, out, nx, ny, NX, NY, blockIdx.x, blockIdx.y, k0, k1, cf,
+                                         tile, &rsum);
+  if (MODE != kSweep) {
+    const double t = block_sum_fixed<TX * TY>(rsum, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+      partials[blockIdx.x + gridDim.x * ((i64)blockIdx.y + (i64)gridDim.y * blockIdx.z)] = t;
+  }
+}
+
 template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
 __global__ void __launch_bounds__(TX* TY)
     star_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
@@ -317,13 +454,17 @@ int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* c
   }
 #define STN_SCALAR(M) star_kernel<T, R, HAS_B, HAS_C0, M>
 #define STN_COL(M) star_col_kernel<T, R, HAS_B, HAS_C0, M, SC_TJ, PF>
+#define STN_PLANE2(M) star2_kernel<T, R, HAS_B, HAS_C0, M>
   if (variant == kStarColumn) {
     STN_LAUNCH_MODES(STN_COL, dim3(32, SC_WARPS))
+  } else if (variant == kStarPlane2) {
+    STN_LAUNCH_MODES(STN_PLANE2, dim3(TX, TY))
   } else {
     STN_LAUNCH_MODES(STN_SCALAR, dim3(TX, TY))
   }
 #undef STN_SCALAR
 #undef STN_COL
+#undef STN_PLANE2
 #undef STN_LAUNCH_MODES
   STN_CUDA_TRY(cudaGetLastError());
   return STN_OK;

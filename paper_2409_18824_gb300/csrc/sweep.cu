@@ -8,7 +8,7 @@ namespace stn {
 static int g_star_variant_override = -1;
 
 int tune_set_star_variant(int v) {
-  if (v < -1 || v > 1) return STN_EINVAL;
+  if (v < -1 || v > 2) return STN_EINVAL;
   g_star_variant_override = v;
   return STN_OK;
 }
@@ -34,6 +34,7 @@ ZPlan plan_star(const Grid& g, int variant, size_t esize) {
     p.tiles_x = (int)((g.nx + TX - 1) / TX);
     p.tiles_y = (int)((g.ny + TY - 1) / TY);
     resident = esize == 4 ? 8 : 5;
+    if (variant == kStarPlane2) resident = esize == 4 ? 6 : 4;
   }
   const i64 want = 152 * resident;
   // enough blocks to fill every SM; chunks of >= 4 planes

@@ -71,7 +71,26 @@ struct SchedArgs {
   long long max_outer;
   int refined;
   long long idle_cycles;      // give up after this many clock cycles without work
+  unsigned long long* stats;  // optional SCHED_NSTATS counters (cycles and counts), or null
 };
+
+// Scheduler counters (summed over CTAs): clock cycles spent finding and
+// claiming units, computing units, completing units (publish of the partial
+// and the done count), in pass epilogues, idle; units done; epilogues run;
+// claim attempts that found nothing.
+enum {
+  SCHED_CYC_CLAIM = 0,
+  SCHED_CYC_UNIT = 1,
+  SCHED_CYC_DONE = 2,
+  SCHED_CYC_EPI = 3,
+  SCHED_CYC_IDLE = 4,
+  SCHED_N_UNITS = 5,
+  SCHED_N_EPI = 6,
+  SCHED_N_MISS = 7,
+  SCHED_NSTATS = 8
+};
+// Counters of the last scheduler launch made by this process.
+void sched_last_stats(unsigned long long* out);
 
 int sched_launch(const SchedArgs& a, int radius, bool has_c0, int ctas, cudaStream_t s);
 // CTAs of one full wave of the scheduler kernel (-1 on error).

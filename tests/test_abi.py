@@ -110,7 +110,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 def test_tuning_knobs(lib):
     assert lib.stencil_tune_get("star_variant") == -1
-    for bad in (-2, 2, 99):
+    for bad in (-2, 3, 99):
         with pytest.raises(lib.StencilError):
             lib.stencil_tune_set("star_variant", bad)
     with pytest.raises(lib.StencilError):

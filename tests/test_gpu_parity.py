@@ -109,7 +109,7 @@ def test_sweep_misaligned_grids_use_scalar_path(lib, cuda, dtype):
         assert abs(lib.residual_norm_f64(d_out, L7, r) - nref) <= NORM_RTOL * nref
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
 def test_every_kernel_variant_bitwise(lib, cuda, variant, r, c):
     """The one-point-per-thread kernel and both register-blocked kernels give the
