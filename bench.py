@@ -419,6 +419,93 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+# ----------------------------------------------- variable coefficient (r=2) --
+def run_varcoef(args):
+    """768x768x384 radius-2 variable-coefficient Poisson problem: per-sweep rates at
+    full size (float Jacobi sweep, double residual), and complete solves to a
+    1e-10 relative residual on a 96x96x48 grid of the same construction (FP32
+    sweeps with FP64 refinement vs plain FP64 Jacobi)."""
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    dev = torch.device("cuda", 0)
+    W = si.VARCOEF_W
+    R = 2
+
+    def problem(nx, ny, nz):
+        a = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3)).to(dev)
+        ustar = torch.from_numpy(si.sine_mode(nx, ny, nz, R)).to(dev)
+        f = torch.zeros_like(ustar)
+        stn.varcoef_apply_f64(ustar, a, f, W, R)  # manufactured right-hand side f = A u*
+        return a, f, ustar
+
+    out = {"workload": "varcoef"}
+    # full size: rates
+    nx, ny, nz = 768, 768, 384
+    a, f, ustar = problem(nx, ny, nz)
+    a32, f32 = a.float(), f.float()
+    e0 = torch.zeros_like(f32)
+    e1 = torch.zeros_like(f32)
+    sweeps = 20
+    stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, 2)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, sweeps)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms32 = ev0.elapsed_time(ev1) / sweeps
+    u = torch.zeros_like(f)
+    stn.varcoef_residual_norm_f64(u, a, f, W, R)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(3):
+        stn.varcoef_residual_norm_f64(u, a, f, W, R)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_res = ev0.elapsed_time(ev1) / 3
+    u64a, u64b = torch.zeros_like(f), torch.zeros_like(f)
+    ev0.record()
+    stn.varcoef_sweep_f64(u64a, u64b, a, f, W, R, 3)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms64 = ev0.elapsed_time(ev1) / 3
+    pts = float(nx) * ny * nz
+    out["full_size"] = {"grid": [nx, ny, nz], "f32_sweep_ms": ms32, "f32_sweep_glups": pts / ms32 / 1e6,
+                        "f32_sweep_hbm_gbs": 16.0 * pts / ms32 / 1e6, "f64_residual_ms": ms_res,
+                        "f64_sweep_ms": ms64, "f64_sweep_glups": pts / ms64 / 1e6}
+    del a, f, ustar, a32, f32, e0, e1, u, u64a, u64b
+    torch.cuda.empty_cache()
+    # reduced grid: complete solves
+    nx, ny, nz = 96, 96, 48
+    a, f, ustar = problem(nx, ny, nz)
+    res = {}
+    for name in ("refined", "plain_f64"):
+        u = torch.zeros_like(f)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "refined":
+            rc, info = stn.jacobi_solve_varcoef_refined(a, f, u, W, R, 1e-10, 4000, 40)
+        else:
+            rc, info = stn.jacobi_solve_varcoef_f64(a, f, u, W, R, 1e-10, 10 ** 6, 200)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        err = float((u - ustar).abs().max() / ustar.abs().max())
+        res[name] = {"seconds": dt, "rc": rc, "rel_res": info["rel_res"], "sweeps": info["iters"],
+                     "outer": info["outer"], "err_vs_manufactured": err}
+    out["reduced_96x96x48"] = res
+    ratio = res["plain_f64"]["seconds"] / res["refined"]["seconds"]
+    line = {"metric": "time to 1e-10 relative residual, variable-coefficient r=2 Poisson (refined vs FP64)",
+            "value": ratio, "unit": "speedup (x)", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": res["refined"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 refined", "data": "synthetic",
+            "config": {"workload": "768x768x384 variable-coefficient 13-point Poisson, a ~ U[0.5,1.5] (seed 3), "
+                                   "manufactured (1,1,1) sine solution; full-size sweep rates + complete solves "
+                                   "on 96x96x48"},
+            "detail": out}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- serving -----
 def serve_requests(count, seed_sizes=6, seed_rhs=7):
     """Per-axis sizes log-uniform in [32, 256] (PCG64 seed 6); right-hand sides
@@ -546,7 +633,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef"])
     ap.add_argument("--requests", type=int, default=48, help="serving workload: requests per trace")
     ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8, 1.1],
                     help="serving workload: offered loads as fractions of the measured capacity")
@@ -566,6 +653,13 @@ def main():
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("steps >= 1, warmup >= 0")
+    if args.workload == "varcoef":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "variable-coefficient workload: CPU oracle arm "
+                              "only implemented for the sweep workloads"}))
+            return
+        run_varcoef(args)
+        return
     if args.workload == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "serving workload: CPU oracle arm only "

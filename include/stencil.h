@@ -109,7 +109,17 @@ int stencil_release_workspace(void);
  *   "batch_engine": batched solvers: 0 dynamic work-unit scheduler (default:
  *                   any CTA may take any unit of any problem in flight),
  *                   1 one thread-block cluster per problem.
- * Every variant, depth and engine computes bitwise the same iterates.  Not thread-safe against
+ * Every variant, depth and engine computes bitwise the same iterates.
+ * Limits and host-side fault injection (for tests of failure handling; no
+ * GPU fault is ever caused):
+ *   "sched_idle_ms": batched scheduler idle limit (default 2000 ms); CTAs
+ *                   that find no work for this long end the launch with
+ *                   STN_ETIMEOUT.
+ *   "fault_withhold_last": 1 = batched scheduler never queues the last
+ *                   problem, so the launch times out (STN_ETIMEOUT).
+ *   "fault_admit_fail": the server's next N admission allocations fail
+ *                   (retried later, like a busy pool); "fault_admit_failed"
+ *                   (read only) counts the injected failures.  Not thread-safe against
  * concurrent launches.  Unknown knob or value: STN_EINVAL.
  */
 int stencil_tune_set(const char* knob, int64_t value);

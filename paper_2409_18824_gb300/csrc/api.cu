@@ -665,6 +665,22 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0 or 1");
     return STN_OK;
   }
+  SchedFaults& f = sched_faults();
+  if (strcmp(knob, "fault_withhold_last") == 0) {
+    if (value < 0 || value > 1) return einval("fault_withhold_last must be 0 or 1");
+    f.withhold_last = (int)value;
+    return STN_OK;
+  }
+  if (strcmp(knob, "sched_idle_ms") == 0) {
+    if (value < 1 || value > 600000) return einval("sched_idle_ms must be in [1, 600000]");
+    f.idle_ms = value;
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_admit_fail") == 0) {
+    if (value < 0) return einval("fault_admit_fail must be >= 0");
+    f.admit_fail = (int)value;
+    return STN_OK;
+  }
   return einval("unknown knob");
 }
 
@@ -681,6 +697,23 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "batch_engine") == 0) {
     *value = tune_get_batch_engine();
+    return STN_OK;
+  }
+  const SchedFaults& f = sched_faults();
+  if (strcmp(knob, "fault_withhold_last") == 0) {
+    *value = f.withhold_last;
+    return STN_OK;
+  }
+  if (strcmp(knob, "sched_idle_ms") == 0) {
+    *value = f.idle_ms;
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_admit_fail") == 0) {
+    *value = f.admit_fail;
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_admit_failed") == 0) {
+    *value = f.admit_failed;
     return STN_OK;
   }
   return einval("unknown knob");

@@ -635,6 +635,7 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
     a.words = (unsigned long long*)(base + o_words);
     a.nslots = nslots;
     a.count = (int)count;
+    a.qlen = sched_faults().withhold_last ? (int)count - 1 : (int)count;
     a.queue = (const int*)(base + o_queue);
     a.qcap = (int)count;
     int* ctr = (int*)(base + o_ctr);
@@ -653,7 +654,8 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
     a.inner_tol = inner_tol;
     a.max_outer = max_outer;
     a.refined = refined ? 1 : 0;
-    a.idle_cycles = 4000000000ll;  // about 2 s at GB300 clocks without any claimable unit
+    // idle limit without any claimable unit (2 s by default), in SM clock cycles
+    a.idle_cycles = sched_faults().idle_ms * 2070000ll;
     if ((rc = sched_launch(a, radius, hc0, ctas, s)) != STN_OK) break;
     if ((e = cudaMemcpyAsync(hres.data(), base + o_res, sizeof(SchedResult) * count, cudaMemcpyDeviceToHost, s))) break;
     if ((e = cudaMemcpyAsync(&herr, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
@@ -663,7 +665,7 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
   if (rc != STN_OK) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "batched scheduler");
   if (herr != 0) {
-    set_error(herr == STN_ETIMEOUT ? "batched scheduler: a CTA found no work for 2 s (stalled)"
+    set_error(herr == STN_ETIMEOUT ? "batched scheduler: CTAs found no work within the idle limit (stalled)"
                                    : "batched scheduler: device error");
     return herr;
   }

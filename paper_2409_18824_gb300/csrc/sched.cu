@@ -387,7 +387,7 @@ __device__ void admit(const SchedArgs& a, int si, int pi) {
 // Takes the next queued problem index, or -1.  For serving the host appends
 // entries and then advances *qtail (system-scope release).
 __device__ int pop_queue(const SchedArgs& a) {
-  const int tail = a.serving ? ld_acquire_sys_s32(a.qtail) : a.count;
+  const int tail = a.serving ? ld_acquire_sys_s32(a.qtail) : a.qlen;
   int h = atomicAdd(a.qhead, 0);
   while (h < tail) {
     const int got = atomicCAS(a.qhead, h, h + 1);
@@ -619,5 +619,10 @@ int sched_ctas(int radius, bool has_c0) {
 }
 
 i64 sched_units(i64 nx, i64 ny, i64 nz) { return make_geo((int)nx, (int)ny, (int)nz).n; }
+
+SchedFaults& sched_faults() {
+  static SchedFaults f;
+  return f;
+}
 
 }  // namespace stn

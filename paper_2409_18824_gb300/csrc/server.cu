@@ -107,7 +107,16 @@ struct ServerImpl {
   int admit_one(Req* r) {
     const size_t n = (size_t)((r->nx + 2 * opts.radius) * (r->ny + 2 * opts.radius) * (r->nz + 2 * opts.radius));
     const size_t n8 = (n * 8 + 255) / 256 * 256, n4 = (n * 4 + 255) / 256 * 256;
-    cudaError_t e = cudaMallocAsync((void**)&r->dev, r->bytes, sc);
+    cudaError_t e;
+    {
+      SchedFaults& f = sched_faults();
+      if (f.admit_fail > 0) {  // injected allocation failure: same path as a busy pool
+        f.admit_fail--;
+        f.admit_failed++;
+        return -1;
+      }
+    }
+    e = cudaMallocAsync((void**)&r->dev, r->bytes, sc);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       return -1;  // pool could not serve it right now: retry later
@@ -201,6 +210,7 @@ struct ServerImpl {
     a.words = words;
     a.nslots = nslots;
     a.count = cap;
+    a.qlen = 0;
     a.queue = queue_d;
     a.qcap = cap;
     a.qhead = ctr + 0;

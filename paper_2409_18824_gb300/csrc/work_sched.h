@@ -53,6 +53,7 @@ struct SchedArgs {
   unsigned long long* words;  // per slot: (pass << 32) | next unit
   int nslots;
   int count;                  // problems in total (batch) / queue capacity bound (serving)
+  int qlen;                   // batch: queue entries available (count, or fewer under fault injection)
   const int* queue;           // problem indices in admission order (ring of qcap)
   int qcap;
   int* qhead;                 // device counter of taken queue entries
@@ -93,6 +94,15 @@ enum {
 void sched_last_stats(unsigned long long* out);
 
 int sched_launch(const SchedArgs& a, int radius, bool has_c0, int ctas, cudaStream_t s);
+
+// Fault injection and limits for tests (process-wide; all default to off).
+struct SchedFaults {
+  int withhold_last = 0;      // batch: never queue the last problem (the CTAs then time out)
+  long long idle_ms = 2000;   // batch: idle limit before STN_ETIMEOUT
+  int admit_fail = 0;         // server: fail this many admission allocations (retried later)
+  long long admit_failed = 0; // server: admission failures seen so far
+};
+SchedFaults& sched_faults();
 // CTAs of one full wave of the scheduler kernel (-1 on error).
 int sched_ctas(int radius, bool has_c0);
 // Work units of a problem's pass.

@@ -134,3 +134,24 @@ def test_refined_adaptive_inner_reaches_tolerance(lib, cuda, engine):
         assert rel <= tol and abs(rel - infos[i]["rel_res"]) <= 1e-6 * tol
         u_ref, _, _, _ = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, 1e-13, 200000, 100)
         assert np.max(np.abs(got - u_ref)) / np.max(np.abs(u_ref)) < 1e-6
+
+
+def test_device_wait_times_out_and_context_survives(lib, cuda):
+    """Failure detection without a GPU fault: the last problem is never queued,
+    so every CTA runs out of work while the batch is unfinished; the bounded
+    idle wait ends the launch with STN_ETIMEOUT, and the next call works."""
+    rhs = make_batch(SIZES[:4])
+    try:
+        lib.stencil_tune_set("sched_idle_ms", 200)
+        lib.stencil_tune_set("fault_withhold_last", 1)
+        d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+        with pytest.raises(lib.StencilError) as ei:
+            lib.jacobi_solve_batched_f64(d_u, [to_dev(b) for b in rhs], L7, 1, 1e-8, 40000, 10)
+        assert ei.value.code == lib.STN_ETIMEOUT
+        assert "idle" in str(ei.value)
+    finally:
+        lib.stencil_tune_set("fault_withhold_last", 0)
+        lib.stencil_tune_set("sched_idle_ms", 2000)
+    d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+    rc, infos = lib.jacobi_solve_batched_f64(d_u, [to_dev(b) for b in rhs], L7, 1, 1e-8, 40000, 10)
+    assert rc == 0 and all(i["status"] == 0 for i in infos)

@@ -120,3 +120,22 @@ def test_serving_shutdown_with_requests_in_flight(lib, cuda):
     t0 = time.time()
     srv.close()  # finishes the submitted requests, then frees everything
     assert time.time() - t0 < 120
+
+
+def test_serving_survives_injected_admission_failures(lib, cuda):
+    """Host-side fault injection: the first admission allocations fail; the
+    server retries them later and every request still completes correctly."""
+    rhss = requests(6, seed=71, lo=8, hi=16)
+    lib.stencil_tune_set("fault_admit_fail", 5)
+    before = lib.stencil_tune_get("fault_admit_failed")
+    try:
+        with lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=True, max_inflight=4) as srv:
+            tickets = [srv.submit(b) for b in rhss]
+            for t, b in zip(tickets, rhss):
+                res = srv.wait(t, 60.0)
+                assert res["status"] == 0
+                u = srv.result(t, b.shape)
+                assert oracle.residual_norm(u, L7, 1, b) / oracle.interior_norm(b, 1) <= 1e-8
+    finally:
+        lib.stencil_tune_set("fault_admit_fail", 0)
+    assert lib.stencil_tune_get("fault_admit_failed") - before == 5
