@@ -106,6 +106,10 @@ int stencil_release_workspace(void);
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
  *                   (temporal blocking): 0 automatic (currently 1), 1 off,
  *                   2..4 (double radius 2: at most 3).
+ *   "solve_graph":  jacobi_solve_f64 iterates inside a CUDA graph whose while
+ *                   node repeats {check_every sweeps, device-side convergence
+ *                   decision} with no host round trip (1, default), or in a
+ *                   host loop that reads the residual every check (0).
  *   "batch_engine": batched solvers: 0 dynamic work-unit scheduler (default:
  *                   any CTA may take any unit of any problem in flight),
  *                   1 one thread-block cluster per problem.

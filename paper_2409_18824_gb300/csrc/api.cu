@@ -333,6 +333,72 @@ static int rhs_norm(Workspace* ws, const T* f, const Grid& g, cudaStream_t s, do
   return STN_OK;
 }
 
+static int g_solve_graph = 1;
+int tune_set_solve_graph(int v) {
+  if (v < 0 || v > 1) return STN_EINVAL;
+  g_solve_graph = v;
+  return STN_OK;
+}
+int tune_get_solve_graph() { return g_solve_graph; }
+
+// Runs full groups of `group` sweeps inside one CUDA graph: a while node whose
+// body is the group's sweeps (the last one fused with the residual), the
+// device-side decision kernel and, for an odd group, a copy that brings the
+// iterate back to `a`.  Stops on convergence or when the next group would
+// pass max_full.  On return *it_out sweeps are done (a multiple of group) and
+// the iterate is in `a`.
+static int graph_groups(double* a, double* bgrid, const double* db, const Grid& g, const double* coeffs,
+                        Workspace* ws, i64 nparts, double tol, i64 group, i64 max_full,
+                        cudaStream_t s, i64* it_out, bool* conv_out) {
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  cudaGraph_t graph = nullptr, body = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e;
+  int rc = STN_OK;
+  do {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) break;
+    if ((e = cudaGraphCreate(&graph, 0))) break;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault))) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if ((e = cudaGraphAddNode(&wn, graph, nullptr, nullptr, 0, &cp))) break;
+    body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
+    double* cur = a;
+    double* nxt = bgrid;
+    for (i64 k = 0; k < group && rc == STN_OK; k++) {
+      rc = launch_star<double>(cur, db, nxt, g, coeffs, k == group - 1 ? kSweepResidual : kSweep,
+                               ws->partials, cs);
+      std::swap(cur, nxt);
+    }
+    if (rc == STN_OK) rc = launch_decide(ws->partials, nparts, ws->scalars, tol, group, max_full, h, cs);
+    if (rc == STN_OK && cur != a) e = cudaMemcpyAsync(a, cur, bytes, cudaMemcpyDeviceToDevice, cs);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+    if (rc != STN_OK) break;
+    if (e != cudaSuccess) break;
+    if ((e = e2)) break;
+    if ((e = cudaGraphInstantiate(&exec, graph, 0))) break;
+    if ((e = cudaMemsetAsync(ws->scalars + 5, 0, sizeof(double), s))) break;
+    if ((e = cudaGraphLaunch(exec, s))) break;
+    if ((rc = read_scalars(ws, 0, 6, s))) break;
+    *it_out = (i64)ws->host_scalars[5];
+    *conv_out = ws->host_scalars[3] != 0.0;
+  } while (false);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (rc != STN_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "graph-driven solve");
+  return STN_OK;
+}
+
 static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, const double* coeffs,
                        int radius, double tol, i64 max_iters, i64 check_every, stn_solve_info* info,
                        void* stream) {
@@ -360,18 +426,31 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
   if (int rc = launch_copy_halo<double>(du, tmp, g, s)) return rc;
   double bn = 0.0;
   if (int rc = rhs_norm<double>(ws, db, g, s, &bn)) return rc;
-  double* cur = du;
-  double* nxt = tmp;
-  auto step = [&](i64, bool last) -> int {
-    int rc = launch_star<double>(cur, db, nxt, g, coeffs, last ? kSweepResidual : kSweep, ws->partials, s);
-    std::swap(cur, nxt);
-    return rc;
-  };
-  i64 iters = 0;
+  i64 done = 0;
+  bool conv = false;
   double rel = 0, res = 0;
   int status = STN_NOT_CONVERGED;
-  if (int rc = solve_loop(ws, max_iters, check_every, nb_sweep, tol, s, step, &iters, &rel, &res, &status))
-    return rc;
+  const i64 max_full = (max_iters / check_every) * check_every;
+  if (g_solve_graph && max_full >= check_every) {
+    if (int rc = graph_groups(du, tmp, db, g, coeffs, ws, nb_sweep, tol, check_every, max_full, s, &done, &conv))
+      return rc;
+    res = ws->host_scalars[1];
+    rel = ws->host_scalars[2];
+    if (conv) status = STN_OK;
+  }
+  double* cur = du;
+  double* nxt = tmp;
+  if (!conv && done < max_iters) {
+    auto step = [&](i64, bool last) -> int {
+      int rc = launch_star<double>(cur, db, nxt, g, coeffs, last ? kSweepResidual : kSweep, ws->partials, s);
+      std::swap(cur, nxt);
+      return rc;
+    };
+    i64 more = 0;
+    if (int rc = solve_loop(ws, max_iters - done, check_every, nb_sweep, tol, s, step, &more, &rel, &res, &status))
+      return rc;
+    done += more;
+  }
   if (max_iters == 0) {
     // no sweep: measure the residual of the initial guess only
     if (int rc = launch_star<double>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s)) return rc;
@@ -385,7 +464,7 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
   if (int rc = st.finish()) return rc;
   STN_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) {
-    info->iters = iters;
+    info->iters = done;
     info->outer = 0;
     info->rel_res = rel;
     info->res_norm = res;
@@ -665,6 +744,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0 or 1");
     return STN_OK;
   }
+  if (strcmp(knob, "solve_graph") == 0) {
+    if (tune_set_solve_graph((int)value) != STN_OK) return einval("solve_graph must be 0 or 1");
+    return STN_OK;
+  }
   SchedFaults& f = sched_faults();
   if (strcmp(knob, "fault_withhold_last") == 0) {
     if (value < 0 || value > 1) return einval("fault_withhold_last must be 0 or 1");
@@ -697,6 +780,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "batch_engine") == 0) {
     *value = tune_get_batch_engine();
+    return STN_OK;
+  }
+  if (strcmp(knob, "solve_graph") == 0) {
+    *value = tune_get_solve_graph();
     return STN_OK;
   }
   const SchedFaults& f = sched_faults();

@@ -121,6 +121,14 @@ int tune_get_batch_engine();
 // scale = *scale_src (1 when that is 0), and dst[3] = (dst[2] <= tol).
 int launch_finalize(const double* partials, i64 n, double* dst, const double* scale_src,
                     double tol, cudaStream_t s);
+// Graph-driven solve: finalize + convergence decision + iteration count +
+// while-node condition (continue while not converged and another group of
+// `group` sweeps fits under max_full).
+int launch_decide(const double* partials, i64 n, double* dst, double tol, i64 group, i64 max_full,
+                  cudaGraphConditionalHandle h, cudaStream_t s);
+// Tuning: 1 = jacobi_solve_f64 iterates inside a CUDA graph (default), 0 = host loop.
+int tune_set_solve_graph(int v);
+int tune_get_solve_graph();
 // Interior sum of squares of a grid (per-block partials) then finalize.
 template <typename T>
 int launch_interior_sumsq(const T* x, const Grid& g, double* partials, i64* nparts,

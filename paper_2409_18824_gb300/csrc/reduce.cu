@@ -66,6 +66,33 @@ __global__ void __launch_bounds__(FT) finalize_kernel(const double* __restrict__
   }
 }
 
+// Device-side convergence decision of the graph-driven solve: the same
+// fixed-order sum as finalize_kernel (so the same bits as the host-driven
+// loop), then iteration bookkeeping and the while-node condition.
+// dst[0] sum, [1] norm, [2] rel, [3] converged, [5] sweeps done (as double).
+__global__ void __launch_bounds__(FT) decide_kernel(const double* __restrict__ partials, i64 n,
+                                                    double* __restrict__ dst, double tol, i64 group,
+                                                    i64 max_full, cudaGraphConditionalHandle h) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (i64 i = threadIdx.x; i < n; i += FT) v += partials[i];
+  const double t = tree_sum_1024(v, red);
+  if (threadIdx.x == 0) {
+    dst[0] = t;
+    const double nrm = sqrt(t);
+    dst[1] = nrm;
+    double sc = dst[9];
+    if (!(sc > 0.0)) sc = 1.0;
+    const double rel = nrm / sc;
+    dst[2] = rel;
+    const bool conv = rel <= tol;
+    dst[3] = conv ? 1.0 : 0.0;
+    const i64 it = (i64)dst[5] + group;
+    dst[5] = (double)it;
+    cudaGraphSetConditional(h, (!conv && it + group <= max_full) ? 1u : 0u);
+  }
+}
+
 __global__ void __launch_bounds__(FT) max_finalize_kernel(const double* __restrict__ partials,
                                                           i64 n, double* __restrict__ dst) {
   __shared__ double red[32];
@@ -109,6 +136,13 @@ __global__ void __launch_bounds__(256) interior_sumsq_kernel(const T* __restrict
 int launch_finalize(const double* partials, i64 n, double* dst, const double* scale_src, double tol,
                     cudaStream_t s) {
   finalize_kernel<<<1, FT, 0, s>>>(partials, n, dst, scale_src, tol);
+  STN_CUDA_TRY(cudaGetLastError());
+  return STN_OK;
+}
+
+int launch_decide(const double* partials, i64 n, double* dst, double tol, i64 group, i64 max_full,
+                  cudaGraphConditionalHandle h, cudaStream_t s) {
+  decide_kernel<<<1, FT, 0, s>>>(partials, n, dst, tol, group, max_full, h);
   STN_CUDA_TRY(cudaGetLastError());
   return STN_OK;
 }

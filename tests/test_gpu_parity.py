@@ -219,8 +219,17 @@ def test_residual_norm_deterministic(lib, cuda):
 
 
 # ------------------------------------------------------------------ solves --
-@pytest.mark.parametrize("shape,K", [((12, 9, 7), 5), ((33, 17, 9), 20), ((5, 4, 6), 1)])
-def test_jacobi_solve_matches_oracle(lib, cuda, shape, K):
+@pytest.fixture(params=[1, 0], ids=["graph", "hostloop"])
+def solve_mode(request, lib):
+    """Both iteration drivers: the CUDA graph with a device-side while node and
+    the host loop; they launch the same kernels, so they give the same bits."""
+    lib.stencil_tune_set("solve_graph", request.param)
+    yield request.param
+    lib.stencil_tune_set("solve_graph", 1)
+
+
+@pytest.mark.parametrize("shape,K", [((12, 9, 7), 5), ((33, 17, 9), 20), ((5, 4, 6), 1), ((20, 20, 20), 7)])
+def test_jacobi_solve_matches_oracle(lib, cuda, shape, K, solve_mode):
     nx, ny, nz = shape
     b = si.normal_interior(nx, ny, nz, 1, seed=5)
     u0 = np.zeros_like(b)
@@ -234,11 +243,11 @@ def test_jacobi_solve_matches_oracle(lib, cuda, shape, K):
     assert_bitwise(to_host(d_u), u_ref)
 
 
-def test_jacobi_solve_not_converged_and_zero_iters(lib, cuda):
+def test_jacobi_solve_not_converged_and_zero_iters(lib, cuda, solve_mode):
     b = si.normal_interior(10, 10, 10, 1, seed=6)
     d_u = to_dev(np.zeros_like(b))
     rc, info = lib.jacobi_solve_f64(to_dev(b), d_u, L7, 1, 1e-14, 30, 7)
-    assert rc == lib.STN_NOT_CONVERGED and info["iters"] == 30
+    assert rc == lib.STN_NOT_CONVERGED and info["iters"] == 30  # 4 full groups (graph) + a remainder of 2
     u_ref, it_ref, rel_ref, _ = oracle.jacobi_solve(b, np.zeros_like(b), L7, 1, 1e-14, 30, 7)
     assert_bitwise(to_host(d_u), u_ref)
     assert abs(info["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
