@@ -73,8 +73,8 @@ def load_peaks():
 # by its 32.8 M updates; summaries under profiles/).  Set to None whenever the
 # kernel changes until it is captured again.
 TRAFFIC_BYTES_PER_LUP = {
-    ("f64", 0): 498.2e6 / 320 ** 3,   # plane kernel (star_kernel<double,1>)
-    ("f32", -1): 226.9e6 / 320 ** 3,  # column kernel (star_col_kernel<float,1>)
+    ("f64", 0): 491.5e6 / 320 ** 3,   # plane kernel (star_kernel<double,1>, 16-plane chunks)
+    ("f32", -1): 225.6e6 / 320 ** 3,  # column kernel (star_col_kernel<float,1>, 2 planes prefetched)
 }
 
 # FP64 issue rate of this GPU measured with a throughput probe: 2 double
@@ -176,6 +176,7 @@ def run_cuda(args, wl):
     stream = torch.cuda.current_stream(dev)
     stn.stencil_tune_set("star_variant", args.variant)
     stn.stencil_tune_set("temporal_depth", args.temporal)
+    stn.stencil_tune_set("star_chunks", args.chunks)
 
     if args.kernel_only:
         # a few launches of the dominant kernel alone (for profilers)
@@ -265,7 +266,7 @@ def run_cuda(args, wl):
     bytes_alg = 2.0 * esize * lups_kernel           # read u, write out: compulsory traffic
     tkey = (wl["dtype"], 0 if (f64 and args.variant in (-1, 0)) else (-1 if args.variant == -1 else args.variant))
     tpl = TRAFFIC_BYTES_PER_LUP.get(tkey)
-    traffic = tpl * lups_kernel if (tpl is not None and args.temporal in (0, 1)) else None
+    traffic = tpl * lups_kernel if (tpl is not None and args.temporal in (0, 1) and args.chunks == 0) else None
     hbm_gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
     hbm_peak = float(peaks["hbm_gbs"])
     if f64:
@@ -300,7 +301,7 @@ def run_cuda(args, wl):
         "data": "synthetic",
         "config": {"workload": wl["desc"], "nx": nx, "ny": ny, "nz": nz, "radius": r,
                    "sweeps_per_step": sweeps, "kernel_variant": args.variant,
-                   "temporal_depth": args.temporal, "l2": "inputs larger than L2 (1 GiB per grid), no flush",
+                   "temporal_depth": args.temporal, "k_chunks": args.chunks, "l2": "inputs larger than L2 (1 GiB per grid), no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_val, "unit": "GLUP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * (1 + sweeps + 2),
@@ -646,6 +647,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=-1,
                     help="star-kernel variant (-1 automatic, 0 one point/thread, 1/2 register-blocked)")
+    ap.add_argument("--chunks", type=int, default=0,
+                    help="k chunks per tile column of the star kernels (0 automatic)")
     ap.add_argument("--temporal", type=int, default=0,
                     help="sweeps fused per HBM pass (0 automatic, 1 off, 2..4)")
     ap.add_argument("--kernel-only", type=int, default=0,

@@ -103,6 +103,11 @@ int stencil_release_workspace(void);
  *                   1 register/shuffle column kernel (8 j rows per thread,
  *                   no shared memory), 2 plane kernel taking two k planes
  *                   per step (more independent work per thread).
+ *   "star_chunks":  0 automatic (default), else the number of k chunks each
+ *                   column of tiles is split into (one block per tile and
+ *                   chunk; clamped to chunks of >= 4 planes).  Changes the
+ *                   grid, never the iterates; the residual's partial sums
+ *                   follow the grid, so its last bits may change.
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
  *                   (temporal blocking): 0 automatic (currently 1), 1 off,
  *                   2..4 (double radius 2: at most 3).

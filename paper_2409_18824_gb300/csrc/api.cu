@@ -740,6 +740,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_temporal_depth((int)value) != STN_OK) return einval("temporal_depth must be 0..4");
     return STN_OK;
   }
+  if (strcmp(knob, "star_chunks") == 0) {
+    if (tune_set_star_chunks((int)value) != STN_OK) return einval("star_chunks must be in [0, 65535]");
+    return STN_OK;
+  }
   if (strcmp(knob, "batch_engine") == 0) {
     if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0 or 1");
     return STN_OK;
@@ -776,6 +780,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "temporal_depth") == 0) {
     *value = tune_get_temporal_depth();
+    return STN_OK;
+  }
+  if (strcmp(knob, "star_chunks") == 0) {
+    *value = tune_get_star_chunks();
     return STN_OK;
   }
   if (strcmp(knob, "batch_engine") == 0) {

@@ -101,6 +101,8 @@ ZPlan plan_temporal(const Grid& g, int depth, int resident);
 // Tuning: temporal depth for stencil_sweep (0 = automatic).
 int tune_set_temporal_depth(int d);
 int tune_get_temporal_depth();
+int tune_set_star_chunks(int c);
+int tune_get_star_chunks();
 
 // ---- batched solves (batched.cu) --------------------------------------------
 // One persistent cluster launch over `count` problems (device grids).

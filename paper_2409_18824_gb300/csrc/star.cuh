@@ -307,19 +307,25 @@ __global__ void __launch_bounds__(TX* TY)
 // ---------------------------------------------------------------------------
 constexpr int SC_WARPS = 4;
 constexpr int SC_TJ = 8;
+// planes of prefetch: two for float (measured best at 512^3), one for double
+// (its wider registers would cost occupancy)
+template <typename T>
+struct ColPF {
+  static constexpr int value = sizeof(T) == 4 ? 2 : 1;
+};
 
-template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE, int TJ, int PF>
-__global__ void __launch_bounds__(32 * SC_WARPS)
+template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE, int TJ, int PF, int WARPS = SC_WARPS>
+__global__ void __launch_bounds__(32 * WARPS)
     star_col_kernel(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ out, int nx,
                     int ny, int nz, int NX, int NY, int kchunk, StarCoeffs<T, R> cf,
                     double* __restrict__ partials) {
   using A = Arith<T>;
   constexpr int Q = 2 * R + 1 + PF;
   constexpr int CW = 32 - 2 * R;  // computing lanes per warp
-  __shared__ double red[SC_WARPS];
+  __shared__ double red[WARPS];
   const int lane = threadIdx.x, w = threadIdx.y;
   const int gi = blockIdx.x * CW + lane;  // padded i of this lane (lane R <-> interior column)
-  const int j0 = R + (blockIdx.y * SC_WARPS + w) * TJ;
+  const int j0 = R + (blockIdx.y * WARPS + w) * TJ;
   const i64 sz = (i64)NX * NY;
   const int k0 = R + blockIdx.z * kchunk;
   const int k1 = min(k0 + kchunk, nz + R);
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(32 * SC_WARPS)
     }
   }
   if (MODE != kSweep) {
-    const double t = block_sum_fixed<32 * SC_WARPS>(rsum, red);
+    const double t = block_sum_fixed<32 * WARPS>(rsum, red);
     if (lane == 0 && w == 0)
       partials[blockIdx.x + gridDim.x * ((i64)blockIdx.y + (i64)gridDim.y * blockIdx.z)] = t;
   }
@@ -445,7 +451,6 @@ int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* c
   for (int d = 0; d <= R; d++) cf.c[d] = (T)coeffs[d];
   dim3 grid(p.tiles_x, p.tiles_y, p.chunks);
   const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz, NX = (int)g.NX(), NY = (int)g.NY();
-  constexpr int PF = 1;
 #define STN_LAUNCH_MODES(KERNEL_EXPR, BLOCK)                                                     \
   switch (mode) {                                                                                \
     case kSweep: KERNEL_EXPR(kSweep)<<<grid, BLOCK, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials); break; \
@@ -453,7 +458,7 @@ int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* c
     default: KERNEL_EXPR(kResidualOnly)<<<grid, BLOCK, 0, s>>>(u, b, out, nx, ny, nz, NX, NY, p.kchunk, cf, partials); break; \
   }
 #define STN_SCALAR(M) star_kernel<T, R, HAS_B, HAS_C0, M>
-#define STN_COL(M) star_col_kernel<T, R, HAS_B, HAS_C0, M, SC_TJ, PF>
+#define STN_COL(M) star_col_kernel<T, R, HAS_B, HAS_C0, M, SC_TJ, ColPF<T>::value>
 #define STN_PLANE2(M) star2_kernel<T, R, HAS_B, HAS_C0, M>
   if (variant == kStarColumn) {
     STN_LAUNCH_MODES(STN_COL, dim3(32, SC_WARPS))

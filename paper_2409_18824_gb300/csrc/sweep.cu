@@ -22,25 +22,88 @@ int tune_set_temporal_depth(int d) {
 }
 int tune_get_temporal_depth() { return g_temporal_depth; }
 
+static int g_star_chunks = 0;
+int tune_set_star_chunks(int c) {
+  if (c < 0 || c > 65535) return STN_EINVAL;
+  g_star_chunks = c;
+  return STN_OK;
+}
+int tune_get_star_chunks() { return g_star_chunks; }
+
+template <typename K>
+static int occupancy(K kernel, int threads) {
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess || v < 1) {
+    (void)cudaGetLastError();
+    v = 4;  // no device (planning only): a fixed estimate
+  }
+  return v;
+}
+
+// Blocks of a star kernel resident per SM, queried once per (variant, element
+// type, radius) on the sweep instance; every mode uses the same plan.
+static int star_resident(int variant, size_t esize, int r) {
+  static int cache[3][2][3] = {};
+  int& c = cache[variant][esize == 8 ? 1 : 0][r];
+  if (c != 0) return c;
+  const int tc = 32 * SC_WARPS, tp = TX * TY;
+  if (esize == 8) {
+    if (variant == kStarColumn)
+      c = r == 1 ? occupancy(star_col_kernel<double, 1, false, false, kSweep, SC_TJ, ColPF<double>::value>, tc)
+                 : occupancy(star_col_kernel<double, 2, false, false, kSweep, SC_TJ, ColPF<double>::value>, tc);
+    else if (variant == kStarPlane2)
+      c = r == 1 ? occupancy(star2_kernel<double, 1, false, false, kSweep>, tp)
+                 : occupancy(star2_kernel<double, 2, false, false, kSweep>, tp);
+    else
+      c = r == 1 ? occupancy(star_kernel<double, 1, false, false, kSweep>, tp)
+                 : occupancy(star_kernel<double, 2, false, false, kSweep>, tp);
+  } else {
+    if (variant == kStarColumn)
+      c = r == 1 ? occupancy(star_col_kernel<float, 1, false, false, kSweep, SC_TJ, ColPF<float>::value>, tc)
+                 : occupancy(star_col_kernel<float, 2, false, false, kSweep, SC_TJ, ColPF<float>::value>, tc);
+    else if (variant == kStarPlane2)
+      c = r == 1 ? occupancy(star2_kernel<float, 1, false, false, kSweep>, tp)
+                 : occupancy(star2_kernel<float, 2, false, false, kSweep>, tp);
+    else
+      c = r == 1 ? occupancy(star_kernel<float, 1, false, false, kSweep>, tp)
+                 : occupancy(star_kernel<float, 2, false, false, kSweep>, tp);
+  }
+  return c;
+}
+
 ZPlan plan_star(const Grid& g, int variant, size_t esize) {
   ZPlan p;
-  // blocks resident per SM for each variant (register-limited)
-  i64 resident;
+  const i64 max_chunks = (g.nz + 3) / 4;  // chunks of >= 4 planes
+  i64 chunks;
   if (variant == kStarColumn) {
+    // one wave at most: k chunks = resident slots / tiles (measured: a partial
+    // wave beats 1.2-1.9 waves by 15-20 % on this memory-bound kernel)
     p.tiles_x = (int)((g.nx + (32 - 2 * g.r) - 1) / (32 - 2 * g.r));
     p.tiles_y = (int)((g.ny + SC_WARPS * SC_TJ - 1) / (SC_WARPS * SC_TJ));
-    resident = esize == 4 ? 8 : 5;
+    const i64 slots = (i64)152 * star_resident(variant, esize, g.r);
+    const i64 tiles = (i64)p.tiles_x * p.tiles_y;
+    chunks = slots / (tiles > 0 ? tiles : 1);
   } else {
     p.tiles_x = (int)((g.nx + TX - 1) / TX);
     p.tiles_y = (int)((g.ny + TY - 1) / TY);
-    resident = esize == 4 ? 8 : 5;
+    i64 resident = esize == 4 ? 8 : 5;
     if (variant == kStarPlane2) resident = esize == 4 ? 6 : 4;
+    // enough blocks to fill every SM
+    const i64 want = 152 * resident;
+    const i64 tiles = (i64)p.tiles_x * p.tiles_y;
+    chunks = (want + tiles - 1) / tiles;
+    if (esize == 8) {
+      // double sweeps are bound by the FP64 pipe, so the extra halo planes of
+      // short chunks cost little while many short blocks keep every SM's pipe
+      // busy to the end (measured at 512^3: 79 -> 86 GLUP/s from one chunk to
+      // chunks of 16 planes; at 320^3: 71 -> 85).  At most 32768 blocks.
+      i64 c16 = (g.nz + 15) / 16;
+      const i64 cap = 32768 / (tiles > 0 ? tiles : 1);
+      if (c16 > cap) c16 = cap;
+      if (c16 > chunks) chunks = c16;
+    }
   }
-  const i64 want = 152 * resident;
-  // enough blocks to fill every SM; chunks of >= 4 planes
-  const i64 tiles = (i64)p.tiles_x * p.tiles_y;
-  i64 chunks = (want + tiles - 1) / tiles;
-  const i64 max_chunks = (g.nz + 3) / 4;
+  if (g_star_chunks > 0) chunks = g_star_chunks;
   if (chunks > max_chunks) chunks = max_chunks;
   if (chunks < 1) chunks = 1;
   p.kchunk = (int)((g.nz + chunks - 1) / chunks);

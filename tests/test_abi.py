@@ -118,7 +118,8 @@ def test_tuning_knobs(lib):
     lib.stencil_tune_set("star_variant", 1)
     assert lib.stencil_tune_get("star_variant") == 1
     lib.stencil_tune_set("star_variant", -1)
-    for knob, good, bad in (("temporal_depth", 3, 5), ("batch_engine", 1, 2), ("solve_graph", 0, 2)):
+    for knob, good, bad in (("temporal_depth", 3, 5), ("batch_engine", 1, 2), ("solve_graph", 0, 2),
+                            ("star_chunks", 7, -1)):
         before = lib.stencil_tune_get(knob)
         with pytest.raises(lib.StencilError):
             lib.stencil_tune_set(knob, bad)

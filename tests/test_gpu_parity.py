@@ -141,6 +141,33 @@ def test_every_kernel_variant_bitwise(lib, cuda, variant, r, c):
         lib.stencil_tune_set("star_variant", -1)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_forced_chunk_counts_bitwise(lib, cuda, variant):
+    """Forcing the number of k chunks (one block per tile and chunk: ragged last
+    chunks, chunks shorter than the radius ring, more chunks than allowed) leaves
+    every sweep bit unchanged and the residual within the norm tolerance."""
+    c = (0.2, 0.1, 0.0333)
+    try:
+        lib.stencil_tune_set("star_variant", variant)
+        for chunks in (1, 2, 3, 5, 7, 1000):
+            lib.stencil_tune_set("star_chunks", chunks)
+            assert lib.stencil_tune_get("star_chunks") == chunks
+            for (nx, ny, nz), r, cf in (((37, 19, 29), 1, L7), ((64, 40, 33), 2, c)):
+                u0 = si.uniform_interior(nx, ny, nz, r, seed=chunks, lo=-1, hi=1)
+                d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+                lib.stencil_sweep_f64(d_in, d_out, cf, r, 2)
+                assert_bitwise(to_host(d_out), oracle.stencil_sweep(u0, cf, r, 2))
+                u32 = u0.astype(np.float32)
+                d_in, d_out = to_dev(u32), to_dev(np.zeros_like(u32))
+                lib.stencil_sweep_f32(d_in, d_out, cf, r, 2)
+                assert_bitwise(to_host(d_out), oracle.stencil_sweep(u32, cf, r, 2))
+                nref = oracle.residual_norm(u0, cf, r)
+                assert abs(lib.residual_norm_f64(to_dev(u0), cf, r) - nref) <= NORM_RTOL * nref
+    finally:
+        lib.stencil_tune_set("star_chunks", 0)
+        lib.stencil_tune_set("star_variant", -1)
+
+
 @pytest.mark.parametrize("depth", [2, 3, 4])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
