@@ -402,7 +402,8 @@ def run_batched(args):
         "dtype": "f32+f64 refined" if refined else "f64", "data": "synthetic",
         "config": {"workload": f"{args.batch} independent 7-point Poisson solves u = S u + b, per-axis sizes "
                                f"log-uniform in [16,128] (seed 4), b ~ N(0,1), tol 1e-8, one persistent "
-                               f"cluster launch" + (", FP32 sweeps with FP64 refinement" if refined else ", FP64"),
+                               f"{'cluster' if stn.stencil_tune_get('batch_engine') == 1 else 'work-unit scheduler'} launch"
+                               + (", FP32 sweeps with FP64 refinement" if refined else ", FP64"),
                    "batch": args.batch, "points": int(pts.sum()), "l2": "no flush (each solve re-reads its grid)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": args.batch / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": total * 8,

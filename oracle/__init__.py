@@ -13,6 +13,10 @@ each function for numpy arrays laid out as the library expects: a C-contiguous
 array of shape (nz+2r, ny+2r, nx+2r), which is the Fortran column-major array
 u(1:nx+2r, 1:ny+2r, 1:nz+2r) (arXiv 2409.18824 Sec. 5.2, Listing 7).
 
+Two-dimensional grids (the paper's own jacobi benchmark) are C-contiguous
+arrays of shape (ny+2r, nx+2r), i fastest; their functions carry a ``2d``
+suffix and are pinned in tests/test_oracle_2d.py.
+
 Pins (tests/test_oracle.py): closed-form eigenmode decay, constant and linear
 invariants, dense brute force, Gaussian elimination, symmetry of the
 variable-coefficient operator.  The refinement driver
@@ -81,6 +85,12 @@ def _load():
                                                             ctypes.c_int, ctypes.c_double, _i64, _i64,
                                                             ctypes.POINTER(_i64), _dp]),
             "oracle_dense_solve": (ctypes.c_int, [_dp, _dp, _i64]),
+            "oracle_sweep2d_f64": (None, [_dp, _dp, _dp, _i64, _i64, _dp, ctypes.c_int]),
+            "oracle_sweep2d_f32": (None, [_fp, _fp, _fp, _i64, _i64, _fp, ctypes.c_int]),
+            "oracle_stencil_sweep2d_f64": (ctypes.c_int, [_dp, _dp, _i64, _i64, _dp, ctypes.c_int, _i64]),
+            "oracle_stencil_sweep2d_f32": (ctypes.c_int, [_fp, _fp, _i64, _i64, _fp, ctypes.c_int, _i64]),
+            "oracle_residual_norm2d_f64": (ctypes.c_double, [_dp, _dp, _i64, _i64, _dp, ctypes.c_int]),
+            "oracle_residual_norm2d_f32": (ctypes.c_double, [_fp, _fp, _i64, _i64, _fp, ctypes.c_int]),
             "oracle_refined_solve_f64": (ctypes.c_int, [_dp, _dp, _i64, _i64, _i64, _dp, ctypes.c_int,
                                                         ctypes.c_double, _i64, _i64, ctypes.POINTER(_i64), _dp]),
         }
@@ -183,6 +193,76 @@ def jacobi_solve(b: np.ndarray | None, u0: np.ndarray, coeffs, r: int, tol: floa
     if st < 0:
         raise MemoryError("oracle allocation failed")
     return u, it.value, rel.value, st
+
+
+# ------------------------------------------------------------------- 2-D --
+def _grid2(a: np.ndarray, dtype) -> np.ndarray:
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"] or a.ndim != 2:
+        raise ValueError(f"oracle wants a C-contiguous 2D {np.dtype(dtype).name} array, got "
+                         f"{a.dtype} {a.shape}")
+    return a
+
+
+def interior_shape2d(u: np.ndarray, r: int):
+    ny, nx = (s - 2 * r for s in u.shape)
+    if min(nx, ny) < 1:
+        raise ValueError("grid smaller than its halo")
+    return nx, ny
+
+
+def _c2(coeffs, dtype):
+    c = np.asarray(coeffs, dtype=np.float64)
+    return np.ascontiguousarray(c if dtype == np.float64 else c.astype(np.float32))
+
+
+def sweep2d(u: np.ndarray, coeffs, r: int, b: np.ndarray | None = None) -> np.ndarray:
+    """One 2-D sweep of a padded (ny+2r, nx+2r) array; the halo is copied."""
+    lib = _load()
+    dt = u.dtype.type
+    _grid2(u, dt)
+    if b is not None:
+        _grid2(b, dt)
+    out = u.copy()
+    c = _c2(coeffs, dt)
+    if dt == np.float64:
+        lib.oracle_sweep2d_f64(_ptr(u, ctypes.c_double), _ptr(b, ctypes.c_double), _ptr(out, ctypes.c_double),
+                               *interior_shape2d(u, r), _ptr(c, ctypes.c_double), r)
+    else:
+        lib.oracle_sweep2d_f32(_ptr(u, ctypes.c_float), _ptr(b, ctypes.c_float), _ptr(out, ctypes.c_float),
+                               *interior_shape2d(u, r), _ptr(c, ctypes.c_float), r)
+    return out
+
+
+def stencil_sweep2d(u: np.ndarray, coeffs, r: int, iters: int) -> np.ndarray:
+    """`iters` 2-D sweeps (no source term); returns the final padded grid."""
+    lib = _load()
+    dt = u.dtype.type
+    _grid2(u, dt)
+    out = np.empty_like(u)
+    c = _c2(coeffs, dt)
+    if dt == np.float64:
+        rc = lib.oracle_stencil_sweep2d_f64(_ptr(u, ctypes.c_double), _ptr(out, ctypes.c_double),
+                                            *interior_shape2d(u, r), _ptr(c, ctypes.c_double), r, iters)
+    else:
+        rc = lib.oracle_stencil_sweep2d_f32(_ptr(u, ctypes.c_float), _ptr(out, ctypes.c_float),
+                                            *interior_shape2d(u, r), _ptr(c, ctypes.c_float), r, iters)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def residual_norm2d(u: np.ndarray, coeffs, r: int, b: np.ndarray | None = None) -> float:
+    lib = _load()
+    dt = u.dtype.type
+    _grid2(u, dt)
+    if b is not None:
+        _grid2(b, dt)
+    c = _c2(coeffs, dt)
+    if dt == np.float64:
+        return lib.oracle_residual_norm2d_f64(_ptr(u, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                              *interior_shape2d(u, r), _ptr(c, ctypes.c_double), r)
+    return lib.oracle_residual_norm2d_f32(_ptr(u, ctypes.c_float), _ptr(b, ctypes.c_float),
+                                          *interior_shape2d(u, r), _ptr(c, ctypes.c_float), r)
 
 
 def _w3(w):

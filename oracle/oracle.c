@@ -41,6 +41,10 @@
  *     Jacobi update u'(p) = (f(p) + N(p)) / D(p) with D = sum w_d kappa and
  *     N = sum w_d kappa u(q), both accumulated d = 1..R, axis x,y,z, the
  *     minus neighbour before the plus neighbour.  (A u)(p) = D u(p) - N.
+ *   - Two-dimensional grids (the paper's own jacobi benchmark is 2-D, Sec. 4):
+ *     a padded (ny+2r) x (nx+2r) array, i fastest, the same Dirichlet halo
+ *     and the same canonical order without the k term:
+ *         S_d = (u[i-d]+u[i+d]) + (u[j-d]+u[j+d]).
  *
  * Functions without an independent pin are marked "parity unpinned" in their
  * comment; every other function is pinned by tests/test_oracle.py (closed
@@ -537,4 +541,115 @@ int oracle_dense_solve(double* A, double* b, i64 n) {
     b[row] = s / A[row * n + row];
   }
   return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Two-dimensional star stencil: the paper's jacobi benchmark (Sec. 4) is a
+ * Jacobi iteration for Laplace's equation on one 2-D grid.  Padded grid of
+ * (ny+2r) rows of NX = nx+2r values, i fastest (Sec. 5.2 indexing with two
+ * indices).  S_d = (u[i-d]+u[i+d]) + (u[j-d]+u[j+d]); acc = c_r*S_r, then
+ * acc + c_d*S_d for d = r-1..1; + c0*u if c0 != 0; + b if b given.
+ * ------------------------------------------------------------------------- */
+void oracle_sweep2d_f64(const double* u, const double* b, double* out, i64 nx, i64 ny,
+                        const double* c, int r) {
+  const i64 NX = nx + 2 * r;
+  for (i64 j = r; j < ny + r; j++)
+    for (i64 i = r; i < nx + r; i++) {
+      const i64 p = i + NX * j;
+      double acc = 0.0;
+      for (int d = r; d >= 1; d--) {
+        double sx = u[p - d] + u[p + d];
+        double sy = u[p - d * NX] + u[p + d * NX];
+        double t = c[d] * (sx + sy);
+        acc = (d == r) ? t : acc + t;
+      }
+      if (c[0] != 0.0) acc = acc + c[0] * u[p];
+      if (b) acc = acc + b[p];
+      out[p] = acc;
+    }
+}
+
+void oracle_sweep2d_f32(const float* u, const float* b, float* out, i64 nx, i64 ny,
+                        const float* c, int r) {
+  const i64 NX = nx + 2 * r;
+  for (i64 j = r; j < ny + r; j++)
+    for (i64 i = r; i < nx + r; i++) {
+      const i64 p = i + NX * j;
+      float acc = 0.0f;
+      for (int d = r; d >= 1; d--) {
+        float sx = u[p - d] + u[p + d];
+        float sy = u[p - d * NX] + u[p + d * NX];
+        float t = c[d] * (sx + sy);
+        acc = (d == r) ? t : acc + t;
+      }
+      if (c[0] != 0.0f) acc = acc + c[0] * u[p];
+      if (b) acc = acc + b[p];
+      out[p] = acc;
+    }
+}
+
+/* `iters` 2-D sweeps from `in` into `out` (halo of `out` = halo of `in`);
+ * Sec. 4: a fixed number of Jacobi iterations. */
+int oracle_stencil_sweep2d_f64(const double* in, double* out, i64 nx, i64 ny, const double* c,
+                               int r, i64 iters) {
+  const i64 n = (nx + 2 * r) * (ny + 2 * r);
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!tmp) return -2;
+  memcpy(out, in, sizeof(double) * (size_t)n);
+  memcpy(tmp, in, sizeof(double) * (size_t)n);
+  for (i64 it = 0; it < iters; it++) {
+    oracle_sweep2d_f64(out, NULL, tmp, nx, ny, c, r);
+    memcpy(out, tmp, sizeof(double) * (size_t)n);
+  }
+  free(tmp);
+  return 0;
+}
+
+int oracle_stencil_sweep2d_f32(const float* in, float* out, i64 nx, i64 ny, const float* c, int r,
+                               i64 iters) {
+  const i64 n = (nx + 2 * r) * (ny + 2 * r);
+  float* tmp = (float*)malloc(sizeof(float) * (size_t)n);
+  if (!tmp) return -2;
+  memcpy(out, in, sizeof(float) * (size_t)n);
+  memcpy(tmp, in, sizeof(float) * (size_t)n);
+  for (i64 it = 0; it < iters; it++) {
+    oracle_sweep2d_f32(out, NULL, tmp, nx, ny, c, r);
+    memcpy(out, tmp, sizeof(float) * (size_t)n);
+  }
+  free(tmp);
+  return 0;
+}
+
+/* sqrt(sum over the interior of ((S u + b) - u)^2), accumulated in double in
+ * j-i order (Sec. 5.3 / Listing 8 add-reduction). */
+double oracle_residual_norm2d_f64(const double* u, const double* b, i64 nx, i64 ny,
+                                  const double* c, int r) {
+  const i64 NX = nx + 2 * r, n = NX * (ny + 2 * r);
+  double* t = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!t) return -1.0;
+  oracle_sweep2d_f64(u, b, t, nx, ny, c, r);
+  double sum = 0.0;
+  for (i64 j = r; j < ny + r; j++)
+    for (i64 i = r; i < nx + r; i++) {
+      const double rho = t[i + NX * j] - u[i + NX * j];
+      sum = sum + rho * rho;
+    }
+  free(t);
+  return sqrt(sum);
+}
+
+double oracle_residual_norm2d_f32(const float* u, const float* b, i64 nx, i64 ny, const float* c,
+                                  int r) {
+  const i64 NX = nx + 2 * r, n = NX * (ny + 2 * r);
+  float* t = (float*)malloc(sizeof(float) * (size_t)n);
+  if (!t) return -1.0;
+  oracle_sweep2d_f32(u, b, t, nx, ny, c, r);
+  double sum = 0.0;
+  for (i64 j = r; j < ny + r; j++)
+    for (i64 i = r; i < nx + r; i++) {
+      const double rho = (double)t[i + NX * j] - (double)u[i + NX * j];
+      sum = sum + rho * rho;
+    }
+  free(t);
+  return sqrt(sum);
 }

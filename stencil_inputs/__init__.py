@@ -19,6 +19,9 @@ Jacobi; its data are not published, so these seeded grids stand in for it):
   * batches of solves with per-axis sizes log-uniform in [16,128] (seed 4),
     right-hand sides N(0,1) (seed 5)
   * serving arrivals: sizes log-uniform in [32,256] (seed 6), Poisson arrivals
+  * the paper's own 2-D jacobi: 1024 x 1024 FP64 r=1, interior U[0,1) seed 7,
+    zero halo, c = {0, 1/4}, 100000 sweeps (2-D grids are C-contiguous arrays
+    of shape (ny+2r, nx+2r), i fastest)
 """
 from __future__ import annotations
 
@@ -28,6 +31,8 @@ import numpy as np
 
 #: 7-point normalised Jacobi weights {c0, c1}: the discrete Laplace update.
 LAPLACE7 = (0.0, 1.0 / 6.0)
+#: 5-point normalised Jacobi weights {c0, c1} of the 2-D Laplace update.
+LAPLACE5 = (0.0, 0.25)
 #: radius-2 weights w = {unused, w1, w2} of the variable-coefficient operator.
 VARCOEF_W = (0.0, 1.0, 0.25)
 
@@ -93,3 +98,36 @@ def poisson_arrival_times(count, rate_per_s, seed):
     """Arrival times (seconds from 0) of a Poisson process with the given rate."""
     gaps = rng(seed).exponential(1.0 / rate_per_s, size=count)
     return np.cumsum(gaps)
+
+
+# ------------------------------------------------------------------- 2-D --
+def padded_shape2d(nx: int, ny: int, r: int):
+    return (ny + 2 * r, nx + 2 * r)
+
+
+def uniform_interior2d(nx, ny, r, seed, dtype=np.float64, lo=0.0, hi=1.0, halo=0.0):
+    """2-D interior ~ U[lo, hi) with i fastest, halo filled with `halo`."""
+    g = np.full(padded_shape2d(nx, ny, r), halo, dtype=np.float64)
+    g[r:r + ny, r:r + nx] = (rng(seed).random(nx * ny) * (hi - lo) + lo).reshape(ny, nx)
+    return g.astype(dtype)
+
+
+def uniform_full2d(nx, ny, r, seed, lo=0.0, hi=1.0, dtype=np.float64):
+    """Every padded 2-D cell (halo included) ~ U[lo, hi)."""
+    shape = padded_shape2d(nx, ny, r)
+    return (rng(seed).random(int(np.prod(shape))) * (hi - lo) + lo).reshape(shape).astype(dtype)
+
+
+def sine_mode2d(nx, ny, r, m=(1, 1), dtype=np.float64):
+    """sin(m_x*pi*i/(nx+1)) * sin(m_y*pi*j/(ny+1)) on the interior, zero halo."""
+    g = np.zeros(padded_shape2d(nx, ny, r), dtype=np.float64)
+    sx = np.sin(m[0] * np.pi * np.arange(1, nx + 1) / (nx + 1))
+    sy = np.sin(m[1] * np.pi * np.arange(1, ny + 1) / (ny + 1))
+    g[r:r + ny, r:r + nx] = sy[:, None] * sx[None, :]
+    return g.astype(dtype)
+
+
+def linear_field2d(nx, ny, r, alpha, beta, delta, dtype=np.float64):
+    """alpha*i + beta*j + delta on every padded 2-D cell (1-based i, j)."""
+    j, i = np.meshgrid(np.arange(1, ny + 2 * r + 1), np.arange(1, nx + 2 * r + 1), indexing="ij")
+    return (alpha * i + beta * j + delta).astype(dtype)
