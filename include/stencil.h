@@ -108,6 +108,11 @@ int stencil_release_workspace(void);
  *                   chunk; clamped to chunks of >= 4 planes).  Changes the
  *                   grid, never the iterates; the residual's partial sums
  *                   follow the grid, so its last bits may change.
+ *   "sweep2d_resident": 2-D sweeps: -1 automatic (default: shared-memory
+ *                   resident whenever the grid fits), 0 always through HBM,
+ *                   1 resident whenever it fits.
+ *   "sweep2d_chunk": most sweeps per resident 2-D launch (default 32768;
+ *                   longer runs take several launches).
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
  *                   (temporal blocking): 0 automatic (currently 1), 1 off,
  *                   2..4 (double radius 2: at most 3).
@@ -126,6 +131,9 @@ int stencil_release_workspace(void);
  *                   STN_ETIMEOUT.
  *   "fault_withhold_last": 1 = batched scheduler never queues the last
  *                   problem, so the launch times out (STN_ETIMEOUT).
+ *   "fault_withhold_2d": 1 = the last band of a resident 2-D sweep never
+ *                   publishes its rows, so its neighbour's wait runs out and
+ *                   the call returns STN_ETIMEOUT.
  *   "fault_admit_fail": the server's next N admission allocations fail
  *                   (retried later, like a busy pool); "fault_admit_failed"
  *                   (read only) counts the injected failures.  Not thread-safe against
@@ -411,6 +419,50 @@ int jacobi_solve_varcoef_refined(const double* a, const double* f, double* u, in
                                  int64_t ny, int64_t nz, const double* w, int radius, double tol,
                                  int64_t inner_sweeps, int64_t max_outer, stn_solve_info* info,
                                  void* stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Two-dimensional grids: the paper's own jacobi benchmark (Sec. 4: a Jacobi
+ * iteration for Laplace's equation on one 2-D 1024 x 1024 grid, 100000
+ * iterations).  A 2-D grid is a padded (ny+2r) x (nx+2r) array with i fastest
+ * (the Fortran array u(1:nx+2r, 1:ny+2r), Sec. 5.2 indexing), the same
+ * Dirichlet halo as the 3-D grids.  Canonical order of one update:
+ *     S_d = (u[i-d]+u[i+d]) + (u[j-d]+u[j+d]);  acc = c_r*S_r;
+ *     acc = acc + c_d*S_d (d = r-1..1);  acc = acc + c0*u if c0 != 0;
+ *     acc = acc + b if b is given.
+ * With c = {0, 1/4} and r = 1 this is the 5-point Laplace Jacobi update.
+ *
+ * stencil_sweep2d_f64 / _f32 -- `iters` 2-D Jacobi sweeps (no source term).
+ *   in      grid holding the starting iterate (its halo is the boundary).
+ *           Grids that fit in the SMs' shared memory (1024 x 1024 doubles
+ *           does) are swept there, one band of rows per SM, and `in` is not
+ *           modified; larger grids are swept through HBM and `in`'s interior
+ *           is clobbered when iters > 1.
+ *   out     receives the result: interior = iterate number `iters`, halo =
+ *           in's halo.  iters == 0 copies in to out.
+ *   coeffs  host, radius+1 doubles {c0, c1[, c2]}; radius 1 or 2.
+ * Device or host grids.  The call synchronises `stream`.
+ * Errors: STN_EINVAL (NULL grid or coeffs, extents < 1 or > 2^28, radius not
+ * 1/2, iters < 0, in and out overlap), STN_ENOMEM, STN_ECUDA, STN_ETIMEOUT (a
+ * band's device-side wait for its neighbour's rows gave up after 2 s; the
+ * context stays usable, `out` is undefined).
+ */
+int stencil_sweep2d_f64(double* in, double* out, int64_t nx, int64_t ny, const double* coeffs,
+                        int radius, int64_t iters, void* stream);
+int stencil_sweep2d_f32(float* in, float* out, int64_t nx, int64_t ny, const double* coeffs,
+                        int radius, int64_t iters, void* stream);
+
+/*
+ * residual_norm2d_f64 / _f32 -- ||rho||_2, rho = (S u + b) - u over the 2-D
+ * interior (the Sec. 5.3 add-reduction of rho^2 in double, fixed order for
+ * given extents, then sqrt).  b may be NULL.  norm_out is a HOST double; the
+ * call synchronises `stream`.  For _f32 the stencil value is float, rho and
+ * its square double.  Errors as residual_norm_f64.
+ */
+int residual_norm2d_f64(const double* u, const double* b, int64_t nx, int64_t ny,
+                        const double* coeffs, int radius, double* norm_out, void* stream);
+int residual_norm2d_f32(const float* u, const float* b, int64_t nx, int64_t ny,
+                        const double* coeffs, int radius, double* norm_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -104,6 +104,10 @@ SIGNATURES = {
     "residual_norm_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f64_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
+    "stencil_sweep2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _vp]),
+    "stencil_sweep2d_f32": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _vp]),
+    "residual_norm2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _dp, _vp]),
+    "residual_norm2d_f32": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _dp, _vp]),
     "jacobi_solve_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _i64, _info_p, _vp]),
     "jacobi_solve_refined_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dbl, _i64, _dbl, _i64, _i64,
                                         _info_p, _vp]),
@@ -190,6 +194,15 @@ def _extents(grid, r, nx, ny, nz):
     return shape[2] - 2 * r, shape[1] - 2 * r, shape[0] - 2 * r
 
 
+def _extents2d(grid, r, nx, ny):
+    if nx is not None:
+        return nx, ny
+    shape = tuple(grid.shape)
+    if len(shape) != 2:
+        raise ValueError("pass nx, ny or a 2D grid")
+    return shape[1] - 2 * r, shape[0] - 2 * r
+
+
 def _check(rc):
     if rc < 0:
         raise StencilError(rc, last_error())
@@ -250,6 +263,39 @@ def residual_norm_f64_noalloc(u, coeffs, radius, b=None, nx=None, ny=None, nz=No
     out = ctypes.c_double(0.0)
     _check(_lib.residual_norm_f64_noalloc(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
                                           _stream(stream, u, b)))
+    return out.value
+
+
+def stencil_sweep2d_f64(in_, out, coeffs, radius, iters, nx=None, ny=None, stream=None):
+    """`iters` 2-D sweeps of a padded (ny+2r, nx+2r) grid (synchronising)."""
+    nx, ny = _extents2d(in_, radius, nx, ny)
+    cp, _keep = _coeffs(coeffs)
+    return _check(_lib.stencil_sweep2d_f64(_addr(in_), _addr(out), nx, ny, cp, radius, iters,
+                                           _stream(stream, in_, out)))
+
+
+def stencil_sweep2d_f32(in_, out, coeffs, radius, iters, nx=None, ny=None, stream=None):
+    nx, ny = _extents2d(in_, radius, nx, ny)
+    cp, _keep = _coeffs(coeffs)
+    return _check(_lib.stencil_sweep2d_f32(_addr(in_), _addr(out), nx, ny, cp, radius, iters,
+                                           _stream(stream, in_, out)))
+
+
+def residual_norm2d_f64(u, coeffs, radius, b=None, nx=None, ny=None, stream=None) -> float:
+    nx, ny = _extents2d(u, radius, nx, ny)
+    cp, _keep = _coeffs(coeffs)
+    out = ctypes.c_double(0.0)
+    _check(_lib.residual_norm2d_f64(_addr(u), _addr(b), nx, ny, cp, radius, ctypes.byref(out),
+                                    _stream(stream, u, b)))
+    return out.value
+
+
+def residual_norm2d_f32(u, coeffs, radius, b=None, nx=None, ny=None, stream=None) -> float:
+    nx, ny = _extents2d(u, radius, nx, ny)
+    cp, _keep = _coeffs(coeffs)
+    out = ctypes.c_double(0.0)
+    _check(_lib.residual_norm2d_f32(_addr(u), _addr(b), nx, ny, cp, radius, ctypes.byref(out),
+                                    _stream(stream, u, b)))
     return out.value
 
 

@@ -290,6 +290,71 @@ static int residual_impl(const T* u, const T* b, i64 nx, i64 ny, i64 nz, const d
   return st.finish();
 }
 
+// ------------------------------------------------------------------- 2-D --
+static int check_grid2d(i64 nx, i64 ny, int r) {
+  if (r != 1 && r != 2) return einval("radius must be 1 or 2");
+  if (nx < 1 || ny < 1) return einval("interior extents must be >= 1");
+  const i64 lim = (i64)1 << 28;
+  if (nx > lim || ny > lim) return einval("extent too large");
+  if ((double)(nx + 2 * r) * (double)(ny + 2 * r) > 9.0e15) return einval("grid too large");
+  return STN_OK;
+}
+
+template <typename T>
+static int sweep2d_impl(T* in, T* out, i64 nx, i64 ny, const double* coeffs, int radius, i64 iters,
+                        void* stream) {
+  clear_error();
+  if (!in || !out) return einval("NULL grid");
+  if (!coeffs) return einval("NULL coeffs");
+  if (int rc = check_grid2d(nx, ny, radius)) return rc;
+  if (iters < 0) return einval("iters < 0");
+  const Grid2 g{nx, ny, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  if (overlap(in, out, bytes)) return einval("in and out overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  T *din, *dout;
+  const Plan2d p = plan_resident2d(g, sizeof(T));
+  const bool resident = use_resident2d(p);
+  if (int rc = st.add(in, bytes, true, iters > 1 && !resident, (void**)&din)) return rc;
+  if (int rc = st.add(out, bytes, false, true, (void**)&dout)) return rc;
+  if (iters == 0) {
+    STN_CUDA_TRY(cudaMemcpyAsync(dout, din, bytes, cudaMemcpyDeviceToDevice, s));
+  } else {
+    Workspace* ws;
+    if (int rc = get_workspace(s, 0, resident ? p.scratch : 0, &ws)) return rc;
+    if (int rc = sweep2d_run<T>(din, dout, g, coeffs, iters, (unsigned char*)ws->grid, p, resident, din, s))
+      return rc;
+  }
+  if (int rc = st.finish()) return rc;
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  return STN_OK;
+}
+
+template <typename T>
+static int residual2d_impl(const T* u, const T* b, i64 nx, i64 ny, const double* coeffs, int radius,
+                           double* norm_out, void* stream) {
+  clear_error();
+  if (!u) return einval("NULL grid");
+  if (!coeffs || !norm_out) return einval("NULL coeffs or norm_out");
+  if (int rc = check_grid2d(nx, ny, radius)) return rc;
+  const Grid2 g{nx, ny, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  T *du, *db;
+  if (int rc = st.add(u, bytes, true, false, (void**)&du)) return rc;
+  if (int rc = st.add(b, bytes, true, false, (void**)&db)) return rc;
+  const i64 nb = star2d_blocks(g);
+  Workspace* ws;
+  if (int rc = get_workspace(s, nb, 0, &ws)) return rc;
+  if (int rc = launch_star2d<T>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s)) return rc;
+  if (int rc = launch_finalize(ws->partials, nb, ws->scalars, nullptr, 0.0, s)) return rc;
+  if (int rc = read_scalars(ws, 0, 2, s)) return rc;
+  *norm_out = ws->host_scalars[1];
+  return st.finish();
+}
+
 // Scalars layout used by the solvers: [0] sum, [1] norm, [2] rel, [3] flag,
 // [4] max|rho|, [8] rhs sum of squares, [9] rhs norm.
 template <typename Step>
@@ -744,6 +809,18 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_star_chunks((int)value) != STN_OK) return einval("star_chunks must be in [0, 65535]");
     return STN_OK;
   }
+  if (strcmp(knob, "sweep2d_resident") == 0) {
+    if (tune_set_resident2d((int)value) != STN_OK) return einval("sweep2d_resident must be -1, 0 or 1");
+    return STN_OK;
+  }
+  if (strcmp(knob, "sweep2d_chunk") == 0) {
+    if (tune_set_chunk2d(value) != STN_OK) return einval("sweep2d_chunk must be in [1, 2^30]");
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_withhold_2d") == 0) {
+    if (tune_set_withhold2d((int)value) != STN_OK) return einval("fault_withhold_2d must be 0 or 1");
+    return STN_OK;
+  }
   if (strcmp(knob, "batch_engine") == 0) {
     if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0 or 1");
     return STN_OK;
@@ -784,6 +861,18 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "star_chunks") == 0) {
     *value = tune_get_star_chunks();
+    return STN_OK;
+  }
+  if (strcmp(knob, "sweep2d_resident") == 0) {
+    *value = tune_get_resident2d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "sweep2d_chunk") == 0) {
+    *value = tune_get_chunk2d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_withhold_2d") == 0) {
+    *value = tune_get_withhold2d();
     return STN_OK;
   }
   if (strcmp(knob, "batch_engine") == 0) {
@@ -930,6 +1019,26 @@ int jacobi_solve_varcoef_refined(const double* a, const double* f, double* u, in
                                  int64_t inner_sweeps, int64_t max_outer, stn_solve_info* info,
                                  void* stream) {
   return refined_impl(a, f, u, nx, ny, nz, w, radius, tol, inner_sweeps, max_outer, info, stream);
+}
+
+int stencil_sweep2d_f64(double* in, double* out, int64_t nx, int64_t ny, const double* coeffs,
+                        int radius, int64_t iters, void* stream) {
+  return sweep2d_impl<double>(in, out, nx, ny, coeffs, radius, iters, stream);
+}
+
+int stencil_sweep2d_f32(float* in, float* out, int64_t nx, int64_t ny, const double* coeffs,
+                        int radius, int64_t iters, void* stream) {
+  return sweep2d_impl<float>(in, out, nx, ny, coeffs, radius, iters, stream);
+}
+
+int residual_norm2d_f64(const double* u, const double* b, int64_t nx, int64_t ny,
+                        const double* coeffs, int radius, double* norm_out, void* stream) {
+  return residual2d_impl<double>(u, b, nx, ny, coeffs, radius, norm_out, stream);
+}
+
+int residual_norm2d_f32(const float* u, const float* b, int64_t nx, int64_t ny,
+                        const double* coeffs, int radius, double* norm_out, void* stream) {
+  return residual2d_impl<float>(u, b, nx, ny, coeffs, radius, norm_out, stream);
 }
 
 }  // extern "C"

@@ -89,6 +89,47 @@ int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coe
 template <typename T>
 int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s);
 
+// ---- two-dimensional star stencil (jacobi2d.cu) ------------------------------
+// Padded (ny+2r) x (nx+2r) grid, i fastest.
+struct Grid2 {
+  i64 nx, ny;
+  int r;
+  i64 NX() const { return nx + 2 * r; }
+  i64 NY() const { return ny + 2 * r; }
+  i64 count() const { return NX() * NY(); }
+};
+// Blocks of the per-sweep 2-D kernel (grid-stride over 32 x 8 tiles).
+constexpr i64 kJ2dBlocks = 152 * 8;
+// Launch plan of the shared-memory-resident 2-D sweep: `nblk` bands of at
+// most `nbmax` rows, one CTA each; `scratch` bytes of global exchange space
+// (counters, status, then the exchange slots at `xchg_off`).
+struct Plan2d {
+  bool ok = false;
+  int nblk = 0, nbmax = 0, threads = 0;
+  size_t smem = 0, xchg_off = 0, scratch = 0;
+};
+Plan2d plan_resident2d(const Grid2& g, size_t esize);
+bool use_resident2d(const Plan2d& p);
+// One launch of the per-sweep kernel: out = S u + b over the interior; in
+// residual modes one partial per block (star2d_blocks(g) entries).
+template <typename T>
+int launch_star2d(const T* u, const T* b, T* out, const Grid2& g, const double* coeffs,
+                  SweepMode mode, double* partials, cudaStream_t s);
+i64 star2d_blocks(const Grid2& g);
+// `iters` sweeps in -> out, resident (scratch of plan.scratch bytes) or per
+// sweep (ping-ponging through `pingpong`, which may be `in`).  Synchronises
+// `s`; STN_ETIMEOUT when a resident band's wait ran out.
+template <typename T>
+int sweep2d_run(const T* in, T* out, const Grid2& g, const double* coeffs, i64 iters,
+                unsigned char* scratch, const Plan2d& p, bool resident, T* pingpong,
+                cudaStream_t s);
+int tune_set_resident2d(int v);
+int tune_get_resident2d();
+int tune_set_chunk2d(i64 v);
+i64 tune_get_chunk2d();
+int tune_set_withhold2d(int v);
+int tune_get_withhold2d();
+
 // ---- temporal blocking (temporal.cu) -----------------------------------------
 // `depth` sweeps of the star stencil (no source term) in one pass: out =
 // S^depth(u) on the interior; bitwise equal to depth separate sweeps.

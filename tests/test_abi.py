@@ -95,6 +95,24 @@ def test_residual_and_solvers_reject_bad_arguments(lib):
                                           ctypes.byref(info), None) == lib.STN_EINVAL
 
 
+@pytest.mark.parametrize("nx,ny,r,iters,why", [
+    (0, 4, 1, 1, "extents"), (4, -1, 1, 1, "extents"), (4, 4, 3, 1, "radius"), (4, 4, 1, -1, "iters"),
+    (1 << 29, 4, 1, 1, "too large")])
+def test_sweep2d_rejects_bad_arguments(lib, nx, ny, r, iters, why):
+    cp, _k = c3(0.0, 0.25, 0.0)
+    for name in ("stencil_sweep2d_f64", "stencil_sweep2d_f32"):
+        assert call(lib, name, FAKE_A, FAKE_B, nx, ny, cp, r, iters, None) == lib.STN_EINVAL, (name, why)
+        assert "invalid argument" in lib.last_error()
+    L = lib.lib()
+    assert L.stencil_sweep2d_f64(None, FAKE_B, 4, 4, cp, 1, 1, None) == lib.STN_EINVAL
+    assert L.stencil_sweep2d_f64(FAKE_A, FAKE_A + 8 * 10, 4, 4, cp, 1, 1, None) == lib.STN_EINVAL
+    assert "overlap" in lib.last_error()
+    out = ctypes.c_double()
+    assert L.residual_norm2d_f64(None, None, 4, 4, cp, 1, ctypes.byref(out), None) == lib.STN_EINVAL
+    assert L.residual_norm2d_f32(FAKE_A, None, 4, 4, cp, 1, None, None) == lib.STN_EINVAL
+    assert L.residual_norm2d_f64(FAKE_A, None, 4, 0, cp, 1, ctypes.byref(out), None) == lib.STN_EINVAL
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     """The package refuses to import when libstencil.so is absent (no fallback)."""
     import shutil
@@ -119,7 +137,9 @@ def test_tuning_knobs(lib):
     assert lib.stencil_tune_get("star_variant") == 1
     lib.stencil_tune_set("star_variant", -1)
     for knob, good, bad in (("temporal_depth", 3, 5), ("batch_engine", 1, 2), ("solve_graph", 0, 2),
-                            ("star_chunks", 7, -1)):
+                            ("star_chunks", 7, -1),
+                            ("sweep2d_resident", 0, 2), ("sweep2d_chunk", 100, 0),
+                            ("fault_withhold_2d", 0, 2)):
         before = lib.stencil_tune_get(knob)
         with pytest.raises(lib.StencilError):
             lib.stencil_tune_set(knob, bad)
