@@ -113,6 +113,9 @@ int stencil_release_workspace(void);
  *                   1 resident whenever it fits.
  *   "sweep2d_chunk": most sweeps per resident 2-D launch (default 32768;
  *                   longer runs take several launches).
+ *   "sweep2d_tma":  resident 2-D sweeps fetch the neighbours' rows by bulk
+ *                   copy when a row's interior is a multiple of 16 bytes (1,
+ *                   default) or always through registers (0).
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
  *                   (temporal blocking): 0 automatic (currently 1), 1 off,
  *                   2..4 (double radius 2: at most 3).

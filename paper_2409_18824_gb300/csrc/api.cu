@@ -817,6 +817,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_chunk2d(value) != STN_OK) return einval("sweep2d_chunk must be in [1, 2^30]");
     return STN_OK;
   }
+  if (strcmp(knob, "sweep2d_tma") == 0) {
+    if (tune_set_tma2d((int)value) != STN_OK) return einval("sweep2d_tma must be 0 or 1");
+    return STN_OK;
+  }
   if (strcmp(knob, "fault_withhold_2d") == 0) {
     if (tune_set_withhold2d((int)value) != STN_OK) return einval("fault_withhold_2d must be 0 or 1");
     return STN_OK;
@@ -869,6 +873,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "sweep2d_chunk") == 0) {
     *value = tune_get_chunk2d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "sweep2d_tma") == 0) {
+    *value = tune_get_tma2d();
     return STN_OK;
   }
   if (strcmp(knob, "fault_withhold_2d") == 0) {

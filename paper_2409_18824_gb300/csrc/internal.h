@@ -105,6 +105,8 @@ constexpr i64 kJ2dBlocks = 152 * 8;
 // (counters, status, then the exchange slots at `xchg_off`).
 struct Plan2d {
   bool ok = false;
+  bool tma = false;     // halo rows by bulk copy (rows a multiple of 16 bytes)
+  int pad = 0, ns = 0;  // shared-memory row layout: column c of a row at pad + c, stride ns
   int nblk = 0, nbmax = 0, threads = 0;
   size_t smem = 0, xchg_off = 0, scratch = 0;
 };
@@ -129,6 +131,8 @@ int tune_set_chunk2d(i64 v);
 i64 tune_get_chunk2d();
 int tune_set_withhold2d(int v);
 int tune_get_withhold2d();
+int tune_set_tma2d(int v);
+int tune_get_tma2d();
 
 // ---- temporal blocking (temporal.cu) -----------------------------------------
 // `depth` sweeps of the star stencil (no source term) in one pass: out =

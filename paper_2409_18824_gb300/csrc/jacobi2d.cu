@@ -11,14 +11,13 @@
 //    a band of rows and keeps two copies of it (the current and the next
 //    iterate, each with R halo rows above and below) in shared memory for
 //    every sweep of the launch, so HBM is read and written once per launch.
-//    Per sweep a CTA computes its R top and R bottom rows first, copies them
-//    to a global exchange slot and publishes a counter (release store), then
-//    computes its inner rows while those rows travel through L2, and finally
-//    waits (acquire poll, bounded) for the neighbours' counters and copies
-//    their boundary rows into its halo rows.  Exchange slots alternate with
-//    the sweep parity: a CTA can only overwrite a slot two sweeps later, after
-//    both neighbours have published the sweep in between, i.e. after they
-//    have read it.
+//    Per sweep a CTA computes its inner rows (which need no neighbour data)
+//    while the neighbours' boundary rows of the previous sweep travel through
+//    L2 -- each warp waits for the neighbours' counters (acquire poll,
+//    bounded) half way through and loads its columns of those rows into
+//    registers -- then computes its R top and R bottom rows, storing them
+//    both to shared memory and to a global exchange slot, and publishes its
+//    counter (release store).  Two barriers per sweep.
 //  * per-sweep.  For grids that do not fit: a grid-stride kernel, one point
 //    per thread, ping-ponging through HBM; it also computes the residual.
 #include "arith.cuh"
@@ -77,18 +76,23 @@ __device__ bool wait_flag(const unsigned long long* flag, unsigned long long tar
   }
 }
 
-// Buffer rows [L0, L1) of a band (buffer row L = padded grid row jb + L),
-// interior columns: nxt = S(cur).  Threads walk the rows x columns rectangle
-// in row-major order without division.
+// ---- shared-memory band layout ----
+// A band buffer holds rows of the padded grid with row stride NS elements;
+// padded column c of buffer row L is at L*NS + P + c.  P and NS are chosen so
+// that every row's interior (column R) starts on a 16-byte boundary, which
+// lets the halo rows arrive by bulk copy.
+
+// Buffer rows [L0, L1), interior columns: nxt = S(cur).  Threads walk the
+// rows x columns rectangle in row-major order without division.
 template <typename T, int R, bool HAS_C0>
-__device__ __forceinline__ void band_rows(const T* cur, T* nxt, int NX, int nx, int L0, int L1,
+__device__ __forceinline__ void band_rows(const T* cur, T* nxt, int NS, int P, int nx, int L0, int L1,
                                           const Co2<T, R>& cf) {
   if (L1 <= L0) return;
   int l = L0 + (int)threadIdx.x / nx;
   int i = (int)threadIdx.x % nx;
   while (l < L1) {
-    const int o = l * NX + i + R;
-    nxt[o] = point2d<T, R, HAS_C0>(cur + o, NX, cf);
+    const int o = l * NS + P + R + i;
+    nxt[o] = point2d<T, R, HAS_C0>(cur + o, NS, cf);
     i += blockDim.x;
     while (i >= nx) {
       i -= nx;
@@ -97,93 +101,240 @@ __device__ __forceinline__ void band_rows(const T* cur, T* nxt, int NX, int nx, 
   }
 }
 
-// Copies `rows` rows of `nx` interior values between shared memory (row
-// stride NX, starting at column R) and a packed global slot.
-template <typename T, int R, bool TO_GLOBAL>
-__device__ __forceinline__ void copy_rows(T* sm, T* gl, int NX, int nx, int rows) {
-  const int n = rows * nx;
-  int l = (int)threadIdx.x / nx;
-  int i = (int)threadIdx.x % nx;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    if (TO_GLOBAL)
-      gl[c] = sm[l * NX + i + R];
-    else
-      sm[l * NX + i + R] = __ldcg(gl + c);
-    i += blockDim.x;
-    while (i >= nx) {
-      i -= nx;
-      l++;
-    }
-  }
-}
-
+// Boundary rows [L0, L1) of the next iterate, as band_rows, each value also
+// stored to this band's exchange slots: own rows [0, R) to `xtop`, own rows
+// [nb - R, nb) to `xbot` (either may be NULL).
 template <typename T, int R, bool HAS_C0>
+__device__ __forceinline__ void edge_rows(const T* cur, T* nxt, int NS, int P, int nx, int L0, int L1,
+                                          int nb, T* xtop, T* xbot, const Co2<T, R>& cf) {
+  if (L1 <= L0) return;
+  int l = L0 + (int)threadIdx.x / nx;
+  int i = (int)threadIdx.x % nx;
+  while (l < L1) {
+    const int o = l * NS + P + R + i;
+    const T v = point2d<T, R, HAS_C0>(cur + o, NS, cf);
+    nxt[o] = v;
+    const int own = l - R;
+    if (xtop && own < R) xtop[own * nx + i] = v;
+    if (xbot && own >= nb - R) xbot[(own - (nb - R)) * nx + i] = v;
+    i += blockDim.x;
+    while (i >= nx) {
+      i -= nx;
+      l++;
+    }
+  }
+}
+
+// ---- mbarrier and bulk-copy helpers (inline PTX) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the completion of the mbarrier phase of parity `parity`.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(m, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(m))
+      : "memory");
+}
+
+// Most interior columns one thread covers in a band row when the halo rows
+// arrive through registers: that path requires nx <= kJ2Cols * blockDim.x.
+constexpr int kJ2Cols = 4;
+
+// One sweep of a band (iterate s in `cur` -> iterate s+1 in `nxt`):
+//   1. first half of the inner rows (they read only the band's own rows);
+//   2. the neighbours' boundary rows of iterate s (exchange slots of parity
+//      s-1, counter s) are fetched: with TMA, thread 0 alone waits for the
+//      counters and issues bulk copies into cur's halo rows, completing on an
+//      mbarrier, so only its warp pauses; without (rows not a multiple of 16
+//      bytes), every warp waits and loads its columns into registers;
+//   3. second half of the inner rows while the rows travel;
+//   4. barrier; the halo rows are in place (mbarrier wait, or register
+//      stores before the barrier);
+//   5. boundary rows of iterate s+1, written to nxt and to this band's
+//      exchange slots of parity s; barrier; thread 0 publishes counter s+1.
+// A band rewrites a slot of parity s only in sweep s+2, after both
+// neighbours have published s+1 -- which they do after reading the slot.
+template <typename T, int R, bool HAS_C0, bool TMA>
 __global__ void __launch_bounds__(1024, 1)
-    j2d_resident_kernel(const T* src, T* dst, int nx, int ny, int NX, int nbmax, int sweeps,
-                        Co2<T, R> cf, T* __restrict__ xchg, unsigned long long* __restrict__ flags,
-                        int* __restrict__ status, long long spin_limit, int withhold_last) {
-  extern __shared__ __align__(16) unsigned char j2_smem[];
+    j2d_resident_kernel(const T* src, T* dst, int nx, int ny, int NX, int NS, int P, int nbmax,
+                        int sweeps, Co2<T, R> cf, T* __restrict__ xchg,
+                        unsigned long long* __restrict__ flags, int* __restrict__ status,
+                        long long spin_limit, int withhold_last) {
+  extern __shared__ __align__(128) unsigned char j2_smem[];
+  __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ int s_abort;
   const int nblk = gridDim.x, b = blockIdx.x;
   const int jb = (int)(((long long)b * ny) / nblk);
-  const int nb = (int)(((long long)(b + 1) * ny) / nblk) - jb;  // own rows (>= R)
+  const int nb = (int)(((long long)(b + 1) * ny) / nblk) - jb;  // own rows (>= R unless nblk == 1)
   const int LR = nb + 2 * R;
   T* buf0 = reinterpret_cast<T*>(j2_smem);
-  T* buf1 = buf0 + (size_t)(nbmax + 2 * R) * NX;
-  if (threadIdx.x == 0) s_abort = ld_volatile_i32(status);
+  T* buf1 = buf0 + (size_t)(nbmax + 2 * R) * NS;
+  if (threadIdx.x == 0) {
+    s_abort = ld_volatile_i32(status);
+    if (TMA) {
+      mbar_init(&s_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+  }
   __syncthreads();
   if (s_abort) return;  // an earlier launch of this call timed out
 
   // both copies <- padded rows [jb, jb + LR) of src, full width
-  for (int c = threadIdx.x; c < LR * NX; c += blockDim.x) {
-    const T v = src[(size_t)jb * NX + c];
-    buf0[c] = v;
-    buf1[c] = v;
-  }
+  for (int L = 0; L < LR; L++)
+    for (int c = threadIdx.x; c < NX; c += blockDim.x) {
+      const T v = src[(size_t)(jb + L) * NX + c];
+      buf0[L * NS + P + c] = v;
+      buf1[L * NS + P + c] = v;
+    }
   __syncthreads();
 
   const bool up = b > 0, down = b + 1 < nblk;
   const size_t slot = (size_t)R * nx;  // one side's rows in an exchange slot
   const bool publish = !(withhold_last && b == nblk - 1);
+  const bool has_inner = nb > 2 * R;
+  const int mid = has_inner ? 2 * R + (nb - 2 * R) / 2 : 2 * R;
+  const int lane = threadIdx.x & 31;
+  unsigned phase = 0;
   for (int s = 0; s < sweeps; s++) {
-    const T* cur = (s & 1) ? buf1 : buf0;
+    T* cur = (s & 1) ? buf1 : buf0;
     T* nxt = (s & 1) ? buf0 : buf1;
-    T* xs = xchg + (size_t)(s & 1) * nblk * 2 * slot;  // this sweep's exchange slots
-    // boundary rows first: own rows [0, R) and [nb - R, nb) = buffer rows
-    // [R, 2R) and [nb, nb + R) (all own rows when the band is that thin)
-    if (nb <= 2 * R) {
-      band_rows<T, R, HAS_C0>(cur, nxt, NX, nx, R, R + nb, cf);
-    } else {
-      band_rows<T, R, HAS_C0>(cur, nxt, NX, nx, R, 2 * R, cf);
-      band_rows<T, R, HAS_C0>(cur, nxt, NX, nx, nb, nb + R, cf);
+    if (has_inner) band_rows<T, R, HAS_C0>(cur, nxt, NS, P, nx, 2 * R, mid, cf);
+    const T* xp = xchg + (size_t)((s - 1) & 1) * nblk * 2 * slot;
+    const T* from_up = up ? xp + (size_t)(2 * (b - 1) + 1) * slot : xp;  // band b-1's bottom rows
+    const T* from_dn = down ? xp + (size_t)(2 * (b + 1)) * slot : xp;    // band b+1's top rows
+    T hv[TMA ? 1 : 2 * R * kJ2Cols];
+    bool ok = true;
+    if (s > 0) {
+      if (TMA) {
+        if (threadIdx.x == 0) {
+          if (up) ok = wait_flag(flags + b - 1, (unsigned long long)s, status, spin_limit);
+          if (ok && down) ok = wait_flag(flags + b + 1, (unsigned long long)s, status, spin_limit);
+          if (ok) {
+            // the rows were written by other SMs' ordinary stores: order them
+            // before this thread's bulk (async-proxy) reads, and this CTA's
+            // earlier reads of the halo rows before the bulk writes
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const unsigned bytes = (unsigned)(nx * sizeof(T));
+            mbar_arrive_expect_tx(&s_mbar, (unsigned)((up ? R : 0) + (down ? R : 0)) * bytes);
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+              if (up) bulk_g2s(cur + r * NS + P + R, from_up + (size_t)r * nx, bytes, &s_mbar);
+              if (down) bulk_g2s(cur + (R + nb + r) * NS + P + R, from_dn + (size_t)r * nx, bytes, &s_mbar);
+            }
+          } else {
+            mbar_arrive_expect_tx(&s_mbar, 0);  // completes the phase: nobody waits on it
+            s_abort = 1;
+          }
+        }
+      } else {
+        if (lane == 0) {
+          if (up) ok = wait_flag(flags + b - 1, (unsigned long long)s, status, spin_limit);
+          if (ok && down) ok = wait_flag(flags + b + 1, (unsigned long long)s, status, spin_limit);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < kJ2Cols; k++) {
+            const int i = (int)threadIdx.x + k * (int)blockDim.x;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+              hv[r * kJ2Cols + k] = (up && i < nx) ? __ldcg(from_up + r * nx + i) : T(0);
+              hv[(R + r) * kJ2Cols + k] = (down && i < nx) ? __ldcg(from_dn + r * nx + i) : T(0);
+            }
+          }
+        } else {
+          s_abort = 1;
+        }
+      }
+    }
+    if (has_inner) band_rows<T, R, HAS_C0>(cur, nxt, NS, P, nx, mid, nb, cf);
+    if (!TMA && s > 0 && ok) {
+#pragma unroll
+      for (int k = 0; k < kJ2Cols; k++) {
+        const int i = (int)threadIdx.x + k * (int)blockDim.x;
+        if (i < nx) {
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            if (up) cur[r * NS + P + R + i] = hv[r * kJ2Cols + k];
+            if (down) cur[(R + nb + r) * NS + P + R + i] = hv[(R + r) * kJ2Cols + k];
+          }
+        }
+      }
     }
     __syncthreads();
-    if (up) copy_rows<T, R, true>(nxt + R * NX, xs + (size_t)(2 * b) * slot, NX, nx, R);
-    if (down) copy_rows<T, R, true>(nxt + nb * NX, xs + (size_t)(2 * b + 1) * slot, NX, nx, R);
+    if (s_abort) return;
+    if (TMA && s > 0) {
+      const bool arrived = mbar_wait(&s_mbar, phase & 1, spin_limit) ||
+                           mbar_wait(&s_mbar, phase & 1, spin_limit);  // once more before leaving
+      phase++;
+      if (!arrived) {
+        atomicExch(status, 1);
+        return;
+      }
+    }
+    T* xs = xchg + (size_t)(s & 1) * nblk * 2 * slot;
+    T* xtop = up ? xs + (size_t)(2 * b) * slot : nullptr;
+    T* xbot = down ? xs + (size_t)(2 * b + 1) * slot : nullptr;
+    if (has_inner) {
+      edge_rows<T, R, HAS_C0>(cur, nxt, NS, P, nx, R, 2 * R, nb, xtop, xbot, cf);
+      edge_rows<T, R, HAS_C0>(cur, nxt, NS, P, nx, nb, nb + R, nb, xtop, xbot, cf);
+    } else {
+      edge_rows<T, R, HAS_C0>(cur, nxt, NS, P, nx, R, R + nb, nb, xtop, xbot, cf);
+    }
     __syncthreads();
     if (threadIdx.x == 0 && publish && (up || down)) {
       __threadfence();
       st_release_u64(flags + b, (unsigned long long)(s + 1));
     }
-    // inner rows while the boundary rows travel
-    if (nb > 2 * R) band_rows<T, R, HAS_C0>(cur, nxt, NX, nx, 2 * R, nb, cf);
-    // neighbours' boundary rows -> this band's halo rows of the next iterate
+  }
+  // The neighbours read this band's rows of src at their start; in place
+  // (src == dst) they must be past it before the rows are overwritten: wait
+  // for their last counter.
+  if (up || down) {
     if (threadIdx.x == 0) {
       bool ok = true;
-      if (up) ok = wait_flag(flags + b - 1, (unsigned long long)(s + 1), status, spin_limit);
-      if (ok && down) ok = wait_flag(flags + b + 1, (unsigned long long)(s + 1), status, spin_limit);
+      if (up) ok = wait_flag(flags + b - 1, (unsigned long long)sweeps, status, spin_limit);
+      if (ok && down) ok = wait_flag(flags + b + 1, (unsigned long long)sweeps, status, spin_limit);
       s_abort = ok ? 0 : 1;
     }
     __syncthreads();
     if (s_abort) return;
-    if (up) copy_rows<T, R, false>(nxt, xs + (size_t)(2 * (b - 1) + 1) * slot, NX, nx, R);
-    if (down) copy_rows<T, R, false>(nxt + (R + nb) * NX, xs + (size_t)(2 * (b + 1)) * slot, NX, nx, R);
-    __syncthreads();
   }
   // own rows (and the grid's top / bottom halo rows for the end bands) -> dst
   const T* fin = (sweeps & 1) ? buf1 : buf0;
   const int L0 = b == 0 ? 0 : R, L1 = down ? R + nb : LR;
-  for (int c = L0 * NX + threadIdx.x; c < L1 * NX; c += blockDim.x) dst[(size_t)jb * NX + c] = fin[c];
+  for (int L = L0; L < L1; L++)
+    for (int c = threadIdx.x; c < NX; c += blockDim.x) dst[(size_t)(jb + L) * NX + c] = fin[L * NS + P + c];
 }
 
 // Per-sweep / residual kernel: 32 x 8 tiles, grid-stride over tiles; in
@@ -258,28 +409,36 @@ int launch_j2d_r(const T* u, const T* b, T* out, const Grid2& g, const double* c
 int g_resident2d = -1;          // -1 automatic, 0 never, 1 whenever it fits
 i64 g_chunk2d = 32768;          // sweeps per resident launch
 int g_withhold2d = 0;           // fault injection: last band never publishes
+int g_tma2d = 1;                // halo rows by bulk copy when rows are 16-byte multiples
 constexpr double kWait2dSeconds = 2.0;
 
-template <typename T, int R, bool HAS_C0>
+template <typename T, int R, bool HAS_C0, bool TMA>
 int launch_resident_t(const T* src, T* dst, const Grid2& g, const double* coeffs, const Plan2d& p,
                       int sweeps, unsigned char* scratch, cudaStream_t s) {
   Co2<T, R> cf;
   for (int d = 0; d <= R; d++) cf.c[d] = (T)coeffs[d];
-  auto kern = j2d_resident_kernel<T, R, HAS_C0>;
+  auto kern = j2d_resident_kernel<T, R, HAS_C0, TMA>;
   STN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
   unsigned long long* flags = reinterpret_cast<unsigned long long*>(scratch);
   int* status = reinterpret_cast<int*>(scratch + 8 * (size_t)p.nblk);
   T* xchg = reinterpret_cast<T*>(scratch + p.xchg_off);
   STN_CUDA_TRY(cudaMemsetAsync(flags, 0, 8 * (size_t)p.nblk, s));
-  int nx = (int)g.nx, ny = (int)g.ny, NX = (int)g.NX(), nbmax = p.nbmax;
+  int nx = (int)g.nx, ny = (int)g.ny, NX = (int)g.NX(), NS = p.ns, P = p.pad, nbmax = p.nbmax;
   int withhold = g_withhold2d;
   long long limit = (long long)(kWait2dSeconds * 2.07e9);
-  void* args[] = {(void*)&src, (void*)&dst, &nx,    &ny,    &NX,    &nbmax,   &sweeps,
-                  &cf,         &xchg,       &flags, &status, &limit, &withhold};
+  void* args[] = {(void*)&src, (void*)&dst, &nx,    &ny,    &NX,    &NS,     &P,     &nbmax,
+                  &sweeps,     &cf,         &xchg,  &flags, &status, &limit, &withhold};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(p.nblk), dim3(p.threads), args,
                                               p.smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(j2d_resident_kernel)");
   return STN_OK;
+}
+
+template <typename T, int R, bool HAS_C0>
+int launch_resident_c(const T* src, T* dst, const Grid2& g, const double* coeffs, const Plan2d& p,
+                      int sweeps, unsigned char* scratch, cudaStream_t s) {
+  return p.tma ? launch_resident_t<T, R, HAS_C0, true>(src, dst, g, coeffs, p, sweeps, scratch, s)
+               : launch_resident_t<T, R, HAS_C0, false>(src, dst, g, coeffs, p, sweeps, scratch, s);
 }
 
 template <typename T>
@@ -287,10 +446,10 @@ int launch_resident(const T* src, T* dst, const Grid2& g, const double* coeffs, 
                     int sweeps, unsigned char* scratch, cudaStream_t s) {
   const bool hc0 = coeffs[0] != 0.0;
   if (g.r == 1)
-    return hc0 ? launch_resident_t<T, 1, true>(src, dst, g, coeffs, p, sweeps, scratch, s)
-               : launch_resident_t<T, 1, false>(src, dst, g, coeffs, p, sweeps, scratch, s);
-  return hc0 ? launch_resident_t<T, 2, true>(src, dst, g, coeffs, p, sweeps, scratch, s)
-             : launch_resident_t<T, 2, false>(src, dst, g, coeffs, p, sweeps, scratch, s);
+    return hc0 ? launch_resident_c<T, 1, true>(src, dst, g, coeffs, p, sweeps, scratch, s)
+               : launch_resident_c<T, 1, false>(src, dst, g, coeffs, p, sweeps, scratch, s);
+  return hc0 ? launch_resident_c<T, 2, true>(src, dst, g, coeffs, p, sweeps, scratch, s)
+             : launch_resident_c<T, 2, false>(src, dst, g, coeffs, p, sweeps, scratch, s);
 }
 
 }  // namespace
@@ -310,7 +469,12 @@ Plan2d plan_resident2d(const Grid2& g, size_t esize) {
   p.nblk = (int)nblk;
   p.nbmax = (int)((g.ny + nblk - 1) / nblk);
   const i64 rows = (i64)p.nbmax + 2 * g.r;
-  const i64 smem = 2 * rows * g.NX() * (i64)esize;
+  // row layout: interior of every row 16-byte aligned (see the kernel)
+  const i64 per16 = 16 / (i64)esize;
+  p.pad = (int)((per16 - g.r % per16) % per16);
+  p.ns = (int)((p.pad + g.NX() + per16 - 1) / per16 * per16);
+  p.tma = (g.nx * (i64)esize) % 16 == 0 && g_tma2d != 0;
+  const i64 smem = 2 * rows * p.ns * (i64)esize;
   i64 thr = (i64)p.nbmax * g.nx;
   thr = (thr + 31) / 32 * 32;
   p.threads = (int)(thr > 1024 ? 1024 : thr);
@@ -318,7 +482,8 @@ Plan2d plan_resident2d(const Grid2& g, size_t esize) {
   p.xchg_off = ((size_t)8 * p.nblk + 8 + 255) / 256 * 256;
   p.scratch = p.xchg_off + (size_t)2 * p.nblk * 2 * g.r * g.nx * esize;
   // leave room for the kernel's static shared memory
-  p.ok = smem + 1024 <= optin && rows * g.NX() < ((i64)1 << 31);
+  p.ok = smem + 1024 <= optin && rows * p.ns < ((i64)1 << 31) &&
+         (p.tma || g.nx <= kJ2Cols * (i64)p.threads);
   return p;
 }
 
@@ -403,5 +568,11 @@ int tune_set_withhold2d(int v) {
   return STN_OK;
 }
 int tune_get_withhold2d() { return g_withhold2d; }
+int tune_set_tma2d(int v) {
+  if (v < 0 || v > 1) return STN_EINVAL;
+  g_tma2d = v;
+  return STN_OK;
+}
+int tune_get_tma2d() { return g_tma2d; }
 
 }  // namespace stn

@@ -40,11 +40,15 @@ def assert_bitwise(got, ref):
     assert bad.size == 0, f"{len(bad)} mismatches, first at {bad[0]}: {got[tuple(bad[0])]} vs {ref[tuple(bad[0])]}"
 
 
-@pytest.fixture(params=["auto", "hbm"])
+@pytest.fixture(params=["auto", "regs", "hbm"])
 def path(request, lib):
-    lib.stencil_tune_set("sweep2d_resident", -1 if request.param == "auto" else 0)
+    """auto: resident, halo rows by bulk copy where rows are 16-byte multiples;
+    regs: resident, halo rows through registers; hbm: per-sweep launches."""
+    lib.stencil_tune_set("sweep2d_resident", 0 if request.param == "hbm" else -1)
+    lib.stencil_tune_set("sweep2d_tma", 0 if request.param == "regs" else 1)
     yield request.param
     lib.stencil_tune_set("sweep2d_resident", -1)
+    lib.stencil_tune_set("sweep2d_tma", 1)
 
 
 SHAPES2D = [(1024, 1024), (37, 19), (1, 1), (1, 50), (50, 1), (130, 7), (2000, 3), (33, 1000),
@@ -97,8 +101,8 @@ def test_sweep2d_paper_length_eigenmode(lib, cuda):
     assert np.all(got[0] == 0) and np.all(got[-1] == 0) and np.all(got[:, 0] == 0) and np.all(got[:, -1] == 0)
 
 
-@pytest.mark.parametrize("chunk", [1, 7, 16])
-def test_sweep2d_several_launches(lib, cuda, chunk):
+@pytest.mark.parametrize("chunk", [1, 2, 7, 16])
+def test_sweep2d_several_launches(lib, cuda, path, chunk):
     """Runs longer than one resident launch continue in place, bit for bit."""
     try:
         lib.stencil_tune_set("sweep2d_chunk", chunk)
@@ -137,12 +141,14 @@ def test_residual2d_matches_oracle(lib, cuda, shape, r, c):
     assert abs(lib.residual_norm2d_f32(to_dev(u32), c, r) - nref) <= NORM_RTOL * nref
 
 
-def test_resident_wait_times_out_and_context_survives(lib, cuda):
+@pytest.mark.parametrize("tma", [1, 0])
+def test_resident_wait_times_out_and_context_survives(lib, cuda, tma):
     """The last band withholds its rows: its neighbour's bounded wait gives up
     (about 2 s), the call returns STN_ETIMEOUT, and the next call is correct."""
     u0 = si.uniform_interior2d(256, 400, 1, seed=11)
     d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
     try:
+        lib.stencil_tune_set("sweep2d_tma", tma)
         lib.stencil_tune_set("fault_withhold_2d", 1)
         with pytest.raises(lib.StencilError) as e:
             lib.stencil_sweep2d_f64(d_in, d_out, L5, 1, 50)
@@ -150,4 +156,5 @@ def test_resident_wait_times_out_and_context_survives(lib, cuda):
     finally:
         lib.stencil_tune_set("fault_withhold_2d", 0)
     lib.stencil_sweep2d_f64(d_in, d_out, L5, 1, 50)
+    lib.stencil_tune_set("sweep2d_tma", 1)
     assert_bitwise(to_host(d_out), oracle.stencil_sweep2d(u0, L5, 1, 50))
