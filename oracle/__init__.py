@@ -85,6 +85,8 @@ def _load():
                                                             ctypes.c_int, ctypes.c_double, _i64, _i64,
                                                             ctypes.POINTER(_i64), _dp]),
             "oracle_dense_solve": (ctypes.c_int, [_dp, _dp, _i64]),
+            "oracle_sum_f64": (ctypes.c_double, [_dp, _i64]),
+            "oracle_dot_f64": (ctypes.c_double, [_dp, _dp, _i64]),
             "oracle_sweep2d_f64": (None, [_dp, _dp, _dp, _i64, _i64, _dp, ctypes.c_int]),
             "oracle_sweep2d_f32": (None, [_fp, _fp, _fp, _i64, _i64, _fp, ctypes.c_int]),
             "oracle_stencil_sweep2d_f64": (ctypes.c_int, [_dp, _dp, _i64, _i64, _dp, ctypes.c_int, _i64]),
@@ -193,6 +195,25 @@ def jacobi_solve(b: np.ndarray | None, u0: np.ndarray, coeffs, r: int, tol: floa
     if st < 0:
         raise MemoryError("oracle allocation failed")
     return u, it.value, rel.value, st
+
+
+# -------------------------------------------------------- sum, dotproduct --
+def _vec(a):
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("oracle wants a C-contiguous float64 array")
+    return a
+
+
+def sum_(x: np.ndarray) -> float:
+    """The sum intrinsic: sequential add-reduction from zero (Sec. 5.3)."""
+    return _load().oracle_sum_f64(_ptr(_vec(x), ctypes.c_double), x.size)
+
+
+def dot(x: np.ndarray, y: np.ndarray) -> float:
+    """The dotproduct intrinsic: sequential add-reduction of x_i * y_i from zero."""
+    if x.size != y.size:
+        raise ValueError("length mismatch")
+    return _load().oracle_dot_f64(_ptr(_vec(x), ctypes.c_double), _ptr(_vec(y), ctypes.c_double), x.size)
 
 
 # ------------------------------------------------------------------- 2-D --

@@ -653,3 +653,21 @@ double oracle_residual_norm2d_f32(const float* u, const float* b, i64 nx, i64 ny
   free(t);
   return sqrt(sum);
 }
+
+/* ---------------------------------------------------------------------------
+ * Array intrinsics of Sec. 5.4 (Table 3): `sum` of a double array and
+ * `dotproduct` of two double vectors, each the linalg.reduce of Sec. 5.3 /
+ * Listing 8 -- an accumulator initialised to zero and an add combiner applied
+ * to the elements in order (for the dot product, to the products).
+ * ------------------------------------------------------------------------- */
+double oracle_sum_f64(const double* x, i64 n) {
+  double acc = 0.0;
+  for (i64 i = 0; i < n; i++) acc = acc + x[i];
+  return acc;
+}
+
+double oracle_dot_f64(const double* x, const double* y, i64 n) {
+  double acc = 0.0;
+  for (i64 i = 0; i < n; i++) acc = acc + x[i] * y[i];
+  return acc;
+}

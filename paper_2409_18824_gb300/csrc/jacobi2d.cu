@@ -82,12 +82,22 @@ __device__ bool wait_flag(const unsigned long long* flag, unsigned long long tar
 // that every row's interior (column R) starts on a 16-byte boundary, which
 // lets the halo rows arrive by bulk copy.
 
-// Buffer rows [L0, L1), interior columns: nxt = S(cur).  Threads walk the
-// rows x columns rectangle in row-major order without division.
+// Buffer rows [L0, L1), interior columns: nxt = S(cur).  Narrow rows: the
+// threads walk the rows x columns rectangle in row-major order without
+// division, so that no thread idles.
 template <typename T, int R, bool HAS_C0>
 __device__ __forceinline__ void band_rows(const T* cur, T* nxt, int NS, int P, int nx, int L0, int L1,
                                           const Co2<T, R>& cf) {
   if (L1 <= L0) return;
+  if (nx >= (int)blockDim.x) {  // rows at least a block wide: plain row loop
+#pragma unroll 2
+    for (int l = L0; l < L1; l++)
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int o = l * NS + P + R + i;
+        nxt[o] = point2d<T, R, HAS_C0>(cur + o, NS, cf);
+      }
+    return;
+  }
   int l = L0 + (int)threadIdx.x / nx;
   int i = (int)threadIdx.x % nx;
   while (l < L1) {
