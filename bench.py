@@ -479,6 +479,150 @@ def run_reference2d(args):
     }), flush=True)
 
 
+# ------------------------------------ the paper's sum / dotproduct runs ----
+INTRINSICS = {
+    "sum": dict(n=32768 * 32768, seed=8, paper_s=1.63, flang_s=1.65,
+                desc="the paper's sum intrinsic: sum of a 32768 x 32768 FP64 array (8.6 GB), U[0,1) seed 8"),
+    "dot": dict(n=1 << 27, seed=9, paper_s=0.81, flang_s=2.70,
+                desc="the paper's dotproduct intrinsic: two 2^27-element (134 M) FP64 vectors, N(0,1) seeds 9, 10"),
+}
+
+
+def intrinsic_inputs(kind):
+    w = INTRINSICS[kind]
+    x = si.rng(w["seed"]).random(w["n"]) if kind == "sum" else si.rng(w["seed"]).standard_normal(w["n"])
+    y = None if kind == "sum" else si.rng(w["seed"] + 1).standard_normal(w["n"])
+    return x, y
+
+
+def run_intrinsic(args, kind):
+    """One step = one sum (or dot product) over the whole array, read from HBM."""
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    w = INTRINSICS[kind]
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    x, y = intrinsic_inputs(kind)
+    dx = torch.from_numpy(x).to(dev)
+    dy = None if y is None else torch.from_numpy(y).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = w["n"]
+    nbytes = 8.0 * n * (1 if kind == "sum" else 2)
+
+    def step():
+        return stn.reduce_sum_f64(dx) if kind == "sum" else stn.dot_f64(dx, dy)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    vals = []
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            vals.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / args.steps / 1e3
+    value = nbytes * ws / sec / 1e9
+    # e2e: the arrays from pinned host memory through the C ABI every step
+    hx = torch.from_numpy(x).pin_memory()
+    hy = None if y is None else torch.from_numpy(y).pin_memory()
+    hxn, hyn = hx.numpy(), (None if hy is None else hy.numpy())
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        stn.reduce_sum_f64(hxn) if kind == "sum" else stn.dot_f64(hxn, hyn)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    peaks, peak_kind = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    note = "timed through the synchronous call: kernel + fixed-order finalize + 8-byte read"
+    if kind == "sum":
+        # one double add per element: bound by the FP64 pipe, not HBM
+        fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        achieved = n / sec / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None, "traffic_unit": "bytes per launch",
+                    "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
+                    "hbm_achieved_gbs": nbytes / sec / 1e9, "hbm_peak_gbs": hbm_peak,
+                    "hbm_frac": nbytes / sec / 1e9 / hbm_peak, "hbm_peak_kind": peak_kind,
+                    "kernel": "sum_kernel", "kernel_ms": ms / args.steps, "note": note}
+    else:
+        roofline = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": nbytes / sec / 1e9 / hbm_peak, "traffic": None, "traffic_unit": "bytes per launch",
+                    "peak_kind": peak_kind, "kernel": "vec_reduce_kernel<true>", "kernel_ms": ms / args.steps,
+                    "note": note}
+    out = {
+        "metric": f"GB/s ({w['desc']})", "value": value, "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "elements": n, "bytes_per_step": nbytes,
+                   "l2": "inputs larger than L2, no flush", "parallelism": "replicas" if ws > 1 else "single"},
+        "seconds_per_run": sec,
+        "paper_seconds": {"mlir_flow_1core": w["paper_s"], "flang_v20_1core": w["flang_s"]},
+        "e2e": {"value": nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": 8},
+        "gpu_launches": args.steps * 2,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "result": vals[-1],
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            val, t = cpu_sample_intrinsic(kind, x, y)
+            out["cpu_baseline"] = {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"the whole workload once, plain C oracle, one thread ({t:.2f} s)"}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_sample_intrinsic(kind, x, y):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.sum_(x) if kind == "sum" else oracle.dot(x, y)
+    t = time.perf_counter() - t0
+    return 8.0 * x.size * (1 if kind == "sum" else 2) / t / 1e9, t
+
+
+def run_reference_intrinsic(args, kind):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = INTRINSICS[kind]
+    x, y = intrinsic_inputs(kind)
+    for _ in range(args.warmup):
+        cpu_sample_intrinsic(kind, x, y)
+    times = [cpu_sample_intrinsic(kind, x, y)[1] for _ in range(args.steps)]
+    total = sum(times)
+    nbytes = 8.0 * w["n"] * (1 if kind == "sum" else 2)
+    value = nbytes * args.steps / total / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": f"GB/s ({w['desc']})", "value": value, "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "elements": w["n"], "parallelism": "single"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: the whole workload, plain C oracle, one thread"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 # ------------------------------------------------------- batched solves ----
 def batch_problems(count, seed_sizes=4, seed_rhs=5):
     """Per-axis sizes log-uniform in [16, 128] (PCG64 seed 4); right-hand sides
@@ -796,7 +940,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d"])
+    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "sum", "dot"])
     ap.add_argument("--requests", type=int, default=48, help="serving workload: requests per trace")
     ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8, 1.1],
                     help="serving workload: offered loads as fractions of the measured capacity")
@@ -840,6 +984,12 @@ def main():
                               "implemented for the sweep workloads"}))
             return
         run_batched(args)
+        return
+    if args.workload in INTRINSICS:
+        if args.impl == "reference":
+            run_reference_intrinsic(args, args.workload)
+        else:
+            run_intrinsic(args, args.workload)
         return
     if args.workload == "jacobi2d":
         if args.impl == "reference":

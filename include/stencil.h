@@ -467,6 +467,25 @@ int residual_norm2d_f64(const double* u, const double* b, int64_t nx, int64_t ny
 int residual_norm2d_f32(const float* u, const float* b, int64_t nx, int64_t ny,
                         const double* coeffs, int radius, double* norm_out, void* stream);
 
+/*
+ * reduce_sum_f64 / dot_f64 -- the Fortran `sum` and `dotproduct` intrinsics
+ * (Sec. 5.4, Table 3: the sum of a 32768 x 32768 double array, the dot
+ * product of two 134-million-element double vectors), i.e. the linalg.reduce
+ * of Sec. 5.3 / Listing 8 with a zero initial value and an add combiner.
+ *   x, y   n contiguous doubles, device or host, 8-byte aligned (read only);
+ *          a 2-D array is summed as its n = nx*ny elements.
+ *   n      >= 0 (n == 0 gives 0).
+ *   out    HOST double receiving the result.  The call synchronises `stream`.
+ * The order of the additions is fixed for given n and for the operands'
+ * offsets modulo 16 bytes (blocked partial sums added in index order), so
+ * the result is reproducible; it differs from a left-to-right sum only by
+ * rounding (dot products use fused multiply-adds).
+ * Errors: STN_EINVAL (NULL out or array with n > 0, n < 0, misaligned
+ * pointer), STN_ENOMEM, STN_ECUDA.
+ */
+int reduce_sum_f64(const double* x, int64_t n, double* out, void* stream);
+int dot_f64(const double* x, const double* y, int64_t n, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

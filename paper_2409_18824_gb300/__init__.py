@@ -104,6 +104,8 @@ SIGNATURES = {
     "residual_norm_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f64_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
+    "reduce_sum_f64": (_int, [_vp, _i64, _dp, _vp]),
+    "dot_f64": (_int, [_vp, _vp, _i64, _dp, _vp]),
     "stencil_sweep2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_sweep2d_f32": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _vp]),
     "residual_norm2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _dp, _vp]),
@@ -263,6 +265,26 @@ def residual_norm_f64_noalloc(u, coeffs, radius, b=None, nx=None, ny=None, nz=No
     out = ctypes.c_double(0.0)
     _check(_lib.residual_norm_f64_noalloc(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
                                           _stream(stream, u, b)))
+    return out.value
+
+
+def _numel(a, n):
+    if n is not None:
+        return n
+    return int(a.numel()) if hasattr(a, "numel") else int(a.size)
+
+
+def reduce_sum_f64(x, n=None, stream=None) -> float:
+    """Sum of the n contiguous doubles of x (the sum intrinsic)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.reduce_sum_f64(_addr(x), _numel(x, n), ctypes.byref(out), _stream(stream, x)))
+    return out.value
+
+
+def dot_f64(x, y, n=None, stream=None) -> float:
+    """Dot product of two contiguous double vectors (the dotproduct intrinsic)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.dot_f64(_addr(x), _addr(y), _numel(x, n), ctypes.byref(out), _stream(stream, x, y)))
     return out.value
 
 

@@ -355,6 +355,32 @@ static int residual2d_impl(const T* u, const T* b, i64 nx, i64 ny, const double*
   return st.finish();
 }
 
+// ------------------------------------------------------ sum, dotproduct --
+static int vec_reduce_impl(const double* x, const double* y, i64 n, double* out, void* stream) {
+  clear_error();
+  if (!out) return einval("NULL out");
+  if (n < 0) return einval("n < 0");
+  if (n > ((i64)1 << 40)) return einval("n too large");
+  if (n > 0 && !x) return einval("NULL array");
+  if (((uintptr_t)x & 7) || ((uintptr_t)y & 7)) return einval("arrays must be 8-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  const double *dx = nullptr, *dy = nullptr;
+  if (n > 0) {
+    if (int rc = st.add(x, (size_t)n * 8, true, false, (void**)&dx)) return rc;
+    if (y)
+      if (int rc = st.add(y, (size_t)n * 8, true, false, (void**)&dy)) return rc;
+  }
+  const i64 nb = vec_reduce_blocks(n);
+  Workspace* ws;
+  if (int rc = get_workspace(s, nb, 0, &ws)) return rc;
+  if (int rc = launch_vec_reduce(dx, y ? dy : nullptr, n, ws->partials, s)) return rc;
+  if (int rc = launch_finalize(ws->partials, nb, ws->scalars, nullptr, 0.0, s)) return rc;
+  if (int rc = read_scalars(ws, 0, 1, s)) return rc;
+  *out = ws->host_scalars[0];
+  return st.finish();
+}
+
 // Scalars layout used by the solvers: [0] sum, [1] norm, [2] rel, [3] flag,
 // [4] max|rho|, [8] rhs sum of squares, [9] rhs norm.
 template <typename Step>
@@ -1047,6 +1073,18 @@ int residual_norm2d_f64(const double* u, const double* b, int64_t nx, int64_t ny
 int residual_norm2d_f32(const float* u, const float* b, int64_t nx, int64_t ny,
                         const double* coeffs, int radius, double* norm_out, void* stream) {
   return residual2d_impl<float>(u, b, nx, ny, coeffs, radius, norm_out, stream);
+}
+
+int reduce_sum_f64(const double* x, int64_t n, double* out, void* stream) {
+  return vec_reduce_impl(x, nullptr, n, out, stream);
+}
+
+int dot_f64(const double* x, const double* y, int64_t n, double* out, void* stream) {
+  if (n > 0 && !y) {
+    clear_error();
+    return einval("NULL array");
+  }
+  return vec_reduce_impl(x, y, n, out, stream);
 }
 
 }  // extern "C"

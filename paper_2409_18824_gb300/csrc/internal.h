@@ -134,6 +134,12 @@ int tune_get_withhold2d();
 int tune_set_tma2d(int v);
 int tune_get_tma2d();
 
+// ---- sum / dotproduct intrinsics (intrinsics.cu) ---------------------------
+// Number of per-block partials launch_vec_reduce writes for n elements.
+i64 vec_reduce_blocks(i64 n);
+// Partials of sum(x[0..n)) (y == NULL) or sum(x[i]*y[i]); fixed order.
+int launch_vec_reduce(const double* x, const double* y, i64 n, double* partials, cudaStream_t s);
+
 // ---- temporal blocking (temporal.cu) -----------------------------------------
 // `depth` sweeps of the star stencil (no source term) in one pass: out =
 // S^depth(u) on the interior; bitwise equal to depth separate sweeps.

@@ -113,6 +113,18 @@ def test_sweep2d_rejects_bad_arguments(lib, nx, ny, r, iters, why):
     assert L.residual_norm2d_f64(FAKE_A, None, 4, 0, cp, 1, ctypes.byref(out), None) == lib.STN_EINVAL
 
 
+def test_sum_and_dot_reject_bad_arguments(lib):
+    L = lib.lib()
+    out = ctypes.c_double()
+    assert L.reduce_sum_f64(None, 10, ctypes.byref(out), None) == lib.STN_EINVAL
+    assert L.reduce_sum_f64(FAKE_A, -1, ctypes.byref(out), None) == lib.STN_EINVAL
+    assert L.reduce_sum_f64(FAKE_A, 10, None, None) == lib.STN_EINVAL
+    assert L.reduce_sum_f64(FAKE_A + 4, 10, ctypes.byref(out), None) == lib.STN_EINVAL
+    assert "aligned" in lib.last_error()
+    assert L.dot_f64(FAKE_A, None, 10, ctypes.byref(out), None) == lib.STN_EINVAL
+    assert L.dot_f64(FAKE_A, FAKE_B + 2, 10, ctypes.byref(out), None) == lib.STN_EINVAL
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     """The package refuses to import when libstencil.so is absent (no fallback)."""
     import shutil
