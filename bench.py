@@ -851,16 +851,51 @@ def run_serving(args):
                 srv.release(t)
             return time.perf_counter() - t0, lat, status
 
+    def run_trace_per_request(arrivals):
+        """The plain comparison: one double Jacobi solve per request, in arrival
+        order, each through jacobi_solve_f64 (its own CUDA-graph solve)."""
+        import queue
+        q = queue.Queue()
+        done = [None] * len(arrivals)
+        status = [None] * len(arrivals)
+
+        def worker():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                i, t_sub = item
+                d_b = torch.from_numpy(rhss[i]).cuda()
+                d_u = torch.zeros_like(d_b)
+                rc, info = stn.jacobi_solve_f64(d_b, d_u, si.LAPLACE7, 1, 1e-8, 10 ** 7, 50)
+                d_u.cpu()
+                done[i] = time.perf_counter() - t_sub
+                status[i] = info["status"]
+
+        th = threading.Thread(target=worker)
+        th.start()
+        t0 = time.perf_counter()
+        for i, at in enumerate(arrivals):
+            d = at - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            q.put((i, time.perf_counter()))
+        q.put(None)
+        th.join()
+        return time.perf_counter() - t0, done, status
+
+    trace = run_trace_per_request if args.per_request else run_trace
     n = len(rhss)
     # capacity: every request at t = 0
     with ClockSampler(local) as clk:
-        span, lat, status = run_trace([0.0] * n)
+        span, lat, status = trace([0.0] * n)
         capacity = n / span
         loads = []
-        for frac in args.loads:
-            rate = frac * capacity
+        rates = args.rates or [frac * capacity for frac in args.loads]
+        for k, rate in enumerate(rates):
+            frac = rate / capacity
             arr = si.poisson_arrival_times(n, rate, seed=8).tolist()
-            span_l, lat_l, st_l = run_trace(arr)
+            span_l, lat_l, st_l = trace(arr)
             loads.append({"offered_frac": frac, "offered_per_s": rate, "solves_per_s": n / span_l,
                           "p50_s": float(np.percentile(lat_l, 50)), "p99_s": float(np.percentile(lat_l, 99)),
                           "converged": int(sum(1 for x in st_l if x == 0))})
@@ -868,9 +903,13 @@ def run_serving(args):
         "metric": "serving solves/s and p50/p99 latency (Poisson arrivals, sizes log-U[32,256], tol 1e-8)",
         "value": capacity, "unit": "solves/s", "n_gpus": ws, "steps": 1, "warmup": 0,
         "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64 refined" if refined else "f64", "data": "synthetic",
+        "dtype": "f64" if (args.per_request or not refined) else "f32+f64 refined", "data": "synthetic",
         "config": {"workload": f"{n} Poisson solve requests, per-axis sizes log-uniform in [32,256] (seed 6), "
-                               f"rhs N(0,1), tol 1e-8, 40 GiB admission budget, continuous batching",
+                               f"rhs N(0,1), tol 1e-8, " + (
+                                   "one double jacobi_solve_f64 per request in arrival order (the plain path)"
+                                   if args.per_request else
+                                   "40 GiB admission budget, continuous batching"
+                                   + ("" if refined else ", double Jacobi")),
                    "requests": n},
         "saturation": {"solves_per_s": capacity, "p50_s": float(np.percentile(lat, 50)),
                        "p99_s": float(np.percentile(lat, 99)), "converged": int(sum(1 for x in status if x == 0))},
@@ -945,6 +984,10 @@ def main():
     ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8, 1.1],
                     help="serving workload: offered loads as fractions of the measured capacity")
     ap.add_argument("--plain", action="store_true", help="serving workload: double Jacobi instead of refinement")
+    ap.add_argument("--per-request", action="store_true",
+                    help="serving workload: one double solve per request in arrival order (the plain comparison)")
+    ap.add_argument("--rates", type=float, nargs="*", default=None,
+                    help="serving workload: absolute offered rates (solves/s) instead of --loads fractions")
     ap.add_argument("--batch", type=int, default=2048, help="problems in the batched workload")
     ap.add_argument("--refined", action="store_true", help="batched workload: FP32 sweeps + FP64 refinement")
     ap.add_argument("--inner-tol", type=float, default=1e-2)

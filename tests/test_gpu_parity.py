@@ -222,6 +222,23 @@ def test_eigenmode_decay_1000_sweeps_128(lib, cuda):
     assert np.max(np.abs(got - expect)) / np.max(np.abs(expect)) < 1e-12
 
 
+def test_full_size_512_1000_sweeps_closed_form(lib, cuda):
+    """The bench workload's size and launch configuration (512^3, 1000 sweeps,
+    the default kernel and plan): the (1,1,1) sine mode ends at lambda^1000 times
+    the start, and the fused residual norm at |1 - lambda| lambda^1000 ||u0||
+    with ||u0||^2 = (513/2)^3."""
+    n = 512
+    u0 = si.sine_mode(n, n, n, 1)
+    lam = math.cos(math.pi / (n + 1))
+    d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+    lib.stencil_sweep_f64(d_in, d_out, L7, 1, 1000)
+    norm = lib.residual_norm_f64(d_out, L7, 1)
+    got = to_host(d_out)
+    assert np.max(np.abs(got - lam ** 1000 * u0)) <= 1e-12 * lam ** 1000
+    expect = abs(1 - lam) * lam ** 1000 * math.sqrt((n + 1) / 2) ** 3
+    assert abs(norm - expect) <= 1e-9 * expect
+
+
 # -------------------------------------------------------------- residuals --
 @pytest.mark.parametrize("shape", SHAPES[:5] + SHAPES[7:9])
 @pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
