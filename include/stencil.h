@@ -108,6 +108,11 @@ int stencil_release_workspace(void);
  *                   chunk; clamped to chunks of >= 4 planes).  Changes the
  *                   grid, never the iterates; the residual's partial sums
  *                   follow the grid, so its last bits may change.
+ *   "var_variant":  variable-coefficient kernels: -1 automatic (default: the
+ *                   register/shuffle column kernel that computes each face
+ *                   coefficient once), 0 the shared-memory plane kernel, 1
+ *                   column.  Bitwise the same results (face coefficients in
+ *                   the normal floating-point range).
  *   "sweep2d_resident": 2-D sweeps: -1 automatic (default: shared-memory
  *                   resident whenever the grid fits), 0 always through HBM,
  *                   1 resident whenever it fits.

@@ -634,7 +634,7 @@ static int var_residual_impl(const double* u, const double* a, const double* f, 
   if (int rc = st.add(u, bytes, true, false, (void**)&du)) return rc;
   if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
   if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
-  const ZPlan p = plan_var(g);
+  const ZPlan p = plan_var(g, 8);
   Workspace* ws;
   if (int rc = get_workspace(s, p.blocks(), 0, &ws)) return rc;
   if (int rc = launch_var<double>(du, da, df, nullptr, g, w, kVarResidual, ws->partials, nullptr, s)) return rc;
@@ -663,7 +663,7 @@ static int var_jacobi_impl(const double* a, const double* f, double* u, i64 nx, 
   if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
   if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
   if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
-  const ZPlan p = plan_var(g);
+  const ZPlan p = plan_var(g, 8);
   Workspace* ws;
   if (int rc = get_workspace(s, p.blocks(), bytes, &ws)) return rc;
   double* tmp = (double*)ws->grid;
@@ -719,7 +719,7 @@ static int refined_impl(const double* a, const double* f, double* u, i64 nx, i64
   if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
   if (int rc = st.add(a, bytes, true, false, (void**)&da)) return rc;
   if (int rc = st.add(f, bytes, true, false, (void**)&df)) return rc;
-  const ZPlan p = plan_var(g);
+  const ZPlan p = plan_var(g, 8);
   Workspace* ws;
   // partials: sums in [0, nb), maxima in [nb, 2nb)
   if (int rc = get_workspace(s, 2 * p.blocks(), bytes, &ws)) return rc;
@@ -843,6 +843,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_chunk2d(value) != STN_OK) return einval("sweep2d_chunk must be in [1, 2^30]");
     return STN_OK;
   }
+  if (strcmp(knob, "var_variant") == 0) {
+    if (tune_set_var_variant((int)value) != STN_OK) return einval("var_variant must be -1, 0 or 1");
+    return STN_OK;
+  }
   if (strcmp(knob, "sweep2d_tma") == 0) {
     if (tune_set_tma2d((int)value) != STN_OK) return einval("sweep2d_tma must be 0 or 1");
     return STN_OK;
@@ -899,6 +903,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "sweep2d_chunk") == 0) {
     *value = tune_get_chunk2d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "var_variant") == 0) {
+    *value = tune_get_var_variant();
     return STN_OK;
   }
   if (strcmp(knob, "sweep2d_tma") == 0) {

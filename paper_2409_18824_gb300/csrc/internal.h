@@ -189,7 +189,10 @@ int launch_interior_sumsq(const T* x, const Grid& g, double* partials, i64* npar
 
 // ---- variable coefficient (varcoef.cu) --------------------------------------
 enum VarMode { kVarSweep = 0, kVarApply = 1, kVarResidual = 2, kVarRefine = 3 };
-ZPlan plan_var(const Grid& g);
+ZPlan plan_var(const Grid& g, size_t esize);
+// Variable-coefficient kernel choice: -1 automatic (column), 0 plane, 1 column.
+int tune_set_var_variant(int v);
+int tune_get_var_variant();
 // kVarRefine writes rho = f - A u (double) into out's interior and per-block
 // partial sums of rho^2 / maxima of |rho| into partials / partials_max.
 template <typename T>

@@ -304,9 +304,17 @@ def test_jacobi_solve_not_converged_and_zero_iters(lib, cuda, solve_mode):
 VW = si.VARCOEF_W
 
 
-@pytest.mark.parametrize("shape", [(21, 13, 9), (40, 7, 12), (1, 3, 2)])
+@pytest.fixture(params=[-1, 0])
+def var_variant(request, lib):
+    """-1: the column kernel with shared face coefficients (default); 0: the plane kernel."""
+    lib.stencil_tune_set("var_variant", request.param)
+    yield request.param
+    lib.stencil_tune_set("var_variant", -1)
+
+
+@pytest.mark.parametrize("shape", [(21, 13, 9), (40, 7, 12), (1, 3, 2), (60, 37, 19), (29, 5, 33)])
 @pytest.mark.parametrize("R", [1, 2])
-def test_varcoef_apply_sweep_residual(lib, cuda, shape, R):
+def test_varcoef_apply_sweep_residual(lib, cuda, var_variant, shape, R):
     nx, ny, nz = shape
     a = si.uniform_full(nx, ny, nz, R, seed=3)
     f = si.normal_interior(nx, ny, nz, R, seed=5)
@@ -335,7 +343,7 @@ def test_varcoef_apply_sweep_residual(lib, cuda, shape, R):
     assert abs(lib.varcoef_residual_norm_f64(to_dev(u), to_dev(a), to_dev(f), w, R) - nref) <= NORM_RTOL * nref
 
 
-def test_varcoef_jacobi_solve_matches_oracle(lib, cuda):
+def test_varcoef_jacobi_solve_matches_oracle(lib, cuda, var_variant):
     nx, ny, nz, R = 14, 9, 11, 2
     a = si.uniform_full(nx, ny, nz, R, seed=3)
     f = si.normal_interior(nx, ny, nz, R, seed=5)
@@ -347,7 +355,7 @@ def test_varcoef_jacobi_solve_matches_oracle(lib, cuda):
     assert_bitwise(to_host(d_u), u_ref)
 
 
-def test_refined_solve_matches_oracle(lib, cuda):
+def test_refined_solve_matches_oracle(lib, cuda, var_variant):
     """Manufactured (1,1,1) sine-mode solution: f = A u* by the oracle.  The float
     inner sweeps and the double residual/update are bitwise on both sides, so
     the refined iterate must agree bitwise while the outer-step counts agree."""
