@@ -178,7 +178,7 @@ def test_temporal_blocking_bitwise(lib, cuda, depth, dtype, r, c):
     try:
         lib.stencil_tune_set("temporal_depth", depth)
         for shape, iters in [((64, 64, 64), 2 * depth + 1), ((37, 19, 11), depth), ((125, 33, 40), 7),
-                             ((3, 2, 1), depth + 2), ((62, 16, 2), 2 * depth)]:
+                             ((3, 2, 1), depth + 2), ((62, 16, 2), 2 * depth), ((70, 45, 100), depth + 1)]:
             nx, ny, nz = shape
             u0 = si.uniform_interior(nx, ny, nz, r, seed=nx + 3, lo=-1, hi=1, dtype=dtype)
             halo = np.ones_like(u0, dtype=bool)
