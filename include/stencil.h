@@ -108,6 +108,11 @@ int stencil_release_workspace(void);
  *                   chunk; clamped to chunks of >= 4 planes).  Changes the
  *                   grid, never the iterates; the residual's partial sums
  *                   follow the grid, so its last bits may change.
+ *   "repeat_graph": 1 (default): sweep loops of grids up to 2^22 points and at
+ *                   least 16 sweeps (stencil_sweep_*, varcoef_sweep_*, the
+ *                   refined solver's inner sweeps) run as a CUDA graph whose
+ *                   while node repeats 16 sweeps on the device; 0: one stream
+ *                   launch per sweep.  Same kernels, same results.
  *   "var_variant":  variable-coefficient kernels: -1 automatic (default: the
  *                   register/shuffle column kernel that computes each face
  *                   coefficient once), 0 the shared-memory plane kernel, 1

@@ -196,6 +196,71 @@ class Stager {
   bool any_host_ = false;
 };
 
+// ----------------------------------------------------- repeated sweeps --
+// Sweep loops over small grids are bound by launch cost, not by the kernels
+// (a 64^3 sweep computes in ~3 us but a stream launch costs about as much
+// again).  graph_repeat captures `body` -- an even number of ping-pong sweeps,
+// so the iterate is back in its first buffer -- once into the body of a CUDA
+// graph while node and lets the device repeat it `reps` times, counting in
+// a workspace scalar.  The same kernels run in the same order, so the results
+// are bitwise those of the host loop.
+static int g_repeat_graph = 1;
+constexpr i64 kRepeatMaxPoints = (i64)1 << 22;  // above this, launches are hidden by the kernels
+constexpr i64 kRepeatBody = 16;                 // sweeps per repetition
+
+static bool use_repeat_graph(const Grid& g, i64 iters) {
+  return g_repeat_graph && iters >= kRepeatBody && g.interior() <= kRepeatMaxPoints;
+}
+
+template <typename Body>
+static int graph_repeat(Workspace* ws, i64 reps, cudaStream_t s, Body&& body) {
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(ws->scalars + 12);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaSuccess;
+  int rc = STN_OK;
+  do {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) break;
+    if ((e = cudaGraphCreate(&graph, 0))) break;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault))) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if ((e = cudaGraphAddNode(&wn, graph, nullptr, nullptr, 0, &cp))) break;
+    if ((e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)))
+      break;
+    rc = body(cs);
+    if (rc == STN_OK) rc = launch_count(ctr, reps, h, cs);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+    if (rc != STN_OK) break;
+    if ((e = e2)) break;
+    if ((e = cudaGraphInstantiate(&exec, graph, 0))) break;
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(*ctr), s))) break;
+    if ((e = cudaGraphLaunch(exec, s))) break;
+  } while (false);
+  // an executable graph that is still running is freed when it completes
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (rc != STN_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "graph-repeated sweeps");
+  return STN_OK;
+}
+
+int tune_set_repeat_graph(int v) {
+  if (v < 0 || v > 1) return STN_EINVAL;
+  g_repeat_graph = v;
+  return STN_OK;
+}
+int tune_get_repeat_graph() { return g_repeat_graph; }
+
 // --------------------------------------------------------------- drivers --
 template <typename T>
 static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeffs, int radius,
@@ -230,6 +295,19 @@ static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeff
       if (int rc = launch_temporal<T>(cur, nxt, g, coeffs, depth, s)) return rc;
       std::swap(cur, nxt);
     }
+  }
+  if (depth <= 1 && use_repeat_graph(g, iters)) {
+    Workspace* ws;
+    if (int rc = get_workspace(s, 0, 0, &ws)) return rc;
+    const i64 reps = iters / kRepeatBody;
+    int rc = graph_repeat(ws, reps, s, [&](cudaStream_t cs) -> int {
+      for (i64 k = 0; k < kRepeatBody; k++)
+        if (int r = launch_star<T>(k % 2 ? nxt : cur, nullptr, k % 2 ? cur : nxt, g, coeffs, kSweep, nullptr, cs))
+          return r;
+      return STN_OK;
+    });
+    if (rc) return rc;
+    it = reps * kRepeatBody;
   }
   for (; it < iters; it++) {
     if (int rc = launch_star<T>(cur, nullptr, nxt, g, coeffs, kSweep, nullptr, s)) return rc;
@@ -593,7 +671,22 @@ static int var_sweep_impl(T* in, T* out, const T* a, const T* f, i64 nx, i64 ny,
   if (int rc = launch_copy_halo<T>(din, dout, g, s)) return rc;
   T* cur = din;
   T* nxt = dout;
-  for (i64 it = 0; it < iters; it++) {
+  i64 it = 0;
+  if (use_repeat_graph(g, iters)) {
+    Workspace* ws;
+    if (int rc = get_workspace(s, 0, 0, &ws)) return rc;
+    const i64 reps = iters / kRepeatBody;
+    int rc = graph_repeat(ws, reps, s, [&](cudaStream_t cs) -> int {
+      for (i64 k = 0; k < kRepeatBody; k++)
+        if (int r = launch_var<T>(k % 2 ? nxt : cur, da, df, k % 2 ? cur : nxt, g, w, kVarSweep, nullptr,
+                                  nullptr, cs))
+          return r;
+      return STN_OK;
+    });
+    if (rc) return rc;
+    it = reps * kRepeatBody;
+  }
+  for (; it < iters; it++) {
     if (int rc = launch_var<T>(cur, da, df, nxt, g, w, kVarSweep, nullptr, nullptr, s)) return rc;
     std::swap(cur, nxt);
   }
@@ -754,7 +847,20 @@ static int refined_impl(const double* a, const double* f, double* u, i64 nx, i64
     STN_CUDA_TRY(cudaMemsetAsync(e, 0, 2 * b32, s));
     float* cur = e;
     float* nxt = e2;
-    for (i64 it = 0; it < inner_sweeps; it++) {
+    i64 it = 0;
+    if (use_repeat_graph(g, inner_sweeps)) {
+      const i64 reps = inner_sweeps / kRepeatBody;
+      int rc = graph_repeat(ws, reps, s, [&](cudaStream_t cs) -> int {
+        for (i64 k = 0; k < kRepeatBody; k++)
+          if (int r = launch_var<float>(k % 2 ? nxt : cur, a32, r32, k % 2 ? cur : nxt, g, w, kVarSweep,
+                                        nullptr, nullptr, cs))
+            return r;
+        return STN_OK;
+      });
+      if (rc) return rc;
+      it = reps * kRepeatBody;
+    }
+    for (; it < inner_sweeps; it++) {
       if (int rc = launch_var<float>(cur, a32, r32, nxt, g, w, kVarSweep, nullptr, nullptr, s)) return rc;
       std::swap(cur, nxt);
     }
@@ -843,6 +949,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_chunk2d(value) != STN_OK) return einval("sweep2d_chunk must be in [1, 2^30]");
     return STN_OK;
   }
+  if (strcmp(knob, "repeat_graph") == 0) {
+    if (tune_set_repeat_graph((int)value) != STN_OK) return einval("repeat_graph must be 0 or 1");
+    return STN_OK;
+  }
   if (strcmp(knob, "var_variant") == 0) {
     if (tune_set_var_variant((int)value) != STN_OK) return einval("var_variant must be -1, 0 or 1");
     return STN_OK;
@@ -903,6 +1013,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "sweep2d_chunk") == 0) {
     *value = tune_get_chunk2d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "repeat_graph") == 0) {
+    *value = tune_get_repeat_graph();
     return STN_OK;
   }
   if (strcmp(knob, "var_variant") == 0) {

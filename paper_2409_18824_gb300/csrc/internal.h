@@ -179,6 +179,8 @@ int launch_finalize(const double* partials, i64 n, double* dst, const double* sc
 // `group` sweeps fits under max_full).
 int launch_decide(const double* partials, i64 n, double* dst, double tol, i64 group, i64 max_full,
                   cudaGraphConditionalHandle h, cudaStream_t s);
+// Counter node of a device-repeated graph body (see graph_repeat in api.cu).
+int launch_count(unsigned long long* ctr, i64 n, cudaGraphConditionalHandle h, cudaStream_t s);
 // Tuning: 1 = jacobi_solve_f64 iterates inside a CUDA graph (default), 0 = host loop.
 int tune_set_solve_graph(int v);
 int tune_get_solve_graph();

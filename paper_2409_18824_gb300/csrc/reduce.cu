@@ -93,6 +93,15 @@ __global__ void __launch_bounds__(FT) decide_kernel(const double* __restrict__ p
   }
 }
 
+// Loop counter of a device-repeated graph body: one more repetition done;
+// the while node runs again while fewer than n are done.
+__global__ void count_kernel(unsigned long long* __restrict__ ctr, unsigned long long n,
+                             cudaGraphConditionalHandle h) {
+  const unsigned long long v = *ctr + 1;
+  *ctr = v;
+  cudaGraphSetConditional(h, v < n ? 1u : 0u);
+}
+
 __global__ void __launch_bounds__(FT) max_finalize_kernel(const double* __restrict__ partials,
                                                           i64 n, double* __restrict__ dst) {
   __shared__ double red[32];
@@ -143,6 +152,12 @@ int launch_finalize(const double* partials, i64 n, double* dst, const double* sc
 int launch_decide(const double* partials, i64 n, double* dst, double tol, i64 group, i64 max_full,
                   cudaGraphConditionalHandle h, cudaStream_t s) {
   decide_kernel<<<1, FT, 0, s>>>(partials, n, dst, tol, group, max_full, h);
+  STN_CUDA_TRY(cudaGetLastError());
+  return STN_OK;
+}
+
+int launch_count(unsigned long long* ctr, i64 n, cudaGraphConditionalHandle h, cudaStream_t s) {
+  count_kernel<<<1, 1, 0, s>>>(ctr, (unsigned long long)n, h);
   STN_CUDA_TRY(cudaGetLastError());
   return STN_OK;
 }

@@ -109,6 +109,39 @@ def test_sweep_misaligned_grids_use_scalar_path(lib, cuda, dtype):
         assert abs(lib.residual_norm_f64(d_out, L7, r) - nref) <= NORM_RTOL * nref
 
 
+@pytest.mark.parametrize("repeat", [1, 0])
+@pytest.mark.parametrize("n_iters", [16, 37, 100])
+def test_graph_repeated_sweeps_bitwise(lib, cuda, repeat, n_iters):
+    """Sweep loops run as a device-repeated CUDA graph (repeat_graph 1: 16 sweeps
+    per repetition plus a host-launched remainder) or as stream launches (0):
+    the same bits as the oracle either way, for stencil and variable-coefficient
+    sweeps and for the refined solver's inner loop."""
+    try:
+        lib.stencil_tune_set("repeat_graph", repeat)
+        for (nx, ny, nz), r, c in (((64, 64, 64), 1, L7), ((37, 19, 11), 2, (0.2, 0.1, 0.0333))):
+            u0 = si.uniform_interior(nx, ny, nz, r, seed=n_iters, lo=-1, hi=1)
+            ref = oracle.stencil_sweep(u0, c, r, n_iters)
+            d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+            lib.stencil_sweep_f64(d_in, d_out, c, r, n_iters)
+            assert_bitwise(to_host(d_out), ref)
+            u32 = u0.astype(np.float32)
+            d_in, d_out = to_dev(u32), to_dev(np.zeros_like(u32))
+            lib.stencil_sweep_f32(d_in, d_out, c, r, n_iters)
+            assert_bitwise(to_host(d_out), oracle.stencil_sweep(u32, c, r, n_iters))
+        nx, ny, nz, R = 21, 13, 9, 2
+        a = si.uniform_full(nx, ny, nz, R, seed=3)
+        f = si.normal_interior(nx, ny, nz, R, seed=5)
+        u = si.uniform_interior(nx, ny, nz, R, seed=6)
+        ref = u
+        for _ in range(n_iters):
+            ref = oracle.varcoef_sweep(ref, a, f, VW, R)
+        d_in, d_out = to_dev(u), to_dev(np.zeros_like(u))
+        lib.varcoef_sweep_f64(d_in, d_out, to_dev(a), to_dev(f), VW, R, n_iters)
+        assert_bitwise(to_host(d_out), ref)
+    finally:
+        lib.stencil_tune_set("repeat_graph", 1)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
 def test_every_kernel_variant_bitwise(lib, cuda, variant, r, c):
@@ -355,7 +388,14 @@ def test_varcoef_jacobi_solve_matches_oracle(lib, cuda, var_variant):
     assert_bitwise(to_host(d_u), u_ref)
 
 
-def test_refined_solve_matches_oracle(lib, cuda, var_variant):
+@pytest.fixture(params=[1, 0])
+def repeat_graph(request, lib):
+    lib.stencil_tune_set("repeat_graph", request.param)
+    yield request.param
+    lib.stencil_tune_set("repeat_graph", 1)
+
+
+def test_refined_solve_matches_oracle(lib, cuda, var_variant, repeat_graph):
     """Manufactured (1,1,1) sine-mode solution: f = A u* by the oracle.  The float
     inner sweeps and the double residual/update are bitwise on both sides, so
     the refined iterate must agree bitwise while the outer-step counts agree."""
