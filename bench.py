@@ -739,6 +739,17 @@ def run_varcoef(args):
     W = si.VARCOEF_W
     R = 2
 
+    if args.kernel_only:
+        # the float variable-coefficient sweep alone at 512 x 512 x 256 (for profilers)
+        nx, ny, nz = 512, 512, 256
+        a32 = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3, dtype=np.float32)).to(dev)
+        f32 = torch.from_numpy(si.normal_interior(nx, ny, nz, R, seed=4, dtype=np.float32)).to(dev)
+        e0 = torch.zeros_like(f32)
+        e1 = torch.zeros_like(f32)
+        stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, args.kernel_only)
+        torch.cuda.synchronize()
+        return
+
     def problem(nx, ny, nz):
         a = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3)).to(dev)
         ustar = torch.from_numpy(si.sine_mode(nx, ny, nz, R)).to(dev)
