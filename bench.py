@@ -143,6 +143,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms, device):
+    """The job's time: the slowest rank's (an all-reduce MAX over the process
+    group; the local value when there is no group or only one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -213,10 +225,7 @@ def run_cuda(args, wl):
         barrier()
         t_wall = time.perf_counter() - t_wall0
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     lups_rank = float(nx) * ny * nz * sweeps * args.steps
     value = lups_rank * ws / (ms * 1e-3) / 1e9
 
@@ -384,10 +393,7 @@ def run_jacobi2d(args):
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     lups = float(nx) * ny * sweeps
     value = lups * args.steps * ws / (ms * 1e-3) / 1e9
 
@@ -532,10 +538,7 @@ def run_intrinsic(args, kind):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     sec = ms / args.steps / 1e3
     value = nbytes * ws / sec / 1e9
     # e2e: the arrays from pinned host memory through the C ABI every step
@@ -682,10 +685,7 @@ def run_batched(args):
             times.append(e0.elapsed_time(e1))
             all_infos = infos
     ms = sum(times)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     pts = np.array([nx * ny * nz for nx, ny, nz in sizes], dtype=np.float64)
     iters = np.array([i["iters"] for i in all_infos], dtype=np.float64)
     lups = float((pts * iters).sum())
