@@ -537,7 +537,7 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
                          double tol, i64 iters, i64 check_every, double inner_tol, i64 max_outer,
                          bool refined, stn_solve_info* infos, cudaStream_t s) {
   const bool hc0 = coeffs[0] != 0.0;
-  const int ctas = sched_ctas(radius, hc0);
+  const int ctas = sched_ctas(radius, hc0, refined);
   if (ctas < 1) {
     set_error("scheduler kernel does not fit on an SM");
     return STN_ECUDA;

@@ -323,7 +323,7 @@ stn_server* stn_server_create(const stn_server_opts* o) {
     return (stn_server*)nullptr;
   };
   if ((e = cudaGetDevice(&s->device))) return bad(e, "cudaGetDevice");
-  s->ctas = sched_ctas(o->radius, o->coeffs[0] != 0.0);
+  s->ctas = sched_ctas(o->radius, o->coeffs[0] != 0.0, o->refined != 0);
   if (s->ctas < 1) {
     set_error("scheduler kernel does not fit on an SM");
     delete s;

@@ -103,8 +103,9 @@ struct SchedFaults {
   long long admit_failed = 0; // server: admission failures seen so far
 };
 SchedFaults& sched_faults();
-// CTAs of one full wave of the scheduler kernel (-1 on error).
-int sched_ctas(int radius, bool has_c0);
+// CTAs of one full wave of the scheduler kernel (-1 on error); refined
+// launches use an instantiation with more resident blocks per SM.
+int sched_ctas(int radius, bool has_c0, bool refined);
 // Work units of a problem's pass.
 i64 sched_units(i64 nx, i64 ny, i64 nz);
 
