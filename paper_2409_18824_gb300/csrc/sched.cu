@@ -37,6 +37,7 @@ namespace {
 
 constexpr int BT = TX * TY;
 constexpr int kSchedMinBlocksRefined = 7;
+constexpr int kSchedMinBlocksPlain = 4;
 
 enum Phase : int {
   PH_IDLE = 0,
@@ -467,7 +468,8 @@ __device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, cons
 // (float inner sweeps, latency-bound) runs faster with more resident warps:
 // with 7 blocks per SM a batch of 256 refined solves went from 68.7 to 101.9
 // solves/s, while double batches lost 3.6 % (measured); so refined launches
-// use MINB = 7 and double ones the unconstrained allocation.
+// use MINB = 7 and double ones MINB = 4 (62 registers, no spills; leaving the
+// allocation unconstrained gave 96 registers and 2 blocks per SM).
 template <int R, bool HAS_C0, int MINB>
 __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
   __shared__ SmemPlanes sp;
@@ -600,7 +602,7 @@ int sched_launch(const SchedArgs& a0, int radius, bool has_c0, int ctas, cudaStr
     if (a.refined)                                                             \
       sched_kernel<R_, C0_, kSchedMinBlocksRefined><<<ctas, dim3(TX, TY), 0, s>>>(a); \
     else                                                                       \
-      sched_kernel<R_, C0_, 1><<<ctas, dim3(TX, TY), 0, s>>>(a);               \
+      sched_kernel<R_, C0_, kSchedMinBlocksPlain><<<ctas, dim3(TX, TY), 0, s>>>(a); \
   } while (0)
   if (radius == 1) {
     if (has_c0) STN_SCHED(1, true);
@@ -626,7 +628,7 @@ static cudaError_t sched_occupancy(int* per_sm, int radius, bool has_c0) {
 int sched_ctas(int radius, bool has_c0, bool refined) {
   int per_sm = 0;
   const cudaError_t e = refined ? sched_occupancy<kSchedMinBlocksRefined>(&per_sm, radius, has_c0)
-                                : sched_occupancy<1>(&per_sm, radius, has_c0);
+                                : sched_occupancy<kSchedMinBlocksPlain>(&per_sm, radius, has_c0);
   if (e != cudaSuccess || per_sm < 1) return -1;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
