@@ -28,6 +28,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -143,6 +144,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_info():
+    """CPU model and core count of the machine running the benchmark."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+                if k == "cpu part" and model is None:
+                    model = "arm cpu part " + ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return {"cpu": model or platform.machine(), "cores": os.cpu_count()}
+
+
+def step_stats(events):
+    """Per-step times (ms) from consecutive CUDA events: median, mean, min."""
+    ts = [a.elapsed_time(b) for a, b in zip(events[:-1], events[1:])]
+    return {"median": statistics.median(ts), "mean": statistics.fmean(ts), "min": min(ts), "n": len(ts)}
+
+
 def max_over_ranks(ms, device):
     """The job's time: the slowest rank's (an all-reduce MAX over the process
     group; the local value when there is no group or only one rank)."""
@@ -215,16 +239,17 @@ def run_cuda(args, wl):
     barrier()
     norms = []
     with ClockSampler(local) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         t_wall0 = time.perf_counter()
-        e0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(args.steps):
             norms.append(step())
-        e1.record(stream)
+            evs[i + 1].record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall0
+    e0, e1 = evs[0], evs[-1]
     ms = e0.elapsed_time(e1)
+    per_step = step_stats(evs)
     ms = max_over_ranks(ms, dev)
     lups_rank = float(nx) * ny * nz * sweeps * args.steps
     value = lups_rank * ws / (ms * 1e-3) / 1e9
@@ -317,6 +342,8 @@ def run_cuda(args, wl):
         "roofline": roofline,
         "clocks": clocks,
         "wall_s_timed": t_wall,
+        "step_ms": per_step,
+        "host": host_info(),
         "residual_norm": norms[-1],
     }
     if rank == 0:
@@ -446,6 +473,7 @@ def run_jacobi2d(args):
                      "kernel": "j2d_resident_kernel<double,1>", "kernel_ms": kern_ms,
                      "kernel_sweeps": k_sweeps},
         "clocks": clk.summary(),
+        "host": host_info(),
         "residual_norm": norms[-1],
     }
     if rank == 0:
@@ -482,6 +510,7 @@ def run_reference2d(args):
                          "sample": f"each step: {k} sweeps + 1 residual norm (plain C oracle, one thread) "
                                    f"instead of 100000"},
         "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host_info(),
     }), flush=True)
 
 
@@ -582,6 +611,7 @@ def run_intrinsic(args, kind):
         "gpu_launches": args.steps * 2,
         "roofline": roofline,
         "clocks": clk.summary(),
+        "host": host_info(),
         "result": vals[-1],
     }
     if rank == 0:
@@ -623,6 +653,7 @@ def run_reference_intrinsic(args, kind):
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": "each step: the whole workload, plain C oracle, one thread"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host_info(),
     }), flush=True)
 
 
@@ -980,6 +1011,7 @@ def run_reference(args, wl):
                          "sample": f"each step: {sweeps} sweeps + 1 residual norm of the workload's grid "
                                    f"(plain C oracle, one thread) instead of the full sweep count"},
         "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host_info(),
     }
     print(json.dumps(out), flush=True)
 
