@@ -86,6 +86,8 @@ def _load():
                                                             ctypes.POINTER(_i64), _dp]),
             "oracle_dense_solve": (ctypes.c_int, [_dp, _dp, _i64]),
             "oracle_sum_f64": (ctypes.c_double, [_dp, _i64]),
+            "oracle_advect_f64": (None, [_dp, _dp, _dp, _dp, _dp, _i64, _i64, _i64, _dp]),
+            "oracle_advect_f32": (None, [_fp, _fp, _fp, _fp, _fp, _i64, _i64, _i64, _fp]),
             "oracle_dot_f64": (ctypes.c_double, [_dp, _dp, _i64]),
             "oracle_sweep2d_f64": (None, [_dp, _dp, _dp, _i64, _i64, _dp, ctypes.c_int]),
             "oracle_sweep2d_f32": (None, [_fp, _fp, _fp, _i64, _i64, _fp, ctypes.c_int]),
@@ -195,6 +197,29 @@ def jacobi_solve(b: np.ndarray | None, u0: np.ndarray, coeffs, r: int, tol: floa
     if st < 0:
         raise MemoryError("oracle allocation failed")
     return u, it.value, rel.value, st
+
+
+# ------------------------------------------------------------- advection --
+def advect(u, v, w, q, c) -> np.ndarray:
+    """Tendency of q under the velocity (u, v, w) (flux-form centred advection,
+    halo 1); the result's halo is zero."""
+    lib = _load()
+    dt = u.dtype.type
+    for a in (u, v, w, q):
+        _grid(a, dt)
+        if a.shape != u.shape:
+            raise ValueError("shape mismatch")
+    s = np.zeros_like(u)
+    nx, ny, nz = interior_shape(u, 1)
+    if dt == np.float64:
+        cc = np.ascontiguousarray(c, dtype=np.float64)
+        lib.oracle_advect_f64(*(_ptr(a, ctypes.c_double) for a in (u, v, w, q, s)), nx, ny, nz,
+                              _ptr(cc, ctypes.c_double))
+    else:
+        cc = np.asarray(c, dtype=np.float64).astype(np.float32)
+        lib.oracle_advect_f32(*(_ptr(a, ctypes.c_float) for a in (u, v, w, q, s)), nx, ny, nz,
+                              _ptr(cc, ctypes.c_float))
+    return s
 
 
 # -------------------------------------------------------- sum, dotproduct --

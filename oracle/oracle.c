@@ -41,6 +41,14 @@
  *     Jacobi update u'(p) = (f(p) + N(p)) / D(p) with D = sum w_d kappa and
  *     N = sum w_d kappa u(q), both accumulated d = 1..R, axis x,y,z, the
  *     minus neighbour before the plus neighbour.  (A u)(p) = D u(p) - N.
+ *   - Multi-field advection (a synthetic stand-in for the paper's pw-advection
+ *     and tra-adv workloads, Sec. 4: fields carried by a wind; their formulas
+ *     are not in the paper): second-order centred flux-form advection of a
+ *     field q by the velocity (u, v, w), per axis a with velocity V_a,
+ *         F-(p) = (V(p-e)+V(p)) * (q(p-e)+q(p)),
+ *         F+(p) = (V(p)+V(p+e)) * (q(p)+q(p+e)),
+ *         T_a = c_a * (F- - F+),   s = (T_x + T_y) + T_z,
+ *     every operation rounded separately in this order.
  *   - Two-dimensional grids (the paper's own jacobi benchmark is 2-D, Sec. 4):
  *     a padded (ny+2r) x (nx+2r) array, i fastest, the same Dirichlet halo
  *     and the same canonical order without the k term:
@@ -670,4 +678,51 @@ double oracle_dot_f64(const double* x, const double* y, i64 n) {
   double acc = 0.0;
   for (i64 i = 0; i < n; i++) acc = acc + x[i] * y[i];
   return acc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Multi-field advection stand-in (see the header): the tendency s of one
+ * field q under the velocity (u, v, w) on the interior of a halo-1 grid.
+ * Writes the interior of s only.
+ * ------------------------------------------------------------------------- */
+void oracle_advect_f64(const double* u, const double* v, const double* w, const double* q,
+                       double* s, i64 nx, i64 ny, i64 nz, const double* c) {
+  const i64 NX = nx + 2, NY = ny + 2;
+  const double* vel[3] = {u, v, w};
+  const i64 step[3] = {1, NX, NX * NY};
+  for (i64 k = 1; k <= nz; k++)
+    for (i64 j = 1; j <= ny; j++)
+      for (i64 i = 1; i <= nx; i++) {
+        const i64 p = off3(i, j, k, NX, NY);
+        double t[3];
+        for (int a = 0; a < 3; a++) {
+          const double* V = vel[a];
+          const i64 e = step[a];
+          const double fm = (V[p - e] + V[p]) * (q[p - e] + q[p]);
+          const double fp = (V[p] + V[p + e]) * (q[p] + q[p + e]);
+          t[a] = c[a] * (fm - fp);
+        }
+        s[p] = (t[0] + t[1]) + t[2];
+      }
+}
+
+void oracle_advect_f32(const float* u, const float* v, const float* w, const float* q, float* s,
+                       i64 nx, i64 ny, i64 nz, const float* c) {
+  const i64 NX = nx + 2, NY = ny + 2;
+  const float* vel[3] = {u, v, w};
+  const i64 step[3] = {1, NX, NX * NY};
+  for (i64 k = 1; k <= nz; k++)
+    for (i64 j = 1; j <= ny; j++)
+      for (i64 i = 1; i <= nx; i++) {
+        const i64 p = off3(i, j, k, NX, NY);
+        float t[3];
+        for (int a = 0; a < 3; a++) {
+          const float* V = vel[a];
+          const i64 e = step[a];
+          const float fm = (V[p - e] + V[p]) * (q[p - e] + q[p]);
+          const float fp = (V[p] + V[p + e]) * (q[p] + q[p + e]);
+          t[a] = c[a] * (fm - fp);
+        }
+        s[p] = (t[0] + t[1]) + t[2];
+      }
 }
