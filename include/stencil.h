@@ -496,6 +496,33 @@ int residual_norm2d_f32(const float* u, const float* b, int64_t nx, int64_t ny,
 int reduce_sum_f64(const double* x, int64_t n, double* out, void* stream);
 int dot_f64(const double* x, const double* y, int64_t n, double* out, void* stream);
 
+/*
+ * advect_f64 / _f32 -- multi-field advection, a synthetic stand-in for the
+ * paper's pw-advection and tra-adv workloads (Sec. 4: fields carried by a
+ * wind on 2048 x 1024 x 1024 and 1024 x 512 x 512 grids; the paper gives no
+ * formulas).  Second-order centred flux-form advection of a field q by the
+ * velocity (u, v, w) on a halo-1 grid (the 3-D layout above, radius 1); for
+ * each axis a with velocity component V and interior point p:
+ *     F- = (V(p-e)+V(p)) * (q(p-e)+q(p)),   F+ = (V(p)+V(p+e)) * (q(p)+q(p+e)),
+ *     T_a = c_a * (F- - F+),                 s(p) = (T_x + T_y) + T_z,
+ * each operation rounded separately in this order.  With c_a = 1/(4 h_a) this
+ * is -div(V q) in flux form.
+ *   u, v, w  velocity components (device grids, read only).
+ *   q        NULL: the velocity components advect themselves (the pw-like
+ *            case) and s[0..2] receive their tendencies; otherwise nq (1..6)
+ *            fields, s[0..nq-1] their tendencies (the tra-adv-like case).
+ *   s        output grids; only the interior is written.  Must not overlap
+ *            any input or each other.
+ *   c        host, 3 doubles {c_x, c_y, c_z}.
+ * Device grids only.  Asynchronous on `stream`.
+ * Errors: STN_EINVAL (NULL pointers, nq out of range, non-finite c, bad
+ * extents, overlap, a host pointer), STN_ECUDA.
+ */
+int advect_f64(const double* u, const double* v, const double* w, const double* const* q, int nq,
+               double* const* s, int64_t nx, int64_t ny, int64_t nz, const double* c, void* stream);
+int advect_f32(const float* u, const float* v, const float* w, const float* const* q, int nq,
+               float* const* s, int64_t nx, int64_t ny, int64_t nz, const double* c, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

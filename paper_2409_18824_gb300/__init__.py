@@ -105,6 +105,8 @@ SIGNATURES = {
     "residual_norm_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "residual_norm_f64_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _vp]),
     "reduce_sum_f64": (_int, [_vp, _i64, _dp, _vp]),
+    "advect_f64": (_int, [_vp, _vp, _vp, ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp), _i64, _i64, _i64, _dp, _vp]),
+    "advect_f32": (_int, [_vp, _vp, _vp, ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp), _i64, _i64, _i64, _dp, _vp]),
     "dot_f64": (_int, [_vp, _vp, _i64, _dp, _vp]),
     "stencil_sweep2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_sweep2d_f32": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _vp]),
@@ -272,6 +274,28 @@ def _numel(a, n):
     if n is not None:
         return n
     return int(a.numel()) if hasattr(a, "numel") else int(a.size)
+
+
+def _advect(fn, u, v, w, s, c, q, nx, ny, nz, stream):
+    nx, ny, nz = _extents(u, 1, nx, ny, nz)
+    cp, _keep = _coeffs(c)
+    outs = (_vp * len(s))(*[_addr(x) for x in s])
+    if q is None:
+        qs, nq = None, 3
+    else:
+        qs = (_vp * len(q))(*[_addr(x) for x in q])
+        nq = len(q)
+    return _check(fn(_addr(u), _addr(v), _addr(w), qs, nq, outs, nx, ny, nz, cp, _stream(stream, u, v, w)))
+
+
+def advect_f64(u, v, w, s, c, q=None, nx=None, ny=None, nz=None, stream=None):
+    """Tendencies s[m] of fields q[m] under the velocity (u, v, w) (flux-form
+    centred advection); q=None: the velocity components advect themselves."""
+    return _advect(_lib.advect_f64, u, v, w, s, c, q, nx, ny, nz, stream)
+
+
+def advect_f32(u, v, w, s, c, q=None, nx=None, ny=None, nz=None, stream=None):
+    return _advect(_lib.advect_f32, u, v, w, s, c, q, nx, ny, nz, stream)
 
 
 def reduce_sum_f64(x, n=None, stream=None) -> float:

@@ -11,6 +11,9 @@
 #include <string>
 #include <utility>
 
+#include <cmath>
+#include <vector>
+
 #include "internal.h"
 #include "work_sched.h"
 
@@ -457,6 +460,48 @@ static int vec_reduce_impl(const double* x, const double* y, i64 n, double* out,
   if (int rc = read_scalars(ws, 0, 1, s)) return rc;
   *out = ws->host_scalars[0];
   return st.finish();
+}
+
+// ------------------------------------------------------------- advection --
+template <typename T>
+static int advect_impl(const T* u, const T* v, const T* w, const T* const* q, int nq, T* const* s,
+                       i64 nx, i64 ny, i64 nz, const double* c, void* stream) {
+  clear_error();
+  if (!u || !v || !w || !s) return einval("NULL velocity or output list");
+  if (!c) return einval("NULL coefficients");
+  for (int a = 0; a < 3; a++)
+    if (!std::isfinite(c[a])) return einval("coefficients must be finite");
+  if (int rc = check_grid(nx, ny, nz, 1)) return rc;
+  const int nout = q ? nq : 3;
+  if (q && (nq < 1 || nq > 6)) return einval("nq must be in 1..6");
+  const Grid g{nx, ny, nz, 1};
+  const size_t bytes = (size_t)g.count() * sizeof(T);
+  std::vector<const void*> ins = {u, v, w};
+  for (int m = 0; q && m < nq; m++) {
+    if (!q[m]) return einval("NULL field");
+    ins.push_back(q[m]);
+  }
+  for (int m = 0; m < nout; m++) {
+    if (!s[m]) return einval("NULL output");
+    for (const void* x : ins)
+      if (overlap(s[m], x, bytes)) return einval("an output overlaps an input");
+    for (int o = 0; o < m; o++)
+      if (overlap(s[m], s[o], bytes)) return einval("outputs overlap");
+  }
+  std::vector<const void*> all = ins;
+  for (int m = 0; m < nout; m++) all.push_back(s[m]);
+  for (const void* x : all) {
+    bool host = false;
+    if (int rc = classify(x, &host)) return rc;
+    if (host) return einval("advect takes device grids only");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!q) return launch_advect<T>(u, v, w, nullptr, 3, s, g, c, st);
+  for (int g0 = 0; g0 < nq; g0 += 3) {
+    const int n = std::min(3, nq - g0);
+    if (int rc = launch_advect<T>(u, v, w, q + g0, n, s + g0, g, c, st)) return rc;
+  }
+  return STN_OK;
 }
 
 // Scalars layout used by the solvers: [0] sum, [1] norm, [2] rel, [3] flag,
@@ -1207,6 +1252,16 @@ int dot_f64(const double* x, const double* y, int64_t n, double* out, void* stre
     return einval("NULL array");
   }
   return vec_reduce_impl(x, y, n, out, stream);
+}
+
+int advect_f64(const double* u, const double* v, const double* w, const double* const* q, int nq,
+               double* const* s, int64_t nx, int64_t ny, int64_t nz, const double* c, void* stream) {
+  return advect_impl<double>(u, v, w, q, nq, s, nx, ny, nz, c, stream);
+}
+
+int advect_f32(const float* u, const float* v, const float* w, const float* const* q, int nq,
+               float* const* s, int64_t nx, int64_t ny, int64_t nz, const double* c, void* stream) {
+  return advect_impl<float>(u, v, w, q, nq, s, nx, ny, nz, c, stream);
 }
 
 }  // extern "C"

@@ -140,6 +140,13 @@ i64 vec_reduce_blocks(i64 n);
 // Partials of sum(x[0..n)) (y == NULL) or sum(x[i]*y[i]); fixed order.
 int launch_vec_reduce(const double* x, const double* y, i64 n, double* partials, cudaStream_t s);
 
+// ---- multi-field advection (advect.cu) --------------------------------------
+// Tendencies s[m] of fields q[m] (m < nq <= 3) under the velocity (u, v, w);
+// q == NULL: the velocity components advect themselves (s[0..2]).
+template <typename T>
+int launch_advect(const T* u, const T* v, const T* w, const T* const* q, int nq, T* const* s,
+                  const Grid& g, const double* c, cudaStream_t st);
+
 // ---- temporal blocking (temporal.cu) -----------------------------------------
 // `depth` sweeps of the star stencil (no source term) in one pass: out =
 // S^depth(u) on the interior; bitwise equal to depth separate sweeps.

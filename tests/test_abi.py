@@ -125,6 +125,24 @@ def test_sum_and_dot_reject_bad_arguments(lib):
     assert L.dot_f64(FAKE_A, FAKE_B + 2, 10, ctypes.byref(out), None) == lib.STN_EINVAL
 
 
+def test_advect_rejects_bad_arguments(lib):
+    L = lib.lib()
+    cp, _k = c3(0.25, 0.25, 0.25)
+    outs = (ctypes.c_void_p * 3)(FAKE_B, FAKE_B + (1 << 20), FAKE_B + (2 << 20))
+    assert L.advect_f64(None, FAKE_A, FAKE_A, None, 3, outs, 4, 4, 4, cp, None) == lib.STN_EINVAL
+    assert L.advect_f64(FAKE_A, FAKE_A, FAKE_A, None, 3, None, 4, 4, 4, cp, None) == lib.STN_EINVAL
+    assert L.advect_f64(FAKE_A, FAKE_A, FAKE_A, None, 3, outs, 4, 4, 4, None, None) == lib.STN_EINVAL
+    nan, _n = c3(0.25, float("nan"), 0.25)
+    assert L.advect_f32(FAKE_A, FAKE_A, FAKE_A, None, 3, outs, 4, 4, 4, nan, None) == lib.STN_EINVAL
+    assert L.advect_f64(FAKE_A, FAKE_A, FAKE_A, None, 3, outs, 0, 4, 4, cp, None) == lib.STN_EINVAL
+    qs = (ctypes.c_void_p * 7)(*([FAKE_A] * 7))
+    assert L.advect_f64(FAKE_A, FAKE_A, FAKE_A, qs, 7, outs, 4, 4, 4, cp, None) == lib.STN_EINVAL
+    same = (ctypes.c_void_p * 3)(FAKE_A, FAKE_B, FAKE_B + (1 << 20))
+    assert L.advect_f64(FAKE_A, FAKE_A + (1 << 24), FAKE_A + (2 << 24), None, 3, same, 4, 4, 4, cp, None) \
+        == lib.STN_EINVAL
+    assert "overlap" in lib.last_error()
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     """The package refuses to import when libstencil.so is absent (no fallback)."""
     import shutil
