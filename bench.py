@@ -657,6 +657,168 @@ def run_reference_intrinsic(args, kind):
     }), flush=True)
 
 
+# ------------------------------------------- the advection stand-in (pw-like) ----
+ADVECT = dict(nx=2048, ny=1024, nz=1024, c=(0.25, 0.25, 0.25),
+              desc="multi-field advection stand-in for the paper's pw-advection (its formulas are not "
+                   "in the paper): u, v, w on 2048 x 1024 x 1024 FP64 advect themselves (second-order "
+                   "centred flux form), fields from the integer hash of stencil_inputs.hash_field")
+ADVECT_FP64_OPS = 48.0   # double ops per cell: one flux per face and field (3 each), 3 (diff, scale) pairs, 2 adds
+ADVECT_BYTES = 48.0      # read u, v, w; write three tendencies
+
+
+def hash_field_device(NX, NY, NZ, comp, dtype, device):
+    """stencil_inputs.hash_field on the device, plane by plane (bitwise the same values)."""
+    import torch
+    a, b, c, d = si.HASH_MULS
+    out = torch.empty((NZ, NY, NX), dtype=dtype, device=device)
+    i = torch.arange(NX, device=device, dtype=torch.int64)
+    j = torch.arange(NY, device=device, dtype=torch.int64)
+    base = a * i[None, :] + b * j[:, None] + d * comp
+    for k in range(NZ):
+        h = (base + c * k) % 65536
+        out[k] = (h.to(torch.float64) / 32768.0 - 1.0).to(dtype)
+    return out
+
+
+def run_advect(args):
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    w = ADVECT
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    NX, NY, NZ = nx + 2, ny + 2, nz + 2
+    vel = [hash_field_device(NX, NY, NZ, m, torch.float64, dev) for m in range(3)]
+    outs = [torch.empty_like(vel[0]) for _ in range(3)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        stn.advect_f64(vel[0], vel[1], vel[2], outs, w["c"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk:
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for k in range(args.steps):
+            step()
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dev)
+    cells = float(nx) * ny * nz
+    sec = ms / args.steps / 1e3
+    value = cells * ws / sec / 1e9
+    checksum = float(outs[0][1:-1, 1:-1, 1:-1].double().abs().sum().item())
+    del vel, outs
+    torch.cuda.empty_cache()
+    # e2e at the tra-adv grid size (1024 x 512 x 512, 1/4 of the cells): the
+    # three fields from pinned host memory in, the three tendencies out
+    ex, ey, ez = 1024, 512, 512
+    hv = [torch.from_numpy(si.hash_field(ex + 2, ey + 2, 0, ez + 2, m)).pin_memory() for m in range(3)]
+    ho = [torch.empty_like(hv[0]).pin_memory() for _ in range(3)]
+    dv = [torch.empty(hv[0].shape, dtype=torch.float64, device=dev) for _ in range(3)]
+    do = [torch.empty_like(dv[0]) for _ in range(3)]
+    for dd, hh in zip(dv, hv):
+        dd.copy_(hh, non_blocking=True)
+    stn.advect_f64(dv[0], dv[1], dv[2], do, w["c"])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        for dd, hh in zip(dv, hv):
+            dd.copy_(hh, non_blocking=True)
+        stn.advect_f64(dv[0], dv[1], dv[2], do, w["c"])
+        for hh, dd in zip(ho, do):
+            hh.copy_(dd, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / 2
+    peaks, peak_kind = load_peaks()
+    fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    hbm_peak = float(peaks["hbm_gbs"])
+    achieved = cells * ADVECT_FP64_OPS / sec / 1e12
+    out = {
+        "metric": "Gcells/s (advection stand-in, pw-like, 2048 x 1024 x 1024 FP64)",
+        "value": value, "unit": "Gcells/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "nx": nx, "ny": ny, "nz": nz, "fields": 3,
+                   "l2": "inputs larger than L2 (17 GB per field), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "paper_context": "pw-advection: one EPYC core 86.47 s (MLIR flow, Table 2), V100 OpenACC 22.78 s at "
+                         "1.1 billion cells (Table 5); iteration counts not stated, so not comparable",
+        "e2e": {"value": float(ex) * ey * ez / e2e_s / 1e9, "unit": "Gcells/s",
+                "h2d_bytes_per_step": 3 * hv[0].numel() * 8, "d2h_bytes_per_step": 3 * hv[0].numel() * 8,
+                "grid": [ex, ey, ez]},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": None, "traffic_unit": "bytes per launch",
+                     "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
+                     "ops_per_cell": ADVECT_FP64_OPS, "hbm_achieved_gbs": cells * ADVECT_BYTES / sec / 1e9,
+                     "hbm_peak_gbs": hbm_peak, "hbm_frac": cells * ADVECT_BYTES / sec / 1e9 / hbm_peak,
+                     "hbm_peak_kind": peak_kind, "kernel": "advect_kernel<double,3,self>",
+                     "kernel_ms": ms / args.steps},
+        "step_ms": step_stats(evs),
+        "clocks": clk.summary(),
+        "host": host_info(),
+        "checksum_abs_su": checksum,
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            val, t = cpu_sample_advect()
+            out["cpu_baseline"] = {"value": val, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{ADVECT_CPU_PASSES} passes over a 256 x 128 x 128 corner of the "
+                                             f"same fields, plain C oracle, one thread ({t:.1f} s)"}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+ADVECT_CPU_PASSES = 100  # passes over the CPU sample (~10 s of one core)
+
+
+def cpu_sample_advect(passes=ADVECT_CPU_PASSES):
+    import oracle
+    nx, ny, nz = 256, 128, 128
+    f = [si.hash_field(nx + 2, ny + 2, 0, nz + 2, m) for m in range(3)]
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        for m in range(3):
+            oracle.advect(f[0], f[1], f[2], f[m], ADVECT["c"])
+    t = time.perf_counter() - t0
+    return float(nx) * ny * nz * passes / t / 1e9, t
+
+
+def run_reference_advect(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_sample_advect(1)
+    passes = 20
+    times = [cpu_sample_advect(passes)[1] for _ in range(args.steps)]
+    value = 256.0 * 128 * 128 * passes * args.steps / sum(times) / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": "Gcells/s (advection stand-in, pw-like, 2048 x 1024 x 1024 FP64)",
+        "value": value, "unit": "Gcells/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": ADVECT["desc"], "parallelism": "single"},
+        "cpu_baseline": {"value": value, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: 20 passes over a 256 x 128 x 128 corner of the fields, plain C "
+                                   "oracle, one thread"},
+        "e2e": {"value": value, "unit": "Gcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host_info(),
+    }), flush=True)
+
+
 # ------------------------------------------------------- batched solves ----
 def batch_problems(count, seed_sizes=4, seed_rhs=5):
     """Per-axis sizes log-uniform in [16, 128] (PCG64 seed 4); right-hand sides
@@ -1022,7 +1184,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "sum", "dot"])
+    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "sum", "dot", "advect"])
     ap.add_argument("--requests", type=int, default=48, help="serving workload: requests per trace")
     ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8, 1.1],
                     help="serving workload: offered loads as fractions of the measured capacity")
@@ -1070,6 +1232,12 @@ def main():
                               "implemented for the sweep workloads"}))
             return
         run_batched(args)
+        return
+    if args.workload == "advect":
+        if args.impl == "reference":
+            run_reference_advect(args)
+        else:
+            run_advect(args)
         return
     if args.workload in INTRINSICS:
         if args.impl == "reference":

@@ -19,6 +19,9 @@ Jacobi; its data are not published, so these seeded grids stand in for it):
   * batches of solves with per-axis sizes log-uniform in [16,128] (seed 4),
     right-hand sides N(0,1) (seed 5)
   * serving arrivals: sizes log-uniform in [32,256] (seed 6), Poisson arrivals
+  * the advection stand-in (pw-like): u, v, w on 2048 x 1024 x 1024 from the
+    integer hash of hash_field (exact in any precision, so a device-side
+    generator can reproduce it bit for bit)
   * the paper's own 2-D jacobi: 1024 x 1024 FP64 r=1, interior U[0,1) seed 7,
     zero halo, c = {0, 1/4}, 100000 sweeps (2-D grids are C-contiguous arrays
     of shape (ny+2r, nx+2r), i fastest)
@@ -131,3 +134,18 @@ def linear_field2d(nx, ny, r, alpha, beta, delta, dtype=np.float64):
     """alpha*i + beta*j + delta on every padded 2-D cell (1-based i, j)."""
     j, i = np.meshgrid(np.arange(1, ny + 2 * r + 1), np.arange(1, nx + 2 * r + 1), indexing="ij")
     return (alpha * i + beta * j + delta).astype(dtype)
+
+
+# ----------------------------------------------------------- hashed fields --
+HASH_MULS = (73, 179, 283, 419)  # per-axis and per-component multipliers
+
+
+def hash_field(NX, NY, k0, k1, comp, dtype=np.float64):
+    """Padded planes [k0, k1) of an NX x NY-plane field whose cell (i, j, k)
+    holds ((73 i + 179 j + 283 k + 419 comp) mod 65536) / 32768 - 1: values in
+    [-1, 1) with 16-bit resolution, exact in float and double."""
+    k, j, i = np.meshgrid(np.arange(k0, k1, dtype=np.int64), np.arange(NY, dtype=np.int64),
+                          np.arange(NX, dtype=np.int64), indexing="ij")
+    a, b, c, d = HASH_MULS
+    h = (a * i + b * j + c * k + d * comp) % 65536
+    return (h.astype(np.float64) / 32768.0 - 1.0).astype(dtype)

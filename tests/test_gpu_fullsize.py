@@ -135,3 +135,45 @@ def test_jacobi2d_1024_sampled_windows(lib, cuda):
                            np.ascontiguousarray(ref[dep:dep + w, dep:dep + w])), (j0, i0)
     full_norm_checks(lib.residual_norm2d_f64(d_out, si.LAPLACE5, r), got,
                      lambda x: oracle.sweep2d(x, si.LAPLACE5, r), r, oracle.residual_norm2d(got, si.LAPLACE5, r))
+
+
+def _hash_field_device(NX, NY, NZ, comp, device):
+    """stencil_inputs.hash_field computed on the device plane by plane (integer
+    arithmetic, then an exact scaling: the same bits as the numpy version)."""
+    import torch
+    a, b, c, d = si.HASH_MULS
+    out = torch.empty((NZ, NY, NX), dtype=torch.float64, device=device)
+    i = torch.arange(NX, device=device, dtype=torch.int64)
+    j = torch.arange(NY, device=device, dtype=torch.int64)
+    base = a * i[None, :] + b * j[:, None] + d * comp
+    for k in range(NZ):
+        out[k] = ((base + c * k) % 65536).to(torch.float64) / 32768.0 - 1.0
+    return out
+
+
+def test_advect_2048x1024x1024_sampled_windows(lib, cuda):
+    """The advection stand-in at the paper's pw-advection size (2048 x 1024 x
+    1024, u, v, w advecting themselves, FP64): windows of 6^3 cells (plus one
+    cell of context) at corners, edges and the middle against the oracle."""
+    import torch
+    nx, ny, nz = 2048, 1024, 1024
+    NX, NY, NZ = nx + 2, ny + 2, nz + 2
+    c = (0.25, 0.25, 0.25)
+    vel = [_hash_field_device(NX, NY, NZ, m, "cuda") for m in range(3)]
+    outs = [torch.empty_like(vel[0]) for _ in range(3)]
+    lib.advect_f64(vel[0], vel[1], vel[2], outs, c)
+    torch.cuda.synchronize()
+    w, dep = 6, 1
+    starts = [windows((n,), w, dep)[0] for n in (NZ, NY, NX)]
+    for k0 in starts[0]:
+        for j0 in starts[1]:
+            for i0 in starts[2]:
+                fw = [si.hash_field(NX, NY, k0 - dep, k0 + w + dep, m)[:, j0 - dep:j0 + w + dep, i0 - dep:i0 + w + dep]
+                      for m in range(3)]
+                fw = [np.ascontiguousarray(x) for x in fw]
+                for m in range(3):
+                    ref = oracle.advect(fw[0], fw[1], fw[2], fw[m], c)[dep:dep + w, dep:dep + w, dep:dep + w]
+                    got = outs[m][k0:k0 + w, j0:j0 + w, i0:i0 + w].cpu().numpy()
+                    assert bitwise(np.ascontiguousarray(got), np.ascontiguousarray(ref)), (m, k0, j0, i0)
+    # the device generator reproduces the host one
+    assert bitwise(vel[1][5:7].cpu().numpy(), si.hash_field(NX, NY, 5, 7, 1))
