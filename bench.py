@@ -692,8 +692,16 @@ def run_advect(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    if args.kernel_only:
+        nx, ny, nz = 512, 512, 256  # profiling size: 6 x 545 MB, above L2
     NX, NY, NZ = nx + 2, ny + 2, nz + 2
     vel = [hash_field_device(NX, NY, NZ, m, torch.float64, dev) for m in range(3)]
+    if args.kernel_only:
+        outs = [torch.empty_like(vel[0]) for _ in range(3)]
+        for _ in range(args.kernel_only):
+            stn.advect_f64(vel[0], vel[1], vel[2], outs, w["c"])
+        torch.cuda.synchronize(dev)
+        return
     outs = [torch.empty_like(vel[0]) for _ in range(3)]
     stream = torch.cuda.current_stream(dev)
 
