@@ -618,19 +618,25 @@ def run_intrinsic(args, kind):
         if not args.no_cpu_baseline:
             val, t = cpu_sample_intrinsic(kind, x, y)
             out["cpu_baseline"] = {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                   "sample": f"the whole workload once, plain C oracle, one thread ({t:.2f} s)"}
+                                   "sample": f"the whole workload {INTRINSIC_CPU_PASSES[kind]} times, plain C "
+                                             f"oracle, one thread ({t:.1f} s)"}
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
-def cpu_sample_intrinsic(kind, x, y):
+INTRINSIC_CPU_PASSES = {"sum": 10, "dot": 100}  # ~10 s of one core each
+
+
+def cpu_sample_intrinsic(kind, x, y, passes=None):
     import oracle
     oracle.build()
+    passes = passes or INTRINSIC_CPU_PASSES[kind]
     t0 = time.perf_counter()
-    oracle.sum_(x) if kind == "sum" else oracle.dot(x, y)
+    for _ in range(passes):
+        oracle.sum_(x) if kind == "sum" else oracle.dot(x, y)
     t = time.perf_counter() - t0
-    return 8.0 * x.size * (1 if kind == "sum" else 2) / t / 1e9, t
+    return 8.0 * x.size * (1 if kind == "sum" else 2) * passes / t / 1e9, t
 
 
 def run_reference_intrinsic(args, kind):
@@ -640,8 +646,8 @@ def run_reference_intrinsic(args, kind):
     w = INTRINSICS[kind]
     x, y = intrinsic_inputs(kind)
     for _ in range(args.warmup):
-        cpu_sample_intrinsic(kind, x, y)
-    times = [cpu_sample_intrinsic(kind, x, y)[1] for _ in range(args.steps)]
+        cpu_sample_intrinsic(kind, x, y, 1)
+    times = [cpu_sample_intrinsic(kind, x, y, 1)[1] for _ in range(args.steps)]
     total = sum(times)
     nbytes = 8.0 * w["n"] * (1 if kind == "sum" else 2)
     value = nbytes * args.steps / total / 1e9
@@ -1205,7 +1211,7 @@ def main():
     ap.add_argument("--refined", action="store_true", help="batched workload: FP32 sweeps + FP64 refinement")
     ap.add_argument("--inner-tol", type=float, default=1e-2)
     ap.add_argument("--inner-max", type=int, default=200000)
-    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sweeps", type=int, default=20, help="oracle sweeps per CPU sample (~10 s at 512^3)")
     ap.add_argument("--cpu-sweeps2d", type=int, default=4000, help="jacobi2d: oracle sweeps per CPU sample")
     ap.add_argument("--sweeps2d", type=int, default=0, help="jacobi2d: sweeps per step (0: the paper's 100000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
