@@ -181,7 +181,8 @@ __device__ __forceinline__ double cluster_sweep(const T* cur, const T* b, T* nxt
     const int ty = tq / w.tiles_x, tx = tq - ty * w.tiles_x;
     const int k0 = R + kci * w.klen;
     const int k1 = min(k0 + w.klen, nz + R);
-    star_tile<T, R, HAS_B, HAS_C0, MODE>(cur, b, nxt, nx, ny, NX, NY, tx, ty, k0, k1, cf, tile, &rsum);
+    star_tile<T, R, HAS_B, HAS_C0, MODE>(cur, b, nxt, nx, ny, NX, NY, tx, ty, k0, k1, cf, TX, TY, &tile[0][0],
+                                         &rsum);
   }
   return rsum;
 }

@@ -51,14 +51,24 @@ enum Phase : int {
   PH_UPDATE = 8,  // refined: u += s * e
 };
 
+// Unit tile shapes: 32 x 8 columns, or 16 x 16 where that covers the
+// problem's (nx, ny) with fewer idle columns (a 16- or 48-wide problem).
+// Both shapes hold BT columns; the block's threads map to the tile flat.
+constexpr int SQ = 16;
+
 struct Geo {
-  int tiles_x, tiles_y, kc, klen, n;
+  int tiles_x, tiles_y, kc, klen, n, sq;  // sq: 1 = 16 x 16 tiles, 0 = 32 x 8
 };
 
 __host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
   Geo g;
-  g.tiles_x = (nx + TX - 1) / TX;
-  g.tiles_y = (ny + TY - 1) / TY;
+  // the shape depends on the extents only, so a problem's reduction order
+  // (and hence its iteration count) is the same in any batch
+  const long long a_wide = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+  const long long a_sq = (long long)((nx + SQ - 1) / SQ) * ((ny + SQ - 1) / SQ);
+  g.sq = a_sq < a_wide;
+  g.tiles_x = g.sq ? (nx + SQ - 1) / SQ : (nx + TX - 1) / TX;
+  g.tiles_y = g.sq ? (ny + SQ - 1) / SQ : (ny + TY - 1) / TY;
   // k chunks sized from the extents alone (the unit split fixes the order of
   // every reduction): aim at ~1024 units per pass so a large problem can
   // occupy the whole GPU, with chunks of 16..64 planes.
@@ -119,14 +129,15 @@ __device__ __forceinline__ double reduce_parts(const double* p, int n, bool is_m
   return s;
 }
 
-// Calls f(p) for every interior point of unit q, k outer; thread (tx, ty)
-// owns one column of the unit's tile.
+// Calls f(p) for every interior point of unit q, k outer; each thread owns
+// one column of the unit's tile.
 template <int R, typename F>
 __device__ __forceinline__ void for_unit_points(const SchedProblem& P, const Geo& g, int q, F&& f) {
   const int tiles = g.tiles_x * g.tiles_y;
   const int kci = q / tiles, tq = q - kci * tiles;
   const int tyi = tq / g.tiles_x, txi = tq - tyi * g.tiles_x;
-  const int i = txi * TX + threadIdx.x + R, j = tyi * TY + threadIdx.y + R;
+  const int tw = g.sq ? SQ : TX, th = BT / tw, t = tid_flat();
+  const int i = txi * tw + t % tw + R, j = tyi * th + t / tw + R;
   if (i >= P.nx + R || j >= P.ny + R) return;
   const i64 NX = P.nx + 2 * R, NY = P.ny + 2 * R;
   const int k0 = R + kci * g.klen, k1 = min(k0 + g.klen, P.nz + R);
@@ -135,25 +146,29 @@ __device__ __forceinline__ void for_unit_points(const SchedProblem& P, const Geo
 
 template <typename T, int R, bool HAS_C0, int MODE>
 __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, const SchedProblem& P,
-                                             const Geo& g, int q, const StarCoeffs<T, R>& cf,
-                                             T (*tile)[TX + 2 * R]) {
+                                             const Geo& g, int q, const StarCoeffs<T, R>& cf, T* plane) {
   const int tiles = g.tiles_x * g.tiles_y;
   const int kci = q / tiles, tq = q - kci * tiles;
   const int tyi = tq / g.tiles_x, txi = tq - tyi * g.tiles_x;
   const int k0 = R + kci * g.klen, k1 = min(k0 + g.klen, P.nz + R);
   const int NX = P.nx + 2 * R, NY = P.ny + 2 * R;
+  const int tw = g.sq ? SQ : TX;
   double rs = 0.0;
   if (b)
-    star_tile<T, R, true, HAS_C0, MODE>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tile, &rs);
+    star_tile<T, R, true, HAS_C0, MODE>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw, plane,
+                                        &rs);
   else
-    star_tile<T, R, false, HAS_C0, MODE>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf,
-                                         tile, &rs);
+    star_tile<T, R, false, HAS_C0, MODE>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw,
+                                         plane, &rs);
   return rs;
 }
 
+// one shared plane of either tile shape (radius <= 2)
+constexpr int kPlaneElems = (TY + 4) * (TX + 4) > (BT / SQ + 4) * (SQ + 4) ? (TY + 4) * (TX + 4)
+                                                                          : (BT / SQ + 4) * (SQ + 4);
 struct SmemPlanes {
-  double d[TY + 4][TX + 4];
-  float f[TY + 4][TX + 4];
+  double d[kPlaneElems];
+  float f[kPlaneElems];
 };
 
 // Processes unit q of the slot's current pass; returns the partial (valid in
@@ -169,8 +184,8 @@ __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedPr
     c64.c[d] = a.coeffs[d];
     c32.c[d] = (float)a.coeffs[d];
   }
-  auto* t64 = reinterpret_cast<double(*)[TX + 2 * R]>(&sp.d[0][0]);
-  auto* t32 = reinterpret_cast<float(*)[TX + 2 * R]>(&sp.f[0][0]);
+  double* t64 = sp.d;
+  float* t32 = sp.f;
   double v = 0.0;
   switch (S.phase) {
     case PH_INIT: {

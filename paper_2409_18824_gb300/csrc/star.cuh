@@ -60,25 +60,31 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 // TY+2R x TX+2R shared plane.  The pointers carry no __restrict__: the
 // batched solver reads grids that other CTAs of its launch wrote, which must
 // go through the coherent load path.
+// The tile is tw x th columns (32 x 8 for the standalone kernel, where the
+// shape folds to constants; the batched scheduler also uses 16 x 16 for
+// narrow problems) with the block's tw * th threads numbered flat, x
+// fastest; `plane` is a (th+2R) x (tw+2R) shared array, row pitch tw+2R.
 template <typename T, int R, bool HAS_B, bool HAS_C0, int MODE>
 __device__ __forceinline__ void star_tile(const T* u, const T* b, T* out, int nx, int ny, int NX, int NY,
                                           int tile_x, int tile_y, int k0, int k1,
-                                          const StarCoeffs<T, R>& cf, T (*tile)[TX + 2 * R],
+                                          const StarCoeffs<T, R>& cf, int tw, int th, T* plane,
                                           double* rsum_io) {
   using A = Arith<T>;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int gi = tile_x * TX + tx + R;  // padded 0-based column index
-  const int gj = tile_y * TY + ty + R;
+  const int flat = (int)(threadIdx.x + blockDim.x * threadIdx.y);
+  const int tx = flat % tw, ty = flat / tw;
+  const int pitch = tw + 2 * R;
+  const int gi = tile_x * tw + tx + R;  // padded 0-based column index
+  const int gj = tile_y * th + ty + R;
   const i64 sy = NX, sz = (i64)NX * NY;
   const bool inx = gi < NX, iny = gj < NY;
   const bool active = (gi < nx + R) && (gj < ny + R);
 
   // halo duties: x halo for the first/last R lanes, y halo for the first/last R rows
-  const bool hx = (tx < R) || (tx >= TX - R);
+  const bool hx = (tx < R) || (tx >= tw - R);
   const int hx_i = (tx < R) ? gi - R : gi + R;
   const int hx_lx = (tx < R) ? tx : tx + 2 * R;
   const bool hx_ok = hx && hx_i < NX && iny;
-  const bool hy = (ty < R) || (ty >= TY - R);
+  const bool hy = (ty < R) || (ty >= th - R);
   const int hy_j = (ty < R) ? gj - R : gj + R;
   const int hy_ly = (ty < R) ? ty : ty + 2 * R;
   const bool hy_ok = hy && hy_j < NY && inx;
@@ -87,6 +93,7 @@ __device__ __forceinline__ void star_tile(const T* u, const T* b, T* out, int nx
   const T* px = u + hx_i + gj * sy;       // x-halo column
   const T* py = u + gi + (i64)hy_j * sy;  // y-halo column
   const bool ld_c = inx && iny;
+  T* const me = plane + (ty + R) * pitch + tx + R;  // this column's cell
 
   T q[2 * R + 1];
 #pragma unroll
@@ -104,16 +111,16 @@ __device__ __forceinline__ void star_tile(const T* u, const T* b, T* out, int nx
       if (hy_ok) hyn = py[(i64)(k + 1) * sz];
     }
     __syncthreads();
-    tile[ty + R][tx + R] = q[R];
-    if (hx) tile[ty + R][hx_lx] = hxv;
-    if (hy) tile[hy_ly][tx + R] = hyv;
+    me[0] = q[R];
+    if (hx) plane[(ty + R) * pitch + hx_lx] = hxv;
+    if (hy) plane[hy_ly * pitch + tx + R] = hyv;
     __syncthreads();
     if (active) {
       T acc = T(0);
 #pragma unroll
       for (int d = R; d >= 1; d--) {
-        T sx = A::add(tile[ty + R][tx + R - d], tile[ty + R][tx + R + d]);
-        T sy_ = A::add(tile[ty + R - d][tx + R], tile[ty + R + d][tx + R]);
+        T sx = A::add(me[-d], me[d]);
+        T sy_ = A::add(me[-d * pitch], me[d * pitch]);
         T szz = A::add(q[R - d], q[R + d]);
         T s = A::add(A::add(sx, sy_), szz);
         T t = A::mul(cf.c[d], s);
@@ -284,8 +291,8 @@ __global__ void __launch_bounds__(TX* TY)
   const int k0 = R + blockIdx.z * kchunk;
   const int k1 = min(k0 + kchunk, nz + R);
   double rsum = 0.0;
-  star_tile<T, R, HAS_B, HAS_C0, MODE>(u, b, out, nx, ny, NX, NY, blockIdx.x, blockIdx.y, k0, k1, cf,
-                                        tile, &rsum);
+  star_tile<T, R, HAS_B, HAS_C0, MODE>(u, b, out, nx, ny, NX, NY, blockIdx.x, blockIdx.y, k0, k1, cf, TX, TY,
+                                        &tile[0][0], &rsum);
   if (MODE != kSweep) {
     const double t = block_sum_fixed<TX * TY>(rsum, red);
     if (threadIdx.x == 0 && threadIdx.y == 0)

@@ -92,6 +92,26 @@ def test_batched_rejects_host_grids(lib, cuda):
         lib.jacobi_solve_batched_f64([np.zeros_like(b)], [b], L7, 1, 1e-8, 10, 10)
 
 
+def test_batched_radius2_with_center_term_matches_oracle(lib, cuda, engine):
+    """A radius-2 star with a centre coefficient (c0 + 6 c1 + 6 c2 = 0.85, a
+    contraction) on problems of both scheduler tile shapes: the 16 x 16, 48 x 9
+    and 12 x 30 problems take 16 x 16 tiles, 64 x 20 and 30 x 3 take 32 x 8;
+    bitwise the oracle's solve, with its sweep count."""
+    c = (0.1, 0.1, 0.025)
+    sizes = [(16, 16, 6), (48, 9, 7), (12, 30, 5), (64, 20, 4), (30, 3, 9)]
+    rhs = [si.normal_interior(nx, ny, nz, 2, seed=40 + i) for i, (nx, ny, nz) in enumerate(sizes)]
+    tol, K, maxit = 1e-10, 7, 5000
+    d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+    rc, infos = lib.jacobi_solve_batched_f64(d_u, [to_dev(b) for b in rhs], c, 2, tol, maxit, K)
+    assert rc == 0
+    for i, b in enumerate(rhs):
+        u_ref, it_ref, rel_ref, st = oracle.jacobi_solve(b, np.zeros_like(b), c, 2, tol, maxit, K)
+        assert st == 0 and infos[i]["status"] == 0
+        assert infos[i]["iters"] == it_ref, (i, infos[i], it_ref)
+        assert abs(infos[i]["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
+        assert bitwise(to_host(d_u[i]), u_ref), i
+
+
 @pytest.mark.parametrize("batched", [False, True])
 def test_refined_fixed_inner_matches_oracle(lib, cuda, engine, batched):
     """With a fixed number of float sweeps per outer step the refinement is a
