@@ -149,7 +149,10 @@ int stencil_release_workspace(void);
  *                   the call returns STN_ETIMEOUT.
  *   "fault_admit_fail": the server's next N admission allocations fail
  *                   (retried later, like a busy pool); "fault_admit_failed"
- *                   (read only) counts the injected failures.  Not thread-safe against
+ *                   (read only) counts the injected failures.
+ * Read only, per calling thread: "last_star_variant" and "last_star_chunks"
+ * (kernel variant and k chunks of the last star-kernel launch),
+ * "last_temporal_depth" (depth used by the last stencil_sweep_* call).  Not thread-safe against
  * concurrent launches.  Unknown knob or value: STN_EINVAL.
  */
 int stencil_tune_set(const char* knob, int64_t value);
@@ -159,6 +162,75 @@ int stencil_tune_set(const char* knob, int64_t value);
  * number of counters written (at most n). */
 int stencil_sched_stats(uint64_t* out, int n);
 int stencil_tune_get(const char* knob, int64_t* value);
+
+/*
+ * Autotuner and tuning cache for the star sweeps (stencil_sweep_*,
+ * stencil_apply_*, residual_norm_*, jacobi_solve_f64; no paper counterpart:
+ * the paper's loop tiling and unrolling are compile-time passes, Sec. 6 and
+ * 6.1, where this picks tile shapes by timing them).  One entry per (device name, element
+ * size, radius, nx, ny, nz) holds the kernel variant (the tile shape: 0 the
+ * 32 x 8 plane kernel, 1 the 30 x 32-row column kernel, 2 the plane kernel
+ * taking two planes per step), the k chunks each tile column is split into,
+ * and the temporal depth (sweeps fused per pass over HBM, 1 = none).  When
+ * the "star_variant", "star_chunks" and "temporal_depth" knobs are automatic,
+ * a call on grids of those extents uses the entry; with no entry the built-in
+ * plan applies.  Every configuration computes bitwise the same iterates;
+ * residual norms may differ in their last bits (their partial sums follow
+ * the grid).  Changing the cache while calls on the same extents are in
+ * flight is not safe (like the knobs).
+ */
+typedef struct stn_tune_entry {
+  char device[64];        /* device name the entry applies to ("" = the current device's) */
+  int64_t nx, ny, nz;     /* interior extents */
+  int32_t esize;          /* element bytes: 8 double, 4 float */
+  int32_t radius;         /* 1 or 2 */
+  int32_t variant;        /* 0, 1 or 2 (see above) */
+  int32_t chunks;         /* k chunks per tile column, >= 1 */
+  int32_t depth;          /* temporal depth 1..4 */
+  int32_t reserved;
+  double glups;           /* measured rate of this configuration (0 if set by hand) */
+  double default_glups;   /* measured rate of the built-in plan */
+} stn_tune_entry;
+
+/* Times the candidate configurations for sweeps of these extents on two
+ * scratch grids the call allocates (2 x (nx+2r)(ny+2r)(nz+2r) x esize bytes of
+ * device memory, zero-filled, freed before return) on the current device and
+ * `stream`: every kernel variant at k-chunk counts around the built-in plan
+ * (its own, half, twice and four times it, and the counts giving 2, 4, 6, 8
+ * and 16 blocks per SM), and temporal depths 2..4; each candidate runs 12 sweeps (`trial_sweeps` > 0 overrides) after
+ * two untimed ones, timed by CUDA events, in two rounds (the faster round
+ * counts).  The fastest configuration is stored in the cache and copied to
+ * *best; the built-in plan is kept unless another is more than 2 % faster.
+ * coeffs: host array of radius+1 doubles, or NULL for {0, 1/6[, 0]}.
+ * When the environment variable STN_TUNE_CACHE names a file, the cache is
+ * written there after tuning.  Synchronises `stream`.
+ * Errors: STN_EINVAL (bad extents, radius or esize, NULL best), STN_ENOMEM,
+ * STN_ECUDA. */
+int stencil_autotune_sweep(int64_t nx, int64_t ny, int64_t nz, int esize, int radius,
+                           const double* coeffs, int trial_sweeps, stn_tune_entry* best, void* stream);
+/* Adds or replaces an entry (device "" = the current device's name).
+ * STN_EINVAL for bad extents, radius, esize, variant (0..2), chunks (1..65535)
+ * or depth (1..4). */
+int stencil_tune_cache_put(const stn_tune_entry* entry);
+/* Looks up the entry for (device, extents, esize, radius); device NULL or ""
+ * = the current device's name.  Returns 1 and fills *out when found, 0 when
+ * not, STN_EINVAL on bad arguments.  The first lookup in a process loads
+ * the file named by STN_TUNE_CACHE, if set and readable. */
+int stencil_tune_cache_get(const char* device, int64_t nx, int64_t ny, int64_t nz, int esize, int radius,
+                           stn_tune_entry* out);
+/* Number of entries. */
+int64_t stencil_tune_cache_size(void);
+/* Removes every entry. */
+int stencil_tune_cache_clear(void);
+/* Writes every entry to `path` as JSON ({"stencil_tune_cache": 1, "entries":
+ * [{...}, ...]}, one entry per line).  STN_EINVAL for a NULL path or a file
+ * that cannot be written (the reason in stencil_last_error). */
+int stencil_tune_cache_save(const char* path);
+/* Reads entries written by stencil_tune_cache_save and adds them (replacing
+ * entries with the same key).  Returns the number of entries read (>= 0), or
+ * STN_EINVAL for a NULL path, an unreadable file or a malformed entry (then
+ * nothing is added). */
+int stencil_tune_cache_load(const char* path);
 
 /*
  * stencil_sweep_f64 / _f32 -- `iters` Jacobi sweeps of the constant-

@@ -77,6 +77,18 @@ class ServerStats(ctypes.Structure):
                 ("running", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t), ("status", ctypes.c_int)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_char * 64), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("esize", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("chunks", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("glups", ctypes.c_double), ("default_glups", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["device"] = self.device.decode()
+        return d
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
                       "(python -c 'import __graft_entry__ as g; g.build()')")
@@ -97,6 +109,13 @@ SIGNATURES = {
     "stencil_tune_set": (_int, [ctypes.c_char_p, _i64]),
     "stencil_tune_get": (_int, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
     "stencil_sched_stats": (_int, [ctypes.POINTER(ctypes.c_uint64), _int]),
+    "stencil_autotune_sweep": (_int, [_i64, _i64, _i64, _int, _int, _dp, _int, ctypes.POINTER(TuneEntry), _vp]),
+    "stencil_tune_cache_put": (_int, [ctypes.POINTER(TuneEntry)]),
+    "stencil_tune_cache_get": (_int, [ctypes.c_char_p, _i64, _i64, _i64, _int, _int, ctypes.POINTER(TuneEntry)]),
+    "stencil_tune_cache_size": (_i64, []),
+    "stencil_tune_cache_clear": (_int, []),
+    "stencil_tune_cache_save": (_int, [ctypes.c_char_p]),
+    "stencil_tune_cache_load": (_int, [ctypes.c_char_p]),
     "stencil_sweep_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_sweep_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
@@ -459,6 +478,46 @@ def stencil_tune_get(knob: str) -> int:
     v = _i64(0)
     _check(_lib.stencil_tune_get(knob.encode(), ctypes.byref(v)))
     return v.value
+
+
+def stencil_autotune_sweep(nx, ny, nz, esize, radius, coeffs=None, trial_sweeps=0, stream=None) -> dict:
+    """Times the sweep configurations for these extents on the device, stores
+    the fastest in the tuning cache and returns it (TuneEntry fields)."""
+    e = TuneEntry()
+    cp, _keep = _coeffs(coeffs) if coeffs is not None else (None, None)
+    _check(_lib.stencil_autotune_sweep(nx, ny, nz, esize, radius, cp, trial_sweeps, ctypes.byref(e),
+                                       _stream(stream)))
+    return e.as_dict()
+
+
+def stencil_tune_cache_put(nx, ny, nz, esize, radius, variant, chunks, depth=1, device="", glups=0.0,
+                           default_glups=0.0):
+    e = TuneEntry(device.encode(), nx, ny, nz, esize, radius, variant, chunks, depth, 0, glups, default_glups)
+    return _check(_lib.stencil_tune_cache_put(ctypes.byref(e)))
+
+
+def stencil_tune_cache_get(nx, ny, nz, esize, radius, device=None):
+    """The cache entry for these extents (dict), or None."""
+    e = TuneEntry()
+    found = _check(_lib.stencil_tune_cache_get(device.encode() if device else None, nx, ny, nz, esize, radius,
+                                               ctypes.byref(e)))
+    return e.as_dict() if found else None
+
+
+def stencil_tune_cache_size() -> int:
+    return _lib.stencil_tune_cache_size()
+
+
+def stencil_tune_cache_clear():
+    return _check(_lib.stencil_tune_cache_clear())
+
+
+def stencil_tune_cache_save(path: str):
+    return _check(_lib.stencil_tune_cache_save(os.fsencode(path)))
+
+
+def stencil_tune_cache_load(path: str) -> int:
+    return _check(_lib.stencil_tune_cache_load(os.fsencode(path)))
 
 
 class Server:

@@ -289,9 +289,14 @@ static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeff
   T* cur = din;
   T* nxt = dout;
   // temporal blocking: `depth` sweeps per pass while at least that many remain
-  int depth = tune_get_temporal_depth();
-  if (depth == 0) depth = 1;  // automatic: single sweeps (measured faster on GB300 so far)
+  // precedence: the autotuner's trial, the knob, the tuning cache, single
+  // sweeps (the built-in choice: measured faster on GB300 so far)
+  int depth = star_force().depth > 0 ? star_force().depth : tune_get_temporal_depth();
+  StarChoice tc;
+  if (depth == 0 && tune_cache_lookup(g, sizeof(T), &tc) && tc.depth > 0) depth = tc.depth;
+  if (depth == 0) depth = 1;
   depth = temporal_depth_supported(depth, sizeof(T), radius);
+  star_last().depth = depth;
   i64 it = 0;
   if (depth > 1) {
     for (; it + depth <= iters; it += depth) {
@@ -1091,6 +1096,18 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "sched_idle_ms") == 0) {
     *value = f.idle_ms;
+    return STN_OK;
+  }
+  if (strcmp(knob, "last_star_variant") == 0) {
+    *value = star_last().variant;
+    return STN_OK;
+  }
+  if (strcmp(knob, "last_star_chunks") == 0) {
+    *value = star_last().chunks;
+    return STN_OK;
+  }
+  if (strcmp(knob, "last_temporal_depth") == 0) {
+    *value = star_last().depth;
     return STN_OK;
   }
   if (strcmp(knob, "fault_admit_fail") == 0) {

@@ -78,6 +78,26 @@ int star_variant(const Grid& g, size_t esize, const void* a, const void* b, cons
 // Tuning override of the variant choice (-1 = automatic).
 int tune_set_star_variant(int v);
 int tune_get_star_variant();
+// A star-sweep configuration: kernel variant (-1 = not set), k chunks per
+// tile column (0 = not set), temporal depth (0 = not set); no_cache makes
+// the planners ignore the tuning cache.
+struct StarChoice {
+  int variant = -1;
+  int chunks = 0;
+  int depth = 0;
+  bool no_cache = false;
+};
+// The configuration the autotuner forces on this thread while it times a
+// candidate (takes precedence over the knobs and the cache).
+StarChoice& star_force();
+// The configuration of this thread's last star launch (variant, chunks) and
+// last stencil_sweep call (depth): read through stencil_tune_get.
+StarChoice& star_last();
+// The tuning-cache entry for sweeps of g's extents and radius with elements
+// of `esize` bytes on the current device, if any (tune.cu).
+bool tune_cache_lookup(const Grid& g, size_t esize, StarChoice* out);
+// SM count of the current device (152 when there is none: planning only).
+int device_sms();
 // Number of per-block partials launch_star writes for these arguments.
 i64 star_blocks(const Grid& g, size_t esize, const void* u, const void* b, const void* out);
 // One launch: out = S u + b over the interior; in residual modes also the

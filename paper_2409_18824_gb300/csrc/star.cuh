@@ -454,6 +454,8 @@ template <typename T, int R, bool HAS_B, bool HAS_C0>
 int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
                   SweepMode mode, double* partials, cudaStream_t s, int variant) {
   const ZPlan p = plan_star(g, variant, sizeof(T));
+  star_last().variant = variant;
+  star_last().chunks = p.chunks;
   StarCoeffs<T, R> cf;
   for (int d = 0; d <= R; d++) cf.c[d] = (T)coeffs[d];
   dim3 grid(p.tiles_x, p.tiles_y, p.chunks);

@@ -30,6 +30,33 @@ int tune_set_star_chunks(int c) {
 }
 int tune_get_star_chunks() { return g_star_chunks; }
 
+StarChoice& star_force() {
+  static thread_local StarChoice f;
+  return f;
+}
+
+StarChoice& star_last() {
+  static thread_local StarChoice f;
+  return f;
+}
+
+int device_sms() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return 152;
+  }
+  if (cache[dev] > 0) return cache[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    (void)cudaGetLastError();
+    return 152;
+  }
+  cache[dev] = sms;
+  return sms;
+}
+
 template <typename K>
 static int occupancy(K kernel, int threads) {
   int v = 0;
@@ -80,7 +107,7 @@ ZPlan plan_star(const Grid& g, int variant, size_t esize) {
     // wave beats 1.2-1.9 waves by 15-20 % on this memory-bound kernel)
     p.tiles_x = (int)((g.nx + (32 - 2 * g.r) - 1) / (32 - 2 * g.r));
     p.tiles_y = (int)((g.ny + SC_WARPS * SC_TJ - 1) / (SC_WARPS * SC_TJ));
-    const i64 slots = (i64)152 * star_resident(variant, esize, g.r);
+    const i64 slots = (i64)device_sms() * star_resident(variant, esize, g.r);
     const i64 tiles = (i64)p.tiles_x * p.tiles_y;
     chunks = slots / (tiles > 0 ? tiles : 1);
   } else {
@@ -89,7 +116,7 @@ ZPlan plan_star(const Grid& g, int variant, size_t esize) {
     i64 resident = esize == 4 ? 8 : 5;
     if (variant == kStarPlane2) resident = esize == 4 ? 6 : 4;
     // enough blocks to fill every SM
-    const i64 want = 152 * resident;
+    const i64 want = (i64)device_sms() * resident;
     const i64 tiles = (i64)p.tiles_x * p.tiles_y;
     chunks = (want + tiles - 1) / tiles;
     if (esize == 8) {
@@ -103,7 +130,14 @@ ZPlan plan_star(const Grid& g, int variant, size_t esize) {
       if (c16 > chunks) chunks = c16;
     }
   }
-  if (g_star_chunks > 0) chunks = g_star_chunks;
+  // precedence: the autotuner's trial, the knob, the tuning cache, the plan
+  StarChoice tc;
+  if (star_force().chunks > 0)
+    chunks = star_force().chunks;
+  else if (g_star_chunks > 0)
+    chunks = g_star_chunks;
+  else if (tune_cache_lookup(g, esize, &tc) && tc.variant == variant && tc.chunks > 0)
+    chunks = tc.chunks;
   if (chunks > max_chunks) chunks = max_chunks;
   if (chunks < 1) chunks = 1;
   p.kchunk = (int)((g.nz + chunks - 1) / chunks);
@@ -118,8 +152,11 @@ int star_variant(const Grid& g, size_t esize, const void* a, const void* b, cons
   (void)c;
   // the column kernel addresses rows with 32-bit offsets: TJ + 2R rows of NX
   if ((i64)(SC_TJ + 4) * g.NX() >= ((i64)1 << 31)) return kStarScalar;
+  if (star_force().variant >= 0) return star_force().variant;
   const int ov = g_star_variant_override;
   if (ov >= 0) return ov;
+  StarChoice tc;
+  if (tune_cache_lookup(g, esize, &tc) && tc.variant >= 0) return tc.variant;
   // float sweeps are memory-bound: the column kernel issues the fewest
   // instructions per update.  Double sweeps are bound by the FP64 pipe: the
   // plane kernel keeps every lane of every FP64 instruction useful.

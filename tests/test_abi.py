@@ -14,7 +14,8 @@ HEADER = os.path.join(ROOT, "include", "stencil.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char|stn_server)\s*\**\s*(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int64_t|int|void|char|stn_server)\s*\**\s*(\w+)\s*\(", src,
+                       flags=re.M)
     return sorted(set(names))
 
 
@@ -176,6 +177,119 @@ def test_tuning_knobs(lib):
         lib.stencil_tune_set(knob, good)
         assert lib.stencil_tune_get(knob) == good
         lib.stencil_tune_set(knob, before)
+
+
+def test_header_parser_sees_every_return_type():
+    names = declared_functions()
+    assert "stencil_tune_cache_size" in names and "stencil_last_error" in names and "stn_server_create" in names
+
+
+@pytest.fixture
+def empty_cache(lib):
+    lib.stencil_tune_cache_clear()
+    yield
+    lib.stencil_tune_cache_clear()
+
+
+def test_tune_cache_put_get_save_load(lib, empty_cache, tmp_path):
+    """The tuning cache round-trips through its JSON file: every field, device
+    names with quotes and braces, replacement of an entry with the same key."""
+    lib.stencil_tune_cache_put(512, 512, 512, 8, 1, 0, 32, 1, device="GPU A", glups=86.25, default_glups=85.5)
+    lib.stencil_tune_cache_put(70, 45, 100, 4, 2, 1, 3, 2, device='odd "name" {x}')
+    lib.stencil_tune_cache_put(512, 512, 512, 8, 1, 2, 16, 1, device="GPU A")  # replaces the first
+    assert lib.stencil_tune_cache_size() == 2
+    e = lib.stencil_tune_cache_get(512, 512, 512, 8, 1, device="GPU A")
+    assert (e["variant"], e["chunks"], e["depth"], e["glups"]) == (2, 16, 1, 0.0)
+    assert lib.stencil_tune_cache_get(512, 512, 512, 8, 2, device="GPU A") is None  # other radius
+    assert lib.stencil_tune_cache_get(512, 512, 512, 4, 1, device="GPU A") is None  # other type
+    assert lib.stencil_tune_cache_get(512, 512, 512, 8, 1, device="GPU B") is None  # other device
+    path = str(tmp_path / "tune.json")
+    lib.stencil_tune_cache_save(path)
+    import json
+    doc = json.load(open(path))
+    assert doc["stencil_tune_cache"] == 1 and len(doc["entries"]) == 2
+    lib.stencil_tune_cache_clear()
+    assert lib.stencil_tune_cache_size() == 0
+    assert lib.stencil_tune_cache_load(path) == 2
+    e = lib.stencil_tune_cache_get(70, 45, 100, 4, 2, device='odd "name" {x}')
+    assert (e["nx"], e["ny"], e["nz"], e["variant"], e["chunks"], e["depth"]) == (70, 45, 100, 1, 3, 2)
+    # a hand-written file with fields in another order and extra keys loads too
+    other = tmp_path / "hand.json"
+    other.write_text('{"entries": [{"depth": 3, "chunks": 5, "variant": 0, "nz": 9, "ny": 8, "nx": 7, '
+                     '"radius": 1, "esize": 8, "device": "GPU C", "note": "x"}], "stencil_tune_cache": 1}')
+    assert lib.stencil_tune_cache_load(str(other)) == 1
+    assert lib.stencil_tune_cache_get(7, 8, 9, 8, 1, device="GPU C")["depth"] == 3
+
+
+def test_tune_cache_rejects_bad_entries_and_files(lib, empty_cache, tmp_path):
+    good = dict(nx=8, ny=8, nz=8, esize=8, radius=1, variant=0, chunks=1, depth=1, device="d")
+    for field, bad in (("esize", 2), ("radius", 3), ("variant", 3), ("variant", -1), ("chunks", 0),
+                       ("chunks", 65536), ("depth", 0), ("depth", 5), ("nx", 0), ("nz", -4)):
+        args = dict(good, **{field: bad})
+        with pytest.raises(lib.StencilError) as ei:
+            lib.stencil_tune_cache_put(**args)
+        assert ei.value.code == lib.STN_EINVAL
+    with pytest.raises(lib.StencilError):
+        lib.stencil_tune_cache_get(8, 8, 8, 3, 1)
+    assert lib.lib().stencil_tune_cache_save(None) == lib.STN_EINVAL
+    assert lib.lib().stencil_tune_cache_load(None) == lib.STN_EINVAL
+    assert lib.lib().stencil_tune_cache_put(None) == lib.STN_EINVAL
+    with pytest.raises(lib.StencilError):
+        lib.stencil_tune_cache_load(str(tmp_path / "missing.json"))
+    with pytest.raises(lib.StencilError):
+        lib.stencil_tune_cache_save(str(tmp_path / "no_dir" / "x.json"))
+    bad_files = [
+        '{"something_else": 1}',
+        '{"stencil_tune_cache": 1}',
+        '{"stencil_tune_cache": 1, "entries": [{"device": "d", "esize": 8}]}',  # fields missing
+        '{"stencil_tune_cache": 1, "entries": [{"device": "d", "esize": 8, "radius": 1, "nx": 8, "ny": 8, '
+        '"nz": 8, "variant": 7, "chunks": 1, "depth": 1}]}',  # out of range
+        '{"stencil_tune_cache": 1, "entries": [{"device": "d", "esize": 8, "radius": 1, "nx": 8.5, "ny": 8, '
+        '"nz": 8, "variant": 0, "chunks": 1, "depth": 1}]}',  # not an integer
+        '{"stencil_tune_cache": 1, "entries": [{"device": "d", "esize": 8',  # truncated
+    ]
+    for i, text in enumerate(bad_files):
+        f = tmp_path / f"bad{i}.json"
+        f.write_text(text)
+        with pytest.raises(lib.StencilError):
+            lib.stencil_tune_cache_load(str(f))
+    assert lib.stencil_tune_cache_size() == 0  # a bad file adds nothing
+    # a file with one good entry before a bad one adds nothing either
+    f = tmp_path / "half.json"
+    f.write_text('{"stencil_tune_cache": 1, "entries": [{"device": "d", "esize": 8, "radius": 1, "nx": 8, '
+                 '"ny": 8, "nz": 8, "variant": 0, "chunks": 1, "depth": 1}, {"device": "d"}]}')
+    with pytest.raises(lib.StencilError):
+        lib.stencil_tune_cache_load(str(f))
+    assert lib.stencil_tune_cache_size() == 0
+
+
+def test_tune_cache_loads_from_environment(tmp_path):
+    """STN_TUNE_CACHE names a file that the first lookup in a process loads."""
+    import subprocess
+    import sys
+    f = tmp_path / "env.json"
+    f.write_text('{"stencil_tune_cache": 1, "entries": [{"device": "E", "esize": 4, "radius": 2, "nx": 3, '
+                 '"ny": 4, "nz": 5, "variant": 1, "chunks": 2, "depth": 1}]}')
+    code = ("import paper_2409_18824_gb300 as s; e = s.stencil_tune_cache_get(3, 4, 5, 4, 2, device='E'); "
+            "print(s.stencil_tune_cache_size(), e['variant'], e['chunks'])")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120,
+                       env=dict(os.environ, STN_TUNE_CACHE=str(f)))
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == ["1", "1", "2"]
+
+
+def test_autotune_rejects_bad_arguments(lib):
+    so = lib.lib()
+    e = lib.TuneEntry()
+    for args in ((0, 8, 8, 8, 1), (8, 8, 8, 2, 1), (8, 8, 8, 8, 3), (1 << 29, 8, 8, 8, 1)):
+        assert so.stencil_autotune_sweep(*args, None, 0, ctypes.byref(e), None) == lib.STN_EINVAL
+    assert so.stencil_autotune_sweep(8, 8, 8, 8, 1, None, -1, ctypes.byref(e), None) == lib.STN_EINVAL
+    assert so.stencil_autotune_sweep(8, 8, 8, 8, 1, None, 0, None, None) == lib.STN_EINVAL
+
+
+def test_read_only_plan_knobs_exist(lib):
+    for knob in ("last_star_variant", "last_star_chunks", "last_temporal_depth"):
+        lib.stencil_tune_get(knob)
 
 
 def test_server_rejects_bad_options(lib):
