@@ -1064,7 +1064,7 @@ def run_serving(args):
 
     def run_trace(arrivals):
         """Submits request i at arrivals[i] seconds; returns (makespan, latencies)."""
-        with stn.Server(hbm_budget=budget, tol=1e-8, refined=refined, inner_sweeps=200000, inner_tol=1e-2,
+        with stn.Server(hbm_budget=budget, tol=args.tol, refined=refined, inner_sweeps=200000, inner_tol=1e-2,
                         check_every=50, max_outer=40, max_inflight=64) as srv:
             t0 = time.perf_counter()
             tickets = []
@@ -1097,7 +1097,7 @@ def run_serving(args):
                 i, t_sub = item
                 d_b = torch.from_numpy(rhss[i]).cuda()
                 d_u = torch.zeros_like(d_b)
-                rc, info = stn.jacobi_solve_f64(d_b, d_u, si.LAPLACE7, 1, 1e-8, 10 ** 7, 50)
+                rc, info = stn.jacobi_solve_f64(d_b, d_u, si.LAPLACE7, 1, args.tol, 10 ** 7, 50)
                 d_u.cpu()
                 done[i] = time.perf_counter() - t_sub
                 status[i] = info["status"]
@@ -1130,12 +1130,12 @@ def run_serving(args):
                           "p50_s": float(np.percentile(lat_l, 50)), "p99_s": float(np.percentile(lat_l, 99)),
                           "converged": int(sum(1 for x in st_l if x == 0))})
     out = {
-        "metric": "serving solves/s and p50/p99 latency (Poisson arrivals, sizes log-U[32,256], tol 1e-8)",
+        "metric": f"serving solves/s and p50/p99 latency (Poisson arrivals, sizes log-U[32,256], tol {args.tol:g})",
         "value": capacity, "unit": "solves/s", "n_gpus": ws, "steps": 1, "warmup": 0,
         "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if (args.per_request or not refined) else "f32+f64 refined", "data": "synthetic",
         "config": {"workload": f"{n} Poisson solve requests, per-axis sizes log-uniform in [32,256] (seed 6), "
-                               f"rhs N(0,1), tol 1e-8, " + (
+                               f"rhs N(0,1), tol {args.tol:g}, " + (
                                    "one double jacobi_solve_f64 per request in arrival order (the plain path)"
                                    if args.per_request else
                                    "40 GiB admission budget, continuous batching"
@@ -1220,6 +1220,8 @@ def main():
     ap.add_argument("--rates", type=float, nargs="*", default=None,
                     help="serving workload: absolute offered rates (solves/s) instead of --loads fractions")
     ap.add_argument("--batch", type=int, default=2048, help="problems in the batched workload")
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="serving workload: relative residual each request is solved to")
     ap.add_argument("--refined", action="store_true", help="batched workload: FP32 sweeps + FP64 refinement")
     ap.add_argument("--inner-tol", type=float, default=1e-2)
     ap.add_argument("--inner-max", type=int, default=200000)
