@@ -98,7 +98,8 @@ int stencil_release_workspace(void);
 /*
  * stencil_tune_set / stencil_tune_get -- process-wide kernel-selection knobs
  * (no paper counterpart; the paper's own tuning is compile-time, Sec. 6).
- *   "star_variant": -1 automatic (default: 1 for float, 0 for double),
+ *   "star_variant": -1 automatic (default: 1 for float at radius 1, 2 for
+ *                   float at radius 2, 0 for double),
  *                   0 shared-memory plane kernel (one point per thread),
  *                   1 register/shuffle column kernel (8 j rows per thread,
  *                   no shared memory), 2 plane kernel taking two k planes

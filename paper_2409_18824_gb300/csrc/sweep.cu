@@ -113,12 +113,14 @@ ZPlan plan_star(const Grid& g, int variant, size_t esize) {
   } else {
     p.tiles_x = (int)((g.nx + TX - 1) / TX);
     p.tiles_y = (int)((g.ny + TY - 1) / TY);
-    i64 resident = esize == 4 ? 8 : 5;
-    if (variant == kStarPlane2) resident = esize == 4 ? 6 : 4;
-    // enough blocks to fill every SM
-    const i64 want = (i64)device_sms() * resident;
+    const i64 slots = (i64)device_sms() * star_resident(variant, esize, g.r);
     const i64 tiles = (i64)p.tiles_x * p.tiles_y;
-    chunks = (want + tiles - 1) / tiles;
+    // waves of resident blocks: one for the float plane kernel; two for
+    // double, whose blocks keep the FP64 pipe busy only while resident (128^3:
+    // 60 -> 73 GLUP/s); four for the float two-plane kernel, the radius-2
+    // float default (512^3: 229 GLUP/s for the column kernel, 355 here)
+    const i64 waves = esize == 8 ? 2 : (variant == kStarPlane2 ? 4 : 1);
+    chunks = (waves * slots + tiles - 1) / tiles;
     if (esize == 8) {
       // double sweeps are bound by the FP64 pipe, so the extra halo planes of
       // short chunks cost little while many short blocks keep every SM's pipe
@@ -157,10 +159,13 @@ int star_variant(const Grid& g, size_t esize, const void* a, const void* b, cons
   if (ov >= 0) return ov;
   StarChoice tc;
   if (tune_cache_lookup(g, esize, &tc) && tc.variant >= 0) return tc.variant;
-  // float sweeps are memory-bound: the column kernel issues the fewest
-  // instructions per update.  Double sweeps are bound by the FP64 pipe: the
-  // plane kernel keeps every lane of every FP64 instruction useful.
-  return esize == 4 ? kStarColumn : kStarScalar;
+  // float sweeps are memory-bound: at radius 1 the column kernel issues the
+  // fewest instructions per update; at radius 2 its register rings cost too
+  // much occupancy and the two-plane kernel is faster (measured 1.3-1.6x).
+  // Double sweeps are bound by the FP64 pipe: the plane kernel keeps every
+  // lane of every FP64 instruction useful.
+  if (esize == 4) return g.r == 1 ? kStarColumn : kStarPlane2;
+  return kStarScalar;
 }
 
 i64 star_blocks(const Grid& g, size_t esize, const void* u, const void* b, const void* out) {
