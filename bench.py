@@ -526,6 +526,62 @@ def run_reference2d(args):
     }), flush=True)
 
 
+# ----------------------- the paper's threaded jacobi on the host cores ----
+# Table 4 of the paper: speed-up over serial of its OpenMP jacobi (its MLIR
+# flow) on 2..64 cores of its CPU.  Context for the host path's scaling.
+PAPER_OPENMP_JACOBI_SPEEDUP = {2: 1.95, 4: 4.01, 8: 5.77, 16: 13.14, 32: 26.14, 64: 72.62}
+
+
+def run_jacobi2d_host(args):
+    """The multi-core host path (libstencil_host.so) on the paper's jacobi
+    grid: K timed steps of `--host-sweeps` sweeps on every hardware thread,
+    then the scaling curve over 1, 2, 4, ... threads (one timed run each)."""
+    import paper_2409_18824_gb300.host as hp
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    nx, ny, sweeps = JACOBI2D["nx"], JACOBI2D["ny"], args.host_sweeps
+    u0 = si.uniform_interior2d(nx, ny, 1, seed=JACOBI2D["seed"])
+    a, out = u0.copy(), np.zeros_like(u0)
+    tmax = hp.threads()
+
+    def run(T, k):
+        a[...] = u0
+        t0 = time.perf_counter()
+        hp.stencil_host_sweep2d_f64(a, out, si.LAPLACE5, 1, k, nthreads=T)
+        norm = hp.stencil_host_residual_norm2d_f64(out, si.LAPLACE5, 1, nthreads=T)
+        return time.perf_counter() - t0, norm
+
+    for _ in range(args.warmup):
+        run(tmax, max(1, sweeps // 10))
+    times = [run(tmax, sweeps)[0] for _ in range(args.steps)]
+    total = sum(times)
+    value = float(nx) * ny * sweeps * args.steps / total / 1e9
+    curve = {}
+    for T in sorted({t for t in (1, 2, 4, 8, 16, 32, 64) if t <= tmax} | {tmax}):
+        dt, _ = run(T, sweeps)
+        curve[T] = float(nx) * ny * sweeps / dt / 1e9
+    speedup = {T: curve[T] / curve[1] for T in curve}
+    full_s = {T: float(nx) * ny * JACOBI2D["sweeps"] / (curve[T] * 1e9) for T in curve}
+    print(json.dumps({
+        "metric": "GLUP/s (the paper's 2-D jacobi, 1024^2 FP64, multi-core host path)",
+        "value": value, "unit": "GLUP/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": JACOBI2D["desc"] + "; host threads, each step " + f"{sweeps} sweeps + 1 residual "
+                               "norm instead of 100000", "nx": nx, "ny": ny, "radius": 1, "sweeps_per_step": sweeps,
+                   "threads": tmax, "parallelism": "host threads (libstencil_host.so)"},
+        "scaling_curve": {"glups": curve, "speedup": speedup,
+                          "paper_table4_speedup": PAPER_OPENMP_JACOBI_SPEEDUP,
+                          "projected_full_run_s": full_s,
+                          "paper_serial_s": {"mlir_flow": 249.08, "cray": 109.89}},
+        "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+        "host": host_info(),
+    }), flush=True)
+
+
 # ------------------------------------ the paper's sum / dotproduct runs ----
 INTRINSICS = {
     "sum": dict(n=32768 * 32768, seed=8, paper_s=1.63, flang_s=1.65,
@@ -1210,7 +1266,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep512", choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "sum", "dot", "advect"])
+    ap.add_argument("--workload", default="sweep512",
+                    choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "jacobi2d_host", "sum",
+                                                 "dot", "advect"])
+    ap.add_argument("--host-sweeps", type=int, default=2000,
+                    help="jacobi2d_host: sweeps per timed step of the multi-core host path")
     ap.add_argument("--requests", type=int, default=48, help="serving workload: requests per trace")
     ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8, 1.1],
                     help="serving workload: offered loads as fractions of the measured capacity")
@@ -1280,6 +1340,12 @@ def main():
             run_reference2d(args)
         else:
             run_jacobi2d(args)
+        return
+    if args.workload == "jacobi2d_host":
+        if args.impl == "reference":
+            run_reference2d(args)
+        else:
+            run_jacobi2d_host(args)
         return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

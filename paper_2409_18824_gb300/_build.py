@@ -47,6 +47,30 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+HOST_SRC = os.path.join(PKG, "host", "stencil_host.cpp")
+HOST_LIB = os.path.join(PKG, "libstencil_host.so")
+# The multi-core host path: its own library, plain C++ (no CUDA), contraction
+# of multiply and add off so that it rounds every operation like the kernels.
+HOST_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off", "-I" + INCLUDE]
+
+
+def build_host(force: bool = False, verbose: bool = False) -> str:
+    deps = [HOST_SRC, os.path.join(INCLUDE, "stencil_host.h")]
+    if force or _stale(HOST_LIB, deps):
+        cxx = shutil.which("g++") or shutil.which("c++")
+        if not cxx:
+            raise RuntimeError("g++ not found")
+        tmp = HOST_LIB + f".tmp{os.getpid()}"
+        cmd = [cxx, *HOST_FLAGS, HOST_SRC, "-o", tmp]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"g++ failed ({r.returncode}):\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, HOST_LIB)
+    return HOST_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -80,3 +104,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(verbose=True))
+    print(build_host(verbose=True))
