@@ -75,7 +75,9 @@ def load_peaks():
 # kernel changes until it is captured again.
 TRAFFIC_BYTES_PER_LUP = {
     ("f64", 0): 491.5e6 / 320 ** 3,   # plane kernel (star_kernel<double,1>, 16-plane chunks)
-    ("f32", -1): 225.6e6 / 320 ** 3,  # column kernel (star_col_kernel<float,1>, 2 planes prefetched)
+    ("f32", 1): 225.6e6 / 320 ** 3,   # column kernel (star_col_kernel<float,1>, 2 planes prefetched)
+    ("f32", 3): 232.9e6 / 320 ** 3,   # staged kernel (star_staged_kernel<float,1>, 152 blocks)
+    ("f32", -1): 232.9e6 / 320 ** 3,  # automatic: the staged kernel for these large float grids
 }
 
 # FP64 issue rate of this GPU measured with a throughput probe: 2 double

@@ -98,12 +98,16 @@ int stencil_release_workspace(void);
 /*
  * stencil_tune_set / stencil_tune_get -- process-wide kernel-selection knobs
  * (no paper counterpart; the paper's own tuning is compile-time, Sec. 6).
- *   "star_variant": -1 automatic (default: 1 for float at radius 1, 2 for
- *                   float at radius 2, 0 for double),
+ *   "star_variant": -1 automatic (default: for float grids of at least 3e7
+ *                   points 3, else 1 at radius 1 and 2 at radius 2; 0 for
+ *                   double),
  *                   0 shared-memory plane kernel (one point per thread),
  *                   1 register/shuffle column kernel (8 j rows per thread,
  *                   no shared memory), 2 plane kernel taking two k planes
- *                   per step (more independent work per thread).
+ *                   per step (more independent work per thread), 3 staged
+ *                   kernel (whole rows of a block's planes stream through a
+ *                   shared-memory ring filled by asynchronous 16-byte copies;
+ *                   grids whose rows are too long for the ring use another).
  *   "star_chunks":  0 automatic (default), else the number of k chunks each
  *                   column of tiles is split into (one block per tile and
  *                   chunk; clamped to chunks of >= 4 planes).  Changes the
@@ -171,7 +175,8 @@ int stencil_tune_get(const char* knob, int64_t* value);
  * 6.1, where this picks tile shapes by timing them).  One entry per (device name, element
  * size, radius, nx, ny, nz) holds the kernel variant (the tile shape: 0 the
  * 32 x 8 plane kernel, 1 the 30 x 32-row column kernel, 2 the plane kernel
- * taking two planes per step), the k chunks each tile column is split into,
+ * taking two planes per step, 3 the staged kernel's whole-row blocks), the
+ * k chunks each tile column is split into,
  * and the temporal depth (sweeps fused per pass over HBM, 1 = none).  When
  * the "star_variant", "star_chunks" and "temporal_depth" knobs are automatic,
  * a call on grids of those extents uses the entry; with no entry the built-in
@@ -185,7 +190,7 @@ typedef struct stn_tune_entry {
   int64_t nx, ny, nz;     /* interior extents */
   int32_t esize;          /* element bytes: 8 double, 4 float */
   int32_t radius;         /* 1 or 2 */
-  int32_t variant;        /* 0, 1 or 2 (see above) */
+  int32_t variant;        /* 0, 1, 2 or 3 (see above) */
   int32_t chunks;         /* k chunks per tile column, >= 1 */
   int32_t depth;          /* temporal depth 1..4 */
   int32_t reserved;
@@ -210,7 +215,7 @@ typedef struct stn_tune_entry {
 int stencil_autotune_sweep(int64_t nx, int64_t ny, int64_t nz, int esize, int radius,
                            const double* coeffs, int trial_sweeps, stn_tune_entry* best, void* stream);
 /* Adds or replaces an entry (device "" = the current device's name).
- * STN_EINVAL for bad extents, radius, esize, variant (0..2), chunks (1..65535)
+ * STN_EINVAL for bad extents, radius, esize, variant (0..3), chunks (1..65535)
  * or depth (1..4). */
 int stencil_tune_cache_put(const stn_tune_entry* entry);
 /* Looks up the entry for (device, extents, esize, radius); device NULL or ""

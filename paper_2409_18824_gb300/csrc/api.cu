@@ -637,7 +637,7 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
   if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
   if (int rc = st.add(rhs, bytes, true, false, (void**)&db)) return rc;
   Workspace* ws;
-  if (int rc = get_workspace(s, plan_star(g, kStarScalar, 8).blocks() + plan_star(g, kStarColumn, 8).blocks() + plan_star(g, kStarPlane2, 8).blocks(), bytes, &ws))
+  if (int rc = get_workspace(s, plan_star(g, kStarScalar, 8).blocks() + plan_star(g, kStarColumn, 8).blocks() + plan_star(g, kStarPlane2, 8).blocks() + plan_star(g, kStarStaged, 8).blocks(), bytes, &ws))
     return rc;
   double* tmp = (double*)ws->grid;
   const i64 nb_sweep = star_blocks(g, sizeof(double), du, db, tmp);
@@ -980,7 +980,7 @@ int stencil_tune_set(const char* knob, int64_t value) {
   clear_error();
   if (!knob) return einval("NULL knob");
   if (strcmp(knob, "star_variant") == 0) {
-    if (tune_set_star_variant((int)value) != STN_OK) return einval("star_variant must be -1, 0, 1 or 2");
+    if (tune_set_star_variant((int)value) != STN_OK) return einval("star_variant must be -1, 0, 1, 2 or 3");
     return STN_OK;
   }
   if (strcmp(knob, "temporal_depth") == 0) {

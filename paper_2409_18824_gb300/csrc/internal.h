@@ -43,6 +43,9 @@ struct ZPlan {
   int tiles_x, tiles_y, chunks;
   int kchunk;
   int variant = 0;
+  // staged variant: interior rows per block, elements per ring stage, and
+  // the dynamic shared memory of its ring
+  int rg = 0, stage_elems = 0, smem = 0;
   i64 blocks() const { return (i64)tiles_x * tiles_y * chunks; }
 };
 
@@ -72,8 +75,14 @@ enum SweepMode { kSweep = 0, kSweepResidual = 1, kResidualOnly = 2 };
 // Star-kernel variants: the shared-memory plane kernel (one point per
 // thread), the shuffle/register column kernel, and the plane kernel taking
 // two planes per step.
-enum StarVariant { kStarScalar = 0, kStarColumn = 1, kStarPlane2 = 2 };
+// The staged kernel: whole rows of a block's planes fetched into a
+// shared-memory ring by asynchronous 16-byte copies.
+enum StarVariant { kStarScalar = 0, kStarColumn = 1, kStarPlane2 = 2, kStarStaged = 3 };
+// Shared-memory ring of a staged block: most of an SM's (one block per SM).
+constexpr int kStagedSmemMax = 220 * 1024;
 ZPlan plan_star(const Grid& g, int variant, size_t esize);
+// Whether the staged kernel's ring fits for this grid (rows not too long).
+bool staged_applicable(const Grid& g, size_t esize);
 int star_variant(const Grid& g, size_t esize, const void* a, const void* b, const void* c);
 // Tuning override of the variant choice (-1 = automatic).
 int tune_set_star_variant(int v);

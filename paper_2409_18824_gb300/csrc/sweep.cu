@@ -8,7 +8,7 @@ namespace stn {
 static int g_star_variant_override = -1;
 
 int tune_set_star_variant(int v) {
-  if (v < -1 || v > 2) return STN_EINVAL;
+  if (v < -1 || v > 3) return STN_EINVAL;
   g_star_variant_override = v;
   return STN_OK;
 }
@@ -98,11 +98,83 @@ static int star_resident(int variant, size_t esize, int r) {
   return c;
 }
 
+// Ring layout of the staged kernel for this grid: rows per block so that the
+// SG_PF + 2R + 1 stages fit kStagedSmemMax (at most 64 rows); false when even
+// one row does not fit.
+static bool staged_layout(const Grid& g, size_t esize, int* rg, int* stage_elems, int* smem) {
+  const int S = 2 * g.r + 1 + SG_PF;
+  const i64 row_bytes = g.NX() * (i64)esize;
+  const i64 stage_max = (kStagedSmemMax / S) & ~(i64)15;
+  i64 rows = (stage_max - 32) / row_bytes - 2 * g.r;
+  if (rows < 1) return false;
+  if (rows > 64) rows = 64;
+  if (rows > g.ny) rows = g.ny;
+  const i64 stage_bytes = ((rows + 2 * g.r) * row_bytes + 32 + 15) & ~(i64)15;
+  *rg = (int)rows;
+  *stage_elems = (int)(stage_bytes / (i64)esize);
+  *smem = (int)(stage_bytes * S);
+  return true;
+}
+
+bool staged_applicable(const Grid& g, size_t esize) {
+  int a, b, c;
+  return staged_layout(g, esize, &a, &b, &c);
+}
+
+// Rows per staged block for this grid (0 when the ring does not fit).
+static int staged_rows(const Grid& g, size_t esize) {
+  int rg = 0, b, c;
+  return staged_layout(g, esize, &rg, &b, &c) ? rg : 0;
+}
+
+// Blocks of the staged kernel resident per SM with `smem` bytes of ring.
+static int staged_resident(size_t esize, int r, int smem) {
+  static int cache_smem[2][3] = {};
+  static int cache_val[2][3] = {};
+  const int e = esize == 8 ? 1 : 0;
+  if (cache_smem[e][r] == smem && cache_val[e][r] > 0) return cache_val[e][r];
+  int v = 0;
+  auto query = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 32 * SG_WARPS, smem);
+    return e;
+  };
+  cudaError_t err;
+  if (esize == 8)
+    err = r == 1 ? query(star_staged_kernel<double, 1, false, false, kSweep>)
+                 : query(star_staged_kernel<double, 2, false, false, kSweep>);
+  else
+    err = r == 1 ? query(star_staged_kernel<float, 1, false, false, kSweep>)
+                 : query(star_staged_kernel<float, 2, false, false, kSweep>);
+  if (err != cudaSuccess || v < 1) {
+    (void)cudaGetLastError();
+    return 2;  // no device (planning only): the design point
+  }
+  cache_smem[e][r] = smem;
+  cache_val[e][r] = v;
+  return v;
+}
+
 ZPlan plan_star(const Grid& g, int variant, size_t esize) {
   ZPlan p;
   const i64 max_chunks = (g.nz + 3) / 4;  // chunks of >= 4 planes
   i64 chunks;
-  if (variant == kStarColumn) {
+  if (variant == kStarStaged && !staged_layout(g, esize, &p.rg, &p.stage_elems, &p.smem)) variant = kStarScalar;
+  if (variant == kStarStaged) {
+    // whole rows per block, one block per SM.  At most one wave: a partial
+    // second wave of these long blocks nearly doubles the time (512^3 float,
+    // 21 row groups: 7 chunks = 147 blocks 704 GLUP/s, 8 chunks = 168 blocks
+    // 417).  When one wave leaves more than a quarter of the SMs idle (many
+    // row groups), many short chunks instead: at least 8 waves, so the tail
+    // is short (768 x 768 x 384 radius 2: 277 GLUP/s in 120 blocks, 401 in
+    // 1560).
+    p.tiles_x = 1;
+    p.tiles_y = (int)((g.ny + p.rg - 1) / p.rg);
+    const i64 slots = (i64)device_sms() * staged_resident(esize, g.r, p.smem);
+    const i64 tiles = p.tiles_y;
+    chunks = slots / tiles;
+    if (chunks < 1 || 4 * chunks * tiles < 3 * slots) chunks = (8 * slots + tiles - 1) / tiles;
+  } else if (variant == kStarColumn) {
     // one wave at most: k chunks = resident slots / tiles (measured: a partial
     // wave beats 1.2-1.9 waves by 15-20 % on this memory-bound kernel)
     p.tiles_x = (int)((g.nx + (32 - 2 * g.r) - 1) / (32 - 2 * g.r));
@@ -154,17 +226,30 @@ int star_variant(const Grid& g, size_t esize, const void* a, const void* b, cons
   (void)c;
   // the column kernel addresses rows with 32-bit offsets: TJ + 2R rows of NX
   if ((i64)(SC_TJ + 4) * g.NX() >= ((i64)1 << 31)) return kStarScalar;
-  if (star_force().variant >= 0) return star_force().variant;
-  const int ov = g_star_variant_override;
-  if (ov >= 0) return ov;
+  int v = -1;
   StarChoice tc;
-  if (tune_cache_lookup(g, esize, &tc) && tc.variant >= 0) return tc.variant;
-  // float sweeps are memory-bound: at radius 1 the column kernel issues the
-  // fewest instructions per update; at radius 2 its register rings cost too
-  // much occupancy and the two-plane kernel is faster (measured 1.3-1.6x).
-  // Double sweeps are bound by the FP64 pipe: the plane kernel keeps every
-  // lane of every FP64 instruction useful.
-  if (esize == 4) return g.r == 1 ? kStarColumn : kStarPlane2;
+  if (star_force().variant >= 0)
+    v = star_force().variant;
+  else if (g_star_variant_override >= 0)
+    v = g_star_variant_override;
+  else if (tune_cache_lookup(g, esize, &tc) && tc.variant >= 0)
+    v = tc.variant;
+  // the staged kernel needs a ring stage of at least one row and its halo
+  if (v == kStarStaged && !staged_applicable(g, esize)) v = -1;
+  if (v >= 0) return v;
+  // float sweeps are memory-bound.  Large grids take the staged kernel,
+  // whose shared-memory ring keeps the most bytes in flight (512^3: 705
+  // GLUP/s against 639 for the column kernel; radius 2: 482 against 338).
+  // Below about 3e7 points, or with rows so long that a block holds fewer
+  // than 8, its blocks are too few or too short: at radius 1 the column
+  // kernel issues the fewest instructions per update; at radius 2 its
+  // register rings cost too much occupancy and the two-plane kernel is
+  // faster (1.3-1.6x).  Double sweeps are bound by the FP64 pipe: the plane
+  // kernel keeps every lane of every FP64 instruction useful.
+  if (esize == 4) {
+    if ((double)g.interior() >= 3e7 && staged_rows(g, esize) >= 8) return kStarStaged;
+    return g.r == 1 ? kStarColumn : kStarPlane2;
+  }
   return kStarScalar;
 }
 

@@ -78,7 +78,7 @@ int check_key(i64 nx, i64 ny, i64 nz, int esize, int radius) {
 }
 
 int check_val(int variant, int chunks, int depth) {
-  if (variant < 0 || variant > 2) return tune_einval("variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) return tune_einval("variant must be 0, 1, 2 or 3");
   if (chunks < 1 || chunks > 65535) return tune_einval("chunks must be in [1, 65535]");
   if (depth < 1 || depth > 4) return tune_einval("depth must be in [1, 4]");
   return STN_OK;
@@ -271,8 +271,9 @@ int autotune_t(const Grid& g, const double* coeffs, int sweeps, cudaStream_t s, 
   star_force().variant = kStarColumn;
   const bool col_ok = star_variant(g, sizeof(T), nullptr, nullptr, nullptr) == kStarColumn;
   star_force().variant = -1;
-  for (int v = 0; v <= 2; v++) {
+  for (int v = 0; v <= 3; v++) {
     if (v == kStarColumn && !col_ok) continue;
+    if (v == kStarStaged && !staged_applicable(g, sizeof(T))) continue;
     for (int c : chunk_candidates(g, v, sizeof(T))) {
       StarChoice ch;
       ch.variant = v;
@@ -497,7 +498,7 @@ int stencil_tune_cache_load(const char* path) {
       return tune_einval("malformed tuning cache entry: " + obj);
     (void)json_number(obj, "glups", &glups);
     (void)json_number(obj, "default_glups", &dglups);
-    if (esize > 8 || r > 2 || variant > 2 || chunks > 65535 || depth > 4)
+    if (esize > 8 || r > 2 || variant > 3 || chunks > 65535 || depth > 4)
       return tune_einval("tuning cache entry out of range: " + obj);
     if (int rc = check_key(nx, ny, nz, (int)esize, (int)r)) return rc;
     if (int rc = check_val((int)variant, (int)chunks, (int)depth)) return rc;

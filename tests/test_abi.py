@@ -159,7 +159,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 def test_tuning_knobs(lib):
     assert lib.stencil_tune_get("star_variant") == -1
-    for bad in (-2, 3, 99):
+    for bad in (-2, 4, 99):
         with pytest.raises(lib.StencilError):
             lib.stencil_tune_set("star_variant", bad)
     with pytest.raises(lib.StencilError):
@@ -223,7 +223,7 @@ def test_tune_cache_put_get_save_load(lib, empty_cache, tmp_path):
 
 def test_tune_cache_rejects_bad_entries_and_files(lib, empty_cache, tmp_path):
     good = dict(nx=8, ny=8, nz=8, esize=8, radius=1, variant=0, chunks=1, depth=1, device="d")
-    for field, bad in (("esize", 2), ("radius", 3), ("variant", 3), ("variant", -1), ("chunks", 0),
+    for field, bad in (("esize", 2), ("radius", 3), ("variant", 4), ("variant", -1), ("chunks", 0),
                        ("chunks", 65536), ("depth", 0), ("depth", 5), ("nx", 0), ("nz", -4)):
         args = dict(good, **{field: bad})
         with pytest.raises(lib.StencilError) as ei:

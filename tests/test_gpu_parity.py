@@ -142,12 +142,13 @@ def test_graph_repeated_sweeps_bitwise(lib, cuda, repeat, n_iters):
         lib.stencil_tune_set("repeat_graph", 1)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("r,c", [(1, (0.0, 1 / 6)), (2, (0.2, 0.1, 0.0333))])
 def test_every_kernel_variant_bitwise(lib, cuda, variant, r, c):
-    """The one-point-per-thread kernel and both register-blocked kernels give the
-    same bits (forced through the tuning knob), for sweeps, residuals and a
-    solve, on shapes ragged against every tile size."""
+    """The one-point-per-thread kernel, both register-blocked kernels and the
+    staged (shared-memory ring) kernel give the same bits (forced through the
+    tuning knob), for sweeps, residuals and a solve, on shapes ragged against
+    every tile size."""
     try:
         lib.stencil_tune_set("star_variant", variant)
         for shape in [(64, 64, 64), (37, 19, 11), (130, 33, 9), (62, 70, 5), (2, 1, 3)]:
@@ -174,7 +175,7 @@ def test_every_kernel_variant_bitwise(lib, cuda, variant, r, c):
         lib.stencil_tune_set("star_variant", -1)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_forced_chunk_counts_bitwise(lib, cuda, variant):
     """Forcing the number of k chunks (one block per tile and chunk: ragged last
     chunks, chunks shorter than the radius ring, more chunks than allowed) leaves
@@ -198,6 +199,42 @@ def test_forced_chunk_counts_bitwise(lib, cuda, variant):
                 assert abs(lib.residual_norm_f64(to_dev(u0), cf, r) - nref) <= NORM_RTOL * nref
     finally:
         lib.stencil_tune_set("star_chunks", 0)
+        lib.stencil_tune_set("star_variant", -1)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_staged_variant_on_unaligned_grids(lib, cuda, dtype, offset):
+    """The staged kernel copies 16-byte chunks of the aligned span around each
+    plane's rows and falls back to single elements where a chunk would reach
+    outside the grid: grids starting 1-3 elements past a 16-byte boundary, and
+    ending off one, give the oracle's bits; long rows that leave no room for a
+    ring stage fall back to another kernel."""
+    import torch
+    try:
+        lib.stencil_tune_set("star_variant", 3)
+        for (nx, ny, nz), r, c in (((37, 19, 11), 1, L7), ((29, 13, 9), 2, (0.2, 0.1, 0.0333))):
+            u0 = si.uniform_interior(nx, ny, nz, r, seed=offset, lo=-1, hi=1, dtype=dtype)
+            n = u0.size
+            flat_in = torch.zeros(n + 8, dtype=torch.float64 if dtype == np.float64 else torch.float32,
+                                  device="cuda")
+            flat_out = torch.zeros_like(flat_in)
+            d_in = flat_in[offset:offset + n].view(u0.shape)
+            d_out = flat_out[(offset + 1) % 4:(offset + 1) % 4 + n].view(u0.shape)
+            d_in.copy_(torch.from_numpy(u0))
+            fn = lib.stencil_sweep_f64 if dtype == np.float64 else lib.stencil_sweep_f32
+            fn(d_in, d_out, c, r, 3)
+            assert lib.stencil_tune_get("last_star_variant") == 3
+            assert_bitwise(to_host(d_out), oracle.stencil_sweep(u0, c, r, 3))
+            # the elements around the views are untouched
+            assert not flat_out[:(offset + 1) % 4].any() and not flat_out[(offset + 1) % 4 + n:].any()
+        # rows too long for a ring stage: another kernel runs, same bits
+        u0 = si.uniform_interior(12000, 2, 3, 2, seed=9, dtype=dtype)
+        d_in, d_out = to_dev(u0), to_dev(np.zeros_like(u0))
+        fn(d_in, d_out, (0.2, 0.1, 0.0333), 2, 2)
+        assert lib.stencil_tune_get("last_star_variant") != 3
+        assert_bitwise(to_host(d_out), oracle.stencil_sweep(u0, (0.2, 0.1, 0.0333), 2, 2))
+    finally:
         lib.stencil_tune_set("star_variant", -1)
 
 
