@@ -593,10 +593,11 @@ INTRINSICS = {
 }
 
 
-def intrinsic_inputs(kind):
+def intrinsic_inputs(kind, n=None):
     w = INTRINSICS[kind]
-    x = si.rng(w["seed"]).random(w["n"]) if kind == "sum" else si.rng(w["seed"]).standard_normal(w["n"])
-    y = None if kind == "sum" else si.rng(w["seed"] + 1).standard_normal(w["n"])
+    n = n or w["n"]
+    x = si.rng(w["seed"]).random(n) if kind == "sum" else si.rng(w["seed"]).standard_normal(n)
+    y = None if kind == "sum" else si.rng(w["seed"] + 1).standard_normal(n)
     return x, y
 
 
@@ -612,11 +613,11 @@ def run_intrinsic(args, kind):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    x, y = intrinsic_inputs(kind)
+    n = args.elements or w["n"]  # a smaller case only for profiling
+    x, y = intrinsic_inputs(kind, n)
     dx = torch.from_numpy(x).to(dev)
     dy = None if y is None else torch.from_numpy(y).to(dev)
     stream = torch.cuda.current_stream(dev)
-    n = w["n"]
     nbytes = 8.0 * n * (1 if kind == "sum" else 2)
 
     def step():
@@ -656,15 +657,19 @@ def run_intrinsic(args, kind):
         # one double add per element: bound by the FP64 pipe, not HBM
         fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         achieved = n / sec / 1e12
+        # DRAM bytes of one launch: ncu on a 2^27-element case read 8.02 B per
+        # element (no re-reads), scaled by the elements
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": None, "traffic_unit": "bytes per launch",
+                    "frac": achieved / fp64_peak, "traffic": 8.02 * n, "traffic_unit": "bytes per launch",
                     "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
                     "hbm_achieved_gbs": nbytes / sec / 1e9, "hbm_peak_gbs": hbm_peak,
                     "hbm_frac": nbytes / sec / 1e9 / hbm_peak, "hbm_peak_kind": peak_kind,
                     "kernel": "sum_kernel", "kernel_ms": ms / args.steps, "note": note}
     else:
+        # ncu on the full 2^27-element dot: 2.1476 GB read, 16.0 B per element
         roofline = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": nbytes / sec / 1e9 / hbm_peak, "traffic": None, "traffic_unit": "bytes per launch",
+                    "frac": nbytes / sec / 1e9 / hbm_peak, "traffic": 2.1476e9 / 2 ** 27 * n,
+                    "traffic_unit": "bytes per launch",
                     "peak_kind": peak_kind, "kernel": "vec_reduce_kernel<true>", "kernel_ms": ms / args.steps,
                     "note": note}
     out = {
@@ -1271,6 +1276,8 @@ def main():
     ap.add_argument("--workload", default="sweep512",
                     choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "jacobi2d_host", "sum",
                                                  "dot", "advect"])
+    ap.add_argument("--elements", type=int, default=0,
+                    help="sum/dot: elements instead of the paper's size (for profiling a smaller case)")
     ap.add_argument("--host-sweeps", type=int, default=2000,
                     help="jacobi2d_host: sweeps per timed step of the multi-core host path")
     ap.add_argument("--requests", type=int, default=48, help="serving workload: requests per trace")
