@@ -316,6 +316,55 @@ def test_refined_solve_reaches_tolerance():
     assert np.max(np.abs(u.ravel()[mask] - x)) / np.max(np.abs(x)) < 10 * np.linalg.cond(Ai) * tol
 
 
+def significant_bits(x):
+    """Bits between the highest and lowest set bit of a dyadic double."""
+    if x == 0:
+        return 0
+    num = abs(int(x * 2.0 ** 60))
+    assert num == abs(x) * 2.0 ** 60  # dyadic with denominator <= 2^60
+    while num % 2 == 0:
+        num //= 2
+    return num.bit_length()
+
+
+@pytest.mark.parametrize("r,c,inner", [(1, (0.0, 0.125), 1), (1, (0.0, 0.125), 3), (1, (0.0, 0.125), 5),
+                                       (2, (0.0625, 0.0625, 0.03125), 1), (2, (0.0625, 0.0625, 0.03125), 2),
+                                       (2, (0.0625, 0.0625, 0.03125), 3)])
+def test_refinement_step_is_exact_on_dyadic_data(r, c, inner):
+    """One outer step of the constant-coefficient refinement, pinned step by
+    step in a regime where float arithmetic is exact: dyadic coefficients, a
+    right-hand side of small dyadic values with max |b| = 1 (so the scale is 1
+    and float(rho / s) = b), and few enough inner sweeps that every float
+    value needs at most 24 significant bits.  Then the inner float Jacobi
+    iterate is the exact e_m = sum_{j<m} S^j b, which numpy computes here in
+    double with the dense operator (any order gives the same exact value), the
+    update gives u_1 = e_m bitwise, and the reported relative residual is
+    ||S u_1 + b - u_1|| / ||b|| computed from the dense operator."""
+    nx, ny, nz = 5, 4, 3
+    rng = np.random.default_rng(61 + inner)
+    b = np.zeros(si.padded_shape(nx, ny, nz, r))
+    b[r:-r, r:-r, r:-r] = rng.integers(-8, 9, size=(nz, ny, nx)) / 8.0
+    b[r, r, r] = 1.0  # max |b| = 1
+    mask = interior_mask(nx, ny, nz, r)
+    S = dense_sweep_operator(nx, ny, nz, r, c)
+    bi = b.ravel()[mask]
+    e = np.zeros(b.size)
+    for _ in range(inner):
+        e_new = np.zeros(b.size)
+        e_new[mask] = S @ e + bi  # halo of e stays 0
+        e = e_new
+    # the regime is exact: every iterate value (and so every partial sum on
+    # the way, which carries no finer bits) fits a float's 24-bit significand
+    assert max(significant_bits(v) for v in e) <= 20
+    u, outer, rel, st = oracle.refined_solve(b, np.zeros_like(b), c, r, 0.0, inner, 1)
+    assert outer == 1 and st == 1
+    assert np.array_equal(u.ravel()[mask], e[mask])  # u_1 = 1 * e_m, bitwise
+    assert not u.ravel()[~mask].any()  # the halo is untouched
+    rho = S @ u.ravel() + bi - u.ravel()[mask]
+    want = np.linalg.norm(rho) / np.linalg.norm(bi)
+    assert abs(rel - want) <= 1e-14 * want
+
+
 def test_constant_refined_solve_reaches_tolerance():
     """Constant-coefficient refinement end state: its reported double residual is
     recomputed from the dense operator, and u matches the direct solve of
