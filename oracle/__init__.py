@@ -19,10 +19,12 @@ suffix and are pinned in tests/test_oracle_2d.py.
 
 Pins (tests/test_oracle.py): closed-form eigenmode decay, constant and linear
 invariants, dense brute force, Gaussian elimination, symmetry of the
-variable-coefficient operator.  The refinement driver
-(``varcoef_refined_solve``) is pinned only through its end state (the double
-residual it reports is recomputed independently) -- its inner steps are
-"parity unpinned".
+variable-coefficient operator.  The constant-coefficient refinement
+(``refined_solve``) is pinned step by step in an exact dyadic regime (one
+outer step equals numpy's dense iteration bitwise) and by its end state.  The
+variable-coefficient refinement driver (``varcoef_refined_solve``) is pinned
+only through its end state (the double residual it reports is recomputed
+independently) -- its inner steps are "parity unpinned".
 """
 from __future__ import annotations
 
