@@ -498,35 +498,54 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
   unsigned long long st[SCHED_NSTATS] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long t0 = clock64();
   for (;;) {
-    if (tid_flat() == 0) {
-      s_slot = -1;
-      if (*(volatile int*)a.error != 0) {
-        s_slot = -3;
-      } else {
-        for (int probe = 0; probe < nslots; probe++) {
-          const int si = (cursor + probe) % nslots;
+    if (tid_flat() < 32) {
+      // warp 0 looks at 32 slots per round trip (from the cursor on), then
+      // tries the ones with units left in slot order, one lane at a time: the
+      // claim and its validation are those of a single thread's scan
+      const int lane = tid_flat();
+      // -1 none yet, -3 stop; lane 0 reads the error word so that every lane
+      // takes the same path through the ballots below
+      int found = lane == 0 && *(volatile int*)a.error != 0 ? -3 : -1;
+      found = __shfl_sync(0xffffffffu, found, 0);
+      for (int base = 0; found == -1 && base < nslots; base += 32) {
+        const int si = (cursor + base + lane) % nslots;
+        bool cand = false;
+        if (base + lane < nslots) {
           const unsigned long long w0 = *(volatile unsigned long long*)&a.words[si];
           const int nu = *(volatile int*)&a.slots[si].nunits;
-          if ((int)(w0 & 0xffffffffu) >= nu) continue;
-          const unsigned long long w = atomicAdd(&a.words[si], 1ull);
-          __threadfence();
-          const unsigned pass = (unsigned)(w >> 32);
-          const int q = (int)(w & 0xffffffffu);
-          const SchedSlot S = vload(&a.slots[si]);
-          if (S.pass == pass && q < S.nunits && S.nunits > 0) {
-            s_state = S;
-            s_prob = vload(&a.probs[S.problem]);
-            s_slot = si;
-            s_unit = q;
-            cursor = si;
-            break;
-          }
+          cand = (int)(w0 & 0xffffffffu) < nu;
         }
-        if (s_slot == -1) {
+        unsigned mask = __ballot_sync(0xffffffffu, cand);
+        while (mask && found == -1) {
+          const int l = __ffs(mask) - 1;
+          mask &= mask - 1;
+          int ok = 0;
+          if (lane == l) {
+            const unsigned long long w = atomicAdd(&a.words[si], 1ull);
+            __threadfence();
+            const unsigned pass = (unsigned)(w >> 32);
+            const int q = (int)(w & 0xffffffffu);
+            const SchedSlot S = vload(&a.slots[si]);
+            if (S.pass == pass && q < S.nunits && S.nunits > 0) {
+              s_state = S;
+              s_prob = vload(&a.probs[S.problem]);
+              s_unit = q;
+              ok = 1;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, ok, l)) found = __shfl_sync(0xffffffffu, si, l);
+        }
+      }
+      if (lane == 0) {
+        s_slot = found;
+        if (found >= 0) {
+          cursor = found;
+        } else if (found == -1) {
           if (try_admit(a)) s_slot = -2;
           else if (!a.serving && *(volatile int*)a.finished >= a.count) s_slot = -3;
         }
       }
+      cursor = __shfl_sync(0xffffffffu, cursor, 0);
     }
     __syncthreads();
     const int si = s_slot;
