@@ -1007,12 +1007,36 @@ def run_batched(args):
         "clocks": clk.summary(),
     }
     if rank == 0:
+        if not args.no_cpu_baseline and not refined:
+            out["cpu_baseline"] = cpu_sample_batched(sizes, seeds, pts, iters)
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
 # ----------------------------------------------- variable coefficient (r=2) --
+def cpu_sample_batched(sizes, seeds, pts, iters, n_sample=8, sweeps=1000):
+    """The oracle's Jacobi sweep rate (one thread) on every 256th problem of the
+    mix, `sweeps` sweeps each, projected onto the whole batch with the sweep
+    counts this run took: solves/s = count / sum(points x sweeps / rate)."""
+    import oracle
+    idx = list(range(0, len(sizes), max(1, len(sizes) // n_sample)))[:n_sample]
+    lup, sec = 0.0, 0.0
+    for i in idx:
+        nx, ny, nz = sizes[i]
+        b = si.normal_interior(nx, ny, nz, 1, seed=seeds[i])
+        t0 = time.perf_counter()
+        oracle.stencil_sweep(b, si.LAPLACE7, 1, sweeps)  # the problem's own values as the grid
+        sec += time.perf_counter() - t0
+        lup += float(nx) * ny * nz * sweeps
+    rate = lup / sec
+    total_s = float((pts * iters).sum()) / rate
+    return {"value": len(sizes) / total_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"projected: the oracle's sweep rate {rate / 1e9:.3f} GLUP/s (one thread, {sweeps} sweeps "
+                      f"on each of problems {idx}, {sec:.1f} s) times the sweep counts of this run's "
+                      f"{len(sizes)} solves ({total_s:.0f} s of oracle work)"}
+
+
 def run_varcoef(args):
     """768x768x384 radius-2 variable-coefficient Poisson problem: per-sweep rates at
     full size (float Jacobi sweep, double residual), and complete solves to a
@@ -1044,61 +1068,79 @@ def run_varcoef(args):
         return a, f, ustar
 
     out = {"workload": "varcoef"}
-    # full size: rates
-    nx, ny, nz = 768, 768, 384
-    a, f, ustar = problem(nx, ny, nz)
-    a32, f32 = a.float(), f.float()
-    e0 = torch.zeros_like(f32)
-    e1 = torch.zeros_like(f32)
-    sweeps = 20
-    stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, 2)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, sweeps)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms32 = ev0.elapsed_time(ev1) / sweeps
-    u = torch.zeros_like(f)
-    stn.varcoef_residual_norm_f64(u, a, f, W, R)
-    torch.cuda.synchronize()
-    ev0.record()
-    for _ in range(3):
-        stn.varcoef_residual_norm_f64(u, a, f, W, R)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms_res = ev0.elapsed_time(ev1) / 3
-    u64a, u64b = torch.zeros_like(f), torch.zeros_like(f)
-    ev0.record()
-    stn.varcoef_sweep_f64(u64a, u64b, a, f, W, R, 3)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms64 = ev0.elapsed_time(ev1) / 3
-    pts = float(nx) * ny * nz
-    out["full_size"] = {"grid": [nx, ny, nz], "f32_sweep_ms": ms32, "f32_sweep_glups": pts / ms32 / 1e6,
-                        "f32_sweep_hbm_gbs": 16.0 * pts / ms32 / 1e6, "f64_residual_ms": ms_res,
-                        "f64_sweep_ms": ms64, "f64_sweep_glups": pts / ms64 / 1e6}
-    del a, f, ustar, a32, f32, e0, e1, u, u64a, u64b
-    torch.cuda.empty_cache()
-    # reduced grid: complete solves
-    nx, ny, nz = 96, 96, 48
-    a, f, ustar = problem(nx, ny, nz)
-    res = {}
-    for name in ("refined", "plain_f64"):
+    with ClockSampler(0) as clk:
+        # full size: rates
+        nx, ny, nz = 768, 768, 384
+        a, f, ustar = problem(nx, ny, nz)
+        a32, f32 = a.float(), f.float()
+        e0 = torch.zeros_like(f32)
+        e1 = torch.zeros_like(f32)
+        sweeps = 20
+        stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, 2)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, sweeps)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms32 = ev0.elapsed_time(ev1) / sweeps
         u = torch.zeros_like(f)
+        stn.varcoef_residual_norm_f64(u, a, f, W, R)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        if name == "refined":
-            rc, info = stn.jacobi_solve_varcoef_refined(a, f, u, W, R, 1e-10, 4000, 40)
-        else:
-            rc, info = stn.jacobi_solve_varcoef_f64(a, f, u, W, R, 1e-10, 10 ** 6, 200)
+        ev0.record()
+        for _ in range(3):
+            stn.varcoef_residual_norm_f64(u, a, f, W, R)
+        ev1.record()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        err = float((u - ustar).abs().max() / ustar.abs().max())
-        res[name] = {"seconds": dt, "rc": rc, "rel_res": info["rel_res"], "sweeps": info["iters"],
-                     "outer": info["outer"], "err_vs_manufactured": err}
-    out["reduced_96x96x48"] = res
+        ms_res = ev0.elapsed_time(ev1) / 3
+        u64a, u64b = torch.zeros_like(f), torch.zeros_like(f)
+        ev0.record()
+        stn.varcoef_sweep_f64(u64a, u64b, a, f, W, R, 3)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1) / 3
+        pts = float(nx) * ny * nz
+        out["full_size"] = {"grid": [nx, ny, nz], "f32_sweep_ms": ms32, "f32_sweep_glups": pts / ms32 / 1e6,
+                            "f32_sweep_hbm_gbs": 16.0 * pts / ms32 / 1e6, "f64_residual_ms": ms_res,
+                            "f64_sweep_ms": ms64, "f64_sweep_glups": pts / ms64 / 1e6}
+        del a, f, ustar, a32, f32, e0, e1, u, u64a, u64b
+        torch.cuda.empty_cache()
+        # reduced grid: complete solves
+        nx, ny, nz = 96, 96, 48
+        a, f, ustar = problem(nx, ny, nz)
+        res = {}
+        for name in ("refined", "plain_f64"):
+            u = torch.zeros_like(f)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "refined":
+                rc, info = stn.jacobi_solve_varcoef_refined(a, f, u, W, R, 1e-10, 4000, 40)
+            else:
+                rc, info = stn.jacobi_solve_varcoef_f64(a, f, u, W, R, 1e-10, 10 ** 6, 200)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            err = float((u - ustar).abs().max() / ustar.abs().max())
+            res[name] = {"seconds": dt, "rc": rc, "rel_res": info["rel_res"], "sweeps": info["iters"],
+                         "outer": info["outer"], "err_vs_manufactured": err}
+        out["reduced_96x96x48"] = res
+        clocks = clk.summary()
     ratio = res["plain_f64"]["seconds"] / res["refined"]["seconds"]
+    # e2e: the refined solve through the C ABI with host (numpy) grids, copies included
+    a_h, f_h, us_h = (t.cpu().numpy() for t in (a, f, ustar))
+    u_h = np.zeros_like(f_h)
+    t0 = time.perf_counter()
+    stn.jacobi_solve_varcoef_refined(a_h, f_h, u_h, W, R, 1e-10, 4000, 40)
+    e2e_s = time.perf_counter() - t0
+    fs = out["full_size"]
+    peaks, peak_kind = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    # ncu on a 512 x 512 x 256 float sweep: 830.4 MB read + 253.1 MB written for
+    # 67.1 M updates = 16.15 B per update, scaled to the full grid
+    roofline = {"bound": "hbm", "achieved": fs["f32_sweep_hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": fs["f32_sweep_hbm_gbs"] / hbm_peak, "traffic": 16.15 * 768 * 768 * 384,
+                "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
+                "kernel": "var_col_kernel<float,2> (one float sweep at 768 x 768 x 384)",
+                "kernel_ms": fs["f32_sweep_ms"]}
     line = {"metric": "time to 1e-10 relative residual, variable-coefficient r=2 Poisson (refined vs FP64)",
             "value": ratio, "unit": "speedup (x)", "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": res["refined"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -1106,8 +1148,47 @@ def run_varcoef(args):
             "config": {"workload": "768x768x384 variable-coefficient 13-point Poisson, a ~ U[0.5,1.5] (seed 3), "
                                    "manufactured (1,1,1) sine solution; full-size sweep rates + complete solves "
                                    "on 96x96x48"},
+            "e2e": {"value": res["plain_f64"]["seconds"] / e2e_s, "unit": "speedup (x)",
+                    "h2d_bytes_per_step": 3 * f_h.nbytes, "d2h_bytes_per_step": f_h.nbytes},
+            # kernels of the timed refined solve: one float sweep each, and per outer
+            # step the residual, its maximum, the scaling and the update
+            "gpu_launches": int(res["refined"]["sweeps"] + 4 * res["refined"]["outer"]),
+            "roofline": roofline,
+            "clocks": clocks,
+            "host": host_info(),
             "detail": out}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample_varcoef()
     print(json.dumps(line), flush=True)
+
+
+def cpu_sample_varcoef():
+    """The oracle's own refined vs plain FP64 solves to 1e-10 on a 24 x 24 x 12
+    grid of the workload's construction (one thread; the speedup, the metric's
+    unit), and its float sweep rate on a 192 x 192 x 96 block."""
+    import oracle
+    W, R = si.VARCOEF_W, 2
+    nx, ny, nz = 24, 24, 12
+    a = si.uniform_full(nx, ny, nz, R, seed=3)
+    f = oracle.varcoef_apply(si.sine_mode(nx, ny, nz, R), a, W, R)
+    t0 = time.perf_counter()
+    oracle.varcoef_refined_solve(a, f, np.zeros_like(f), W, R, 1e-10, 4000, 40)
+    t_ref = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.varcoef_jacobi_solve(a, f, np.zeros_like(f), W, R, 1e-10, 10 ** 6, 200)
+    t_plain = time.perf_counter() - t0
+    bx, by, bz = 192, 192, 96
+    a32 = si.uniform_full(bx, by, bz, R, seed=3, dtype=np.float32)
+    f32 = si.normal_interior(bx, by, bz, R, seed=4, dtype=np.float32)
+    e = np.zeros_like(f32)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        e = oracle.varcoef_sweep(e, a32, f32, W, R)
+    t_sw = time.perf_counter() - t0
+    return {"value": t_plain / t_ref, "unit": "speedup (x)", "cores": 1, "kind": "oracle",
+            "sample": f"refined ({t_ref:.2f} s) vs plain FP64 ({t_plain:.2f} s) oracle solves to 1e-10 on a "
+                      f"24 x 24 x 12 grid of the same construction; float sweep {bx * by * bz * 2 / t_sw / 1e9:.3f} "
+                      f"GLUP/s on {bx} x {by} x {bz}"}
 
 
 # ------------------------------------------------------------- serving -----
