@@ -432,11 +432,12 @@ __global__ void __launch_bounds__(32 * WARPS)
 
 // ---------------------------------------------------------------------------
 // Staged variant: a block owns `rg` interior rows j (whole rows in i) of a
-// chunk of planes.  The planes stream through a ring of SG_S shared-memory
-// stages: the rg + 2R rows a plane contributes are one contiguous span of
-// the grid, fetched as 16-byte asynchronous copies (cp.async.cg) of the
-// 16-byte-aligned chunks covering it, SG_PF planes ahead of the ones in use
-// and waited for with cp.async.wait_group (no spin loop).  Chunks that would
+// chunk of planes.  The planes stream through a ring of 2R + 1 + SG_PF
+// shared-memory stages: the rg + 2R rows a plane contributes are one
+// contiguous span of the grid, fetched as 16-byte asynchronous copies
+// (cp.async.cg) of the 16-byte-aligned chunks covering it, SG_PF planes ahead
+// of the 2R + 1 in use, and waited for with cp.async.wait_group (a hardware
+// wait, no spin loop).  Chunks that would
 // reach outside the grid's own bytes (an unaligned first or last element)
 // are copied element by element instead, so nothing outside [u, u + count)
 // is read.  The bytes in flight live in shared memory, not in registers.
