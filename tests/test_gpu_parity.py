@@ -279,6 +279,50 @@ def test_sweep_host_buffers(lib, cuda):
     assert_bitwise(h_out, ref)
 
 
+def test_host_grids_through_the_abi(lib, cuda):
+    """The calls that stage host grids (the path the bench's e2e figures time)
+    give the device calls' bits: residual norm, Jacobi solve, and the
+    variable-coefficient apply, sweep, residual, solve and refined solve; the
+    constant-coefficient refined solve takes device grids only."""
+    nx, ny, nz, r = 29, 17, 13, 1
+    b = si.normal_interior(nx, ny, nz, r, seed=71)
+    u = si.uniform_interior(nx, ny, nz, r, seed=72, lo=-1, hi=1)
+    assert lib.residual_norm_f64(u, L7, r, b=b) == lib.residual_norm_f64(to_dev(u), L7, r, b=to_dev(b))
+    uh = np.zeros_like(b)
+    rc_h, info_h = lib.jacobi_solve_f64(b, uh, L7, r, 1e-8, 20000, 25)
+    ud = to_dev(np.zeros_like(b))
+    rc_d, info_d = lib.jacobi_solve_f64(to_dev(b), ud, L7, r, 1e-8, 20000, 25)
+    assert rc_h == rc_d == 0 and info_h["iters"] == info_d["iters"]
+    assert_bitwise(uh, to_host(ud))
+    R, W = 2, si.VARCOEF_W
+    a = si.uniform_full(nx, ny, nz, R, seed=73)
+    f = si.normal_interior(nx, ny, nz, R, seed=74)
+    v = si.uniform_interior(nx, ny, nz, R, seed=75)
+    oh = np.zeros_like(v)
+    lib.varcoef_apply_f64(v, a, oh, W, R)
+    od = to_dev(np.zeros_like(v))
+    lib.varcoef_apply_f64(to_dev(v), to_dev(a), od, W, R)
+    assert_bitwise(oh, to_host(od))
+    oh = np.zeros_like(v)
+    lib.varcoef_sweep_f64(v.copy(), oh, a, f, W, R, 3)
+    od = to_dev(np.zeros_like(v))
+    lib.varcoef_sweep_f64(to_dev(v), od, to_dev(a), to_dev(f), W, R, 3)
+    assert_bitwise(oh, to_host(od))
+    assert lib.varcoef_residual_norm_f64(v, a, f, W, R) == lib.varcoef_residual_norm_f64(
+        to_dev(v), to_dev(a), to_dev(f), W, R)
+    for solve, args in ((lib.jacobi_solve_varcoef_f64, (1e-8, 200000, 50)),
+                        (lib.jacobi_solve_varcoef_refined, (1e-10, 300, 40))):
+        uh = np.zeros_like(f)
+        rc_h, info_h = solve(a, f, uh, W, R, *args)
+        ud = to_dev(np.zeros_like(f))
+        rc_d, info_d = solve(to_dev(a), to_dev(f), ud, W, R, *args)
+        assert rc_h == rc_d == 0 and info_h["iters"] == info_d["iters"], (solve, info_h, info_d)
+        assert_bitwise(uh, to_host(ud))
+    with pytest.raises(lib.StencilError) as ei:
+        lib.jacobi_solve_refined_f64(b, np.zeros_like(b), L7, r, 1e-8, 100, 0.0, 10, 5)
+    assert ei.value.code == lib.STN_EINVAL
+
+
 def test_eigenmode_decay_1000_sweeps_128(lib, cuda):
     """Property that holds at any size: the (1,1,1) sine mode decays by exactly
     lambda = (cos tx + cos ty + cos tz)/3 per sweep."""
