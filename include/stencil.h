@@ -128,6 +128,9 @@ int stencil_release_workspace(void);
  *                   1 resident whenever it fits.
  *   "sweep2d_chunk": most sweeps per resident 2-D launch (default 32768;
  *                   longer runs take several launches).
+ *   "sweep2d_ctas_per_sm": resident 2-D bands per SM, 1 (default) to 4; fewer
+ *                   when their shared memory does not fit (1024^2 double: 2 at
+ *                   most).  Same results.
  *   "sweep2d_tma":  resident 2-D sweeps fetch the neighbours' rows by bulk
  *                   copy when a row's interior is a multiple of 16 bytes (1,
  *                   default) or always through registers (0).

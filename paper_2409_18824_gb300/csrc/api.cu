@@ -1007,6 +1007,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_var_variant((int)value) != STN_OK) return einval("var_variant must be -1, 0 or 1");
     return STN_OK;
   }
+  if (strcmp(knob, "sweep2d_ctas_per_sm") == 0) {
+    if (tune_set_ctas2d((int)value) != STN_OK) return einval("sweep2d_ctas_per_sm must be in [1, 4]");
+    return STN_OK;
+  }
   if (strcmp(knob, "sweep2d_tma") == 0) {
     if (tune_set_tma2d((int)value) != STN_OK) return einval("sweep2d_tma must be 0 or 1");
     return STN_OK;
@@ -1071,6 +1075,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "var_variant") == 0) {
     *value = tune_get_var_variant();
+    return STN_OK;
+  }
+  if (strcmp(knob, "sweep2d_ctas_per_sm") == 0) {
+    *value = tune_get_ctas2d();
     return STN_OK;
   }
   if (strcmp(knob, "sweep2d_tma") == 0) {

@@ -162,6 +162,8 @@ int tune_set_withhold2d(int v);
 int tune_get_withhold2d();
 int tune_set_tma2d(int v);
 int tune_get_tma2d();
+int tune_set_ctas2d(int v);
+int tune_get_ctas2d();
 
 // ---- sum / dotproduct intrinsics (intrinsics.cu) ---------------------------
 // Number of per-block partials launch_vec_reduce writes for n elements.

@@ -420,6 +420,7 @@ int g_resident2d = -1;          // -1 automatic, 0 never, 1 whenever it fits
 i64 g_chunk2d = 32768;          // sweeps per resident launch
 int g_withhold2d = 0;           // fault injection: last band never publishes
 int g_tma2d = 1;                // halo rows by bulk copy when rows are 16-byte multiples
+int g_ctas2d = 1;               // resident bands (CTAs) per SM
 constexpr double kWait2dSeconds = 2.0;
 
 template <typename T, int R, bool HAS_C0, bool TMA>
@@ -466,34 +467,40 @@ int launch_resident(const T* src, T* dst, const Grid2& g, const double* coeffs, 
 
 Plan2d plan_resident2d(const Grid2& g, size_t esize) {
   Plan2d p;
-  int dev = 0, sms = 0, optin = 0;
+  int dev = 0, sms = 0, optin = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return p;  // ok = false
   }
-  i64 nblk = g.ny / g.r;  // every band owns at least R rows
-  if (nblk > sms) nblk = sms;
-  if (nblk < 1) nblk = 1;
-  p.nblk = (int)nblk;
-  p.nbmax = (int)((g.ny + nblk - 1) / nblk);
-  const i64 rows = (i64)p.nbmax + 2 * g.r;
-  // row layout: interior of every row 16-byte aligned (see the kernel)
-  const i64 per16 = 16 / (i64)esize;
-  p.pad = (int)((per16 - g.r % per16) % per16);
-  p.ns = (int)((p.pad + g.NX() + per16 - 1) / per16 * per16);
-  p.tma = (g.nx * (i64)esize) % 16 == 0 && g_tma2d != 0;
-  const i64 smem = 2 * rows * p.ns * (i64)esize;
-  i64 thr = (i64)p.nbmax * g.nx;
-  thr = (thr + 31) / 32 * 32;
-  p.threads = (int)(thr > 1024 ? 1024 : thr);
-  p.smem = (size_t)smem;
-  p.xchg_off = ((size_t)8 * p.nblk + 8 + 255) / 256 * 256;
-  p.scratch = p.xchg_off + (size_t)2 * p.nblk * 2 * g.r * g.nx * esize;
-  // leave room for the kernel's static shared memory
-  p.ok = smem + 1024 <= optin && rows * p.ns < ((i64)1 << 31) &&
-         (p.tma || g.nx <= kJ2Cols * (i64)p.threads);
+  // `ctas` bands per SM (the knob), fewer when their shared memory does not fit
+  for (int ctas = g_ctas2d; ctas >= 1; ctas--) {
+    i64 nblk = g.ny / g.r;  // every band owns at least R rows
+    if (nblk > (i64)sms * ctas) nblk = (i64)sms * ctas;
+    if (nblk < 1) nblk = 1;
+    p.nblk = (int)nblk;
+    p.nbmax = (int)((g.ny + nblk - 1) / nblk);
+    const i64 rows = (i64)p.nbmax + 2 * g.r;
+    // row layout: interior of every row 16-byte aligned (see the kernel)
+    const i64 per16 = 16 / (i64)esize;
+    p.pad = (int)((per16 - g.r % per16) % per16);
+    p.ns = (int)((p.pad + g.NX() + per16 - 1) / per16 * per16);
+    p.tma = (g.nx * (i64)esize) % 16 == 0 && g_tma2d != 0;
+    const i64 smem = 2 * rows * p.ns * (i64)esize;
+    i64 thr = (i64)p.nbmax * g.nx;
+    thr = (thr + 31) / 32 * 32;
+    const i64 thr_max = 1024 / ctas;  // the SM's threads shared by its bands
+    p.threads = (int)(thr > thr_max ? thr_max : thr);
+    p.smem = (size_t)smem;
+    p.xchg_off = ((size_t)8 * p.nblk + 8 + 255) / 256 * 256;
+    p.scratch = p.xchg_off + (size_t)2 * p.nblk * 2 * g.r * g.nx * esize;
+    // leave room for the kernel's static shared memory
+    p.ok = smem + 1024 <= optin && rows * p.ns < ((i64)1 << 31) &&
+           (p.tma || g.nx <= kJ2Cols * (i64)p.threads);
+    if (!p.ok || ctas == 1 || (smem + 2048) * ctas <= per_sm) return p;
+  }
   return p;
 }
 
@@ -584,5 +591,11 @@ int tune_set_tma2d(int v) {
   return STN_OK;
 }
 int tune_get_tma2d() { return g_tma2d; }
+int tune_set_ctas2d(int v) {
+  if (v < 1 || v > 4) return STN_EINVAL;
+  g_ctas2d = v;
+  return STN_OK;
+}
+int tune_get_ctas2d() { return g_ctas2d; }
 
 }  // namespace stn

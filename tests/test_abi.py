@@ -170,7 +170,8 @@ def test_tuning_knobs(lib):
     for knob, good, bad in (("temporal_depth", 3, 5), ("batch_engine", 1, 2), ("solve_graph", 0, 2),
                             ("star_chunks", 7, -1), ("var_variant", 0, 2), ("repeat_graph", 0, 2),
                             ("sweep2d_resident", 0, 2), ("sweep2d_chunk", 100, 0),
-                            ("fault_withhold_2d", 0, 2), ("sweep2d_tma", 0, 2)):
+                            ("fault_withhold_2d", 0, 2), ("sweep2d_tma", 0, 2),
+                            ("sweep2d_ctas_per_sm", 2, 5)):
         before = lib.stencil_tune_get(knob)
         with pytest.raises(lib.StencilError):
             lib.stencil_tune_set(knob, bad)

@@ -40,15 +40,18 @@ def assert_bitwise(got, ref):
     assert bad.size == 0, f"{len(bad)} mismatches, first at {bad[0]}: {got[tuple(bad[0])]} vs {ref[tuple(bad[0])]}"
 
 
-@pytest.fixture(params=["auto", "regs", "hbm"])
+@pytest.fixture(params=["auto", "regs", "hbm", "2band", "3band-regs"])
 def path(request, lib):
     """auto: resident, halo rows by bulk copy where rows are 16-byte multiples;
-    regs: resident, halo rows through registers; hbm: per-sweep launches."""
+    regs: resident, halo rows through registers; hbm: per-sweep launches;
+    2band / 3band-regs: resident with 2 or 3 bands per SM where they fit."""
     lib.stencil_tune_set("sweep2d_resident", 0 if request.param == "hbm" else -1)
-    lib.stencil_tune_set("sweep2d_tma", 0 if request.param == "regs" else 1)
+    lib.stencil_tune_set("sweep2d_tma", 0 if "regs" in request.param else 1)
+    lib.stencil_tune_set("sweep2d_ctas_per_sm", {"2band": 2, "3band-regs": 3}.get(request.param, 1))
     yield request.param
     lib.stencil_tune_set("sweep2d_resident", -1)
     lib.stencil_tune_set("sweep2d_tma", 1)
+    lib.stencil_tune_set("sweep2d_ctas_per_sm", 1)
 
 
 SHAPES2D = [(1024, 1024), (37, 19), (1, 1), (1, 50), (50, 1), (130, 7), (2000, 3), (33, 1000),
