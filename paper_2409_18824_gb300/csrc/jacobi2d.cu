@@ -491,7 +491,7 @@ Plan2d plan_resident2d(const Grid2& g, size_t esize) {
     const i64 smem = 2 * rows * p.ns * (i64)esize;
     i64 thr = (i64)p.nbmax * g.nx;
     thr = (thr + 31) / 32 * 32;
-    const i64 thr_max = 1024 / ctas;  // the SM's threads shared by its bands
+    const i64 thr_max = 1024 / ctas / 32 * 32;  // the SM's threads shared by its bands, whole warps
     p.threads = (int)(thr > thr_max ? thr_max : thr);
     p.smem = (size_t)smem;
     p.xchg_off = ((size_t)8 * p.nblk + 8 + 255) / 256 * 256;
