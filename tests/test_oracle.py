@@ -365,6 +365,27 @@ def test_refinement_step_is_exact_on_dyadic_data(r, c, inner):
     assert abs(rel - want) <= 1e-14 * want
 
 
+@pytest.mark.parametrize("m", [7, 20])
+def test_refinement_contracts_an_eigenmode_by_lambda_to_the_inner_sweeps(m):
+    """Closed form for the refinement's outer steps.  With u = 0 and residual
+    rho, one step adds e_m = sum_{j<m} S^j rho, so the next residual is
+    S^m rho exactly (in exact arithmetic).  For a sine eigenmode b (S b = lam
+    b) the relative residual after k outer steps is |lam|^(m k) and the
+    iterate is b (1 - lam^(m k)) / (1 - lam); the float inner sweeps perturb
+    each step by about m (6r+2) 2^-24 relative."""
+    nx, ny, nz, r = 7, 5, 6, 1
+    b = si.sine_mode(nx, ny, nz, r, m=(1, 2, 1))
+    lam = (math.cos(math.pi / (nx + 1)) + math.cos(2 * math.pi / (ny + 1)) + math.cos(math.pi / (nz + 1))) / 3
+    inner = interior(b, r)
+    for k in (1, 2, 3, 4):
+        u, outer, rel, st = oracle.refined_solve(b, np.zeros_like(b), L7, r, 0.0, m, k)
+        assert outer == k and st == 1
+        want = abs(lam) ** (m * k)
+        assert abs(rel / want - 1) <= k * m * 8 * 2.0 ** -24 * 4, (k, rel, want)
+        series = (1 - lam ** (m * k)) / (1 - lam)
+        assert np.max(np.abs(interior(u, r) - series * inner)) <= m * 8 * 2.0 ** -24 * series * np.max(np.abs(inner))
+
+
 def test_constant_refined_solve_reaches_tolerance():
     """Constant-coefficient refinement end state: its reported double residual is
     recomputed from the dense operator, and u matches the direct solve of
