@@ -19,6 +19,8 @@
 //     reduce.cu adds the partials in index order, so the norm is deterministic
 //     for given extents.
 #pragma once
+#include <atomic>
+
 #include "arith.cuh"
 #include "internal.h"
 
@@ -633,14 +635,17 @@ int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* c
 #define STN_PLANE2(M) star2_kernel<T, R, HAS_B, HAS_C0, M>
   if (variant == kStarStaged) {
     // the staged kernels take their shared-memory ring as dynamic memory
-    static bool attr_set[3] = {false, false, false};
+    // per device and mode: the attribute is set (setting it twice is harmless)
+    static std::atomic<bool> attr_set[64][3];
     const int m = mode == kSweep ? 0 : (mode == kSweepResidual ? 1 : 2);
     auto kern = m == 0 ? star_staged_kernel<T, R, HAS_B, HAS_C0, kSweep>
                        : (m == 1 ? star_staged_kernel<T, R, HAS_B, HAS_C0, kSweepResidual>
                                  : star_staged_kernel<T, R, HAS_B, HAS_C0, kResidualOnly>);
-    if (!attr_set[m]) {
+    int dev = 0;
+    STN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev][m].load(std::memory_order_relaxed)) {
       STN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax));
-      attr_set[m] = true;
+      if (dev >= 0 && dev < 64) attr_set[dev][m].store(true, std::memory_order_relaxed);
     }
     // one warp per 32-wide i segment, at most SG_WARPS
     const int nw = (int)std::min<i64>((g.nx + 31) / 32, SG_WARPS);

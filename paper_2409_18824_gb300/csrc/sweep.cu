@@ -1,6 +1,8 @@
 // Host-side planning of the star-stencil kernels (star.cuh) and the tuning
 // override; the kernels themselves are instantiated per element type in
 // sweep_f64.cu and sweep_f32.cu so that the two compile in parallel.
+#include <atomic>
+
 #include "star.cuh"
 
 namespace stn {
@@ -41,19 +43,20 @@ StarChoice& star_last() {
 }
 
 int device_sms() {
-  static int cache[64] = {};
+  static std::atomic<int> cache[64];  // per device ordinal, 0 = not queried yet
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     (void)cudaGetLastError();
     return 152;
   }
-  if (cache[dev] > 0) return cache[dev];
+  const int known = cache[dev].load(std::memory_order_relaxed);
+  if (known > 0) return known;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
     (void)cudaGetLastError();
     return 152;
   }
-  cache[dev] = sms;
+  cache[dev].store(sms, std::memory_order_relaxed);
   return sms;
 }
 
@@ -70,9 +73,11 @@ static int occupancy(K kernel, int threads) {
 // Blocks of a star kernel resident per SM, queried once per (variant, element
 // type, radius) on the sweep instance; every mode uses the same plan.
 static int star_resident(int variant, size_t esize, int r) {
-  static int cache[3][2][3] = {};
-  int& c = cache[variant][esize == 8 ? 1 : 0][r];
-  if (c != 0) return c;
+  static std::atomic<int> cache[3][2][3];  // 0 = not queried yet
+  std::atomic<int>& slot = cache[variant][esize == 8 ? 1 : 0][r];
+  const int known = slot.load(std::memory_order_relaxed);
+  if (known != 0) return known;
+  int c = 0;
   const int tc = 32 * SC_WARPS, tp = TX * TY;
   if (esize == 8) {
     if (variant == kStarColumn)
@@ -95,6 +100,7 @@ static int star_resident(int variant, size_t esize, int r) {
       c = r == 1 ? occupancy(star_kernel<float, 1, false, false, kSweep>, tp)
                  : occupancy(star_kernel<float, 2, false, false, kSweep>, tp);
   }
+  slot.store(c, std::memory_order_relaxed);
   return c;
 }
 
@@ -129,10 +135,11 @@ static int staged_rows(const Grid& g, size_t esize) {
 
 // Blocks of the staged kernel resident per SM with `smem` bytes of ring.
 static int staged_resident(size_t esize, int r, int smem) {
-  static int cache_smem[2][3] = {};
-  static int cache_val[2][3] = {};
+  // last query per (type, radius): (smem << 32) | blocks, 0 = none yet
+  static std::atomic<unsigned long long> cache[2][3];
   const int e = esize == 8 ? 1 : 0;
-  if (cache_smem[e][r] == smem && cache_val[e][r] > 0) return cache_val[e][r];
+  const unsigned long long known = cache[e][r].load(std::memory_order_relaxed);
+  if (known != 0 && (int)(known >> 32) == smem) return (int)(known & 0xffffffffu);
   int v = 0;
   auto query = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
@@ -150,8 +157,7 @@ static int staged_resident(size_t esize, int r, int smem) {
     (void)cudaGetLastError();
     return 2;  // no device (planning only): the design point
   }
-  cache_smem[e][r] = smem;
-  cache_val[e][r] = v;
+  cache[e][r].store(((unsigned long long)(unsigned)smem << 32) | (unsigned)v, std::memory_order_relaxed);
   return v;
 }
 
