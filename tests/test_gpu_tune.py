@@ -50,7 +50,8 @@ def sweep(lib, u0, coeffs, r, iters):
 
 
 @pytest.mark.parametrize("variant,chunks,depth", [(0, 1, 1), (0, 7, 1), (1, 2, 1), (1, 25, 1), (2, 4, 1),
-                                                  (2, 13, 1), (0, 4, 2), (1, 3, 3), (2, 5, 4)])
+                                                  (2, 13, 1), (3, 1, 1), (3, 13, 1), (0, 4, 2), (1, 3, 3),
+                                                  (2, 5, 4), (3, 4, 2)])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_cache_entry_steers_the_plan_and_keeps_the_bits(lib, cuda, variant, chunks, depth, dtype):
     nx, ny, nz, r, iters = 70, 45, 100, 1, 7
@@ -66,7 +67,7 @@ def test_cache_entry_steers_the_plan_and_keeps_the_bits(lib, cuda, variant, chun
     assert bitwise(got, oracle.stencil_sweep(u0, si.LAPLACE7, r, iters))
 
 
-@pytest.mark.parametrize("variant,chunks", [(0, 3), (1, 5), (2, 9)])
+@pytest.mark.parametrize("variant,chunks", [(0, 3), (1, 5), (2, 9), (3, 4)])
 def test_cache_entry_radius2_norm_and_solve(lib, cuda, variant, chunks):
     """Radius 2 with a centre term: sweeps bitwise, the fused norm within
     1e-12 of the oracle's, and a Jacobi solve with the oracle's sweep count."""
