@@ -586,6 +586,54 @@ def run_jacobi2d_host(args):
     }), flush=True)
 
 
+# Table 4 of the paper: its threaded pw-advection (MLIR flow), speed-up over serial.
+PAPER_OPENMP_PW_SPEEDUP = {2: 1.81, 4: 3.34, 8: 5.52, 16: 8.04, 32: 9.77, 64: 10.80}
+
+
+def run_advect_host(args):
+    """The advection stand-in on the host cores (libstencil_host.so): u, v, w
+    advecting themselves on a 512 x 256 x 256 block of the pw-advection fields;
+    K timed steps of one pass on every hardware thread, then the scaling curve."""
+    import paper_2409_18824_gb300.host as hp
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    nx, ny, nz = 512, 256, 256
+    NX, NY, NZ = nx + 2, ny + 2, nz + 2
+    vel = [si.hash_field(NX, NY, 0, NZ, m) for m in range(3)]
+    outs = [np.zeros_like(vel[0]) for _ in range(3)]
+    c = (0.25, 0.25, 0.25)
+    tmax = hp.threads()
+
+    def run(T):
+        t0 = time.perf_counter()
+        hp.stencil_host_advect_f64(vel[0], vel[1], vel[2], outs, c, nthreads=T)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        run(tmax)
+    times = [run(tmax) for _ in range(args.steps)]
+    cells = float(nx) * ny * nz
+    value = cells * args.steps / sum(times) / 1e9
+    curve = {}
+    for T in sorted({t for t in (1, 2, 4, 8, 16, 32, 64) if t <= tmax} | {tmax}):
+        curve[T] = cells / min(run(T) for _ in range(2)) / 1e9
+    print(json.dumps({
+        "metric": "Gcells/s (advection stand-in, u, v, w advecting themselves, FP64, multi-core host path)",
+        "value": value, "unit": "Gcells/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512 x 256 x 256 block of the pw-advection fields (hash_field), one pass per step",
+                   "grid": [nx, ny, nz], "threads": tmax, "parallelism": "host threads (libstencil_host.so)"},
+        "scaling_curve": {"gcells": curve, "speedup": {T: curve[T] / curve[1] for T in curve},
+                          "paper_table4_speedup": PAPER_OPENMP_PW_SPEEDUP},
+        "e2e": {"value": value, "unit": "Gcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+        "host": host_info(),
+    }), flush=True)
+
+
 # ------------------------------------ the paper's sum / dotproduct runs ----
 INTRINSICS = {
     "sum": dict(n=32768 * 32768, seed=8, paper_s=1.63, flang_s=1.65,
@@ -1360,7 +1408,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep512",
                     choices=sorted(WORKLOADS) + ["batch", "serve", "varcoef", "jacobi2d", "jacobi2d_host", "sum",
-                                                 "dot", "advect"])
+                                                 "dot", "advect", "advect_host"])
     ap.add_argument("--elements", type=int, default=0,
                     help="sum/dot: elements instead of the paper's size (for profiling a smaller case)")
     ap.add_argument("--host-sweeps", type=int, default=2000,
@@ -1434,6 +1482,12 @@ def main():
             run_reference2d(args)
         else:
             run_jacobi2d(args)
+        return
+    if args.workload == "advect_host":
+        if args.impl == "reference":
+            run_reference_advect(args)
+        else:
+            run_advect_host(args)
         return
     if args.workload == "jacobi2d_host":
         if args.impl == "reference":

@@ -1,7 +1,8 @@
 /*
  * stencil_host.h -- C ABI of libstencil_host.so: the multi-core host path of
- * the Jacobi sweep, the paper's threaded jacobi (arXiv 2409.18824 Sec. 6.2
- * and Table 4: the benchmark's loops shared out over OpenMP threads).
+ * the Jacobi sweep and of the advection stand-in, the paper's threaded jacobi
+ * and pw-advection (arXiv 2409.18824 Sec. 6.2 and Table 4: the benchmarks'
+ * loops shared out over OpenMP threads).
  *
  * A library of its own: libstencil.so neither links nor calls it, so it is
  * never a fallback for the GPU path.  Grids are HOST arrays in the layout of
@@ -58,6 +59,20 @@ int stencil_host_sweep2d_f64(double* in, double* out, int64_t nx, int64_t ny, co
                              int64_t iters, int nthreads);
 int stencil_host_residual_norm2d_f64(const double* u, const double* b, int64_t nx, int64_t ny,
                                      const double* coeffs, int radius, double* norm_out, int nthreads);
+
+/* The multi-field advection stand-in on the host cores (the paper's threaded
+ * pw-advection, Table 4), the same operation and order as advect_f64 in
+ * include/stencil.h: per axis a with velocity V,
+ *     F- = (V(p-e)+V(p)) * (q(p-e)+q(p)),  F+ = (V(p)+V(p+e)) * (q(p)+q(p+e)),
+ *     T_a = c_a * (F- - F+),               s(p) = (T_x + T_y) + T_z,
+ * each operation rounded separately.  Halo-1 grids of (nz+2, ny+2, nx+2).
+ * q NULL: u, v, w advect themselves and s[0..2] receive their tendencies;
+ * otherwise nq (1..6) fields q[0..nq-1] and s[0..nq-1].  Only the interior of
+ * each s is written; the outputs must not overlap the inputs or each other.
+ * c: 3 finite doubles {c_x, c_y, c_z}.  Errors: -1 (NULL pointers, nq out of
+ * range, non-finite c, bad extents, overlap), -2. */
+int stencil_host_advect_f64(const double* u, const double* v, const double* w, const double* const* q, int nq,
+                            double* const* s, int64_t nx, int64_t ny, int64_t nz, const double* c, int nthreads);
 
 #ifdef __cplusplus
 }

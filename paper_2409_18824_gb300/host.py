@@ -32,6 +32,8 @@ SIGNATURES = {
     "stencil_host_residual_norm_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _dp, _int]),
     "stencil_host_sweep2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _i64, _int]),
     "stencil_host_residual_norm2d_f64": (_int, [_vp, _vp, _i64, _i64, _dp, _int, _dp, _int]),
+    "stencil_host_advect_f64": (_int, [_vp, _vp, _vp, ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp), _i64, _i64,
+                                       _i64, _dp, _int]),
 }
 for _name, (_res, _args) in SIGNATURES.items():
     _fn = getattr(_lib, _name)
@@ -102,3 +104,14 @@ def stencil_host_residual_norm2d_f64(u, coeffs, radius, b=None, nthreads=0) -> f
     _check(_lib.stencil_host_residual_norm2d_f64(_addr(u), _addr(b), nx, ny, cp, radius, ctypes.byref(v),
                                                  nthreads))
     return v.value
+
+
+def stencil_host_advect_f64(u, v, w, s, c, q=None, nthreads=0):
+    """Tendencies of q (a list of fields; None: u, v, w themselves) into the
+    list s; halo-1 grids of shape (nz+2, ny+2, nx+2)."""
+    nz, ny, nx = (d - 2 for d in u.shape)
+    cp, _keep = _coeffs(c)
+    qa = None if q is None else (_vp * len(q))(*[_addr(x) for x in q])
+    sa = (_vp * len(s))(*[_addr(x) for x in s])
+    return _check(_lib.stencil_host_advect_f64(_addr(u), _addr(v), _addr(w), qa, 0 if q is None else len(q), sa,
+                                               nx, ny, nz, cp, nthreads))

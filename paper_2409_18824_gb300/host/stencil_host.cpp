@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <new>
 #include <string>
@@ -221,6 +222,32 @@ int residual(const double* u, const double* b, const Geom& g, const double* c, d
   return 0;
 }
 
+// One row of advection tendencies: for each of the nf fields q[m], s[m] at
+// the row's interior points (i = 1..nx, padded offset p0 + i - 1), in the
+// order of advect_f64.
+void advect_row(const double* __restrict u, const double* __restrict v, const double* __restrict w,
+                const double* const* q, double* const* s, int nf, i64 p0, i64 nx, i64 NX, i64 NXY,
+                const double* c) {
+  const double cx = c[0], cy = c[1], cz = c[2];
+  for (int m = 0; m < nf; m++) {
+    const double* __restrict f = q[m];
+    double* __restrict o = s[m];
+    for (i64 i = 0; i < nx; i++) {
+      const i64 p = p0 + i;
+      const double fmx = (u[p - 1] + u[p]) * (f[p - 1] + f[p]);
+      const double fpx = (u[p] + u[p + 1]) * (f[p] + f[p + 1]);
+      const double tx = cx * (fmx - fpx);
+      const double fmy = (v[p - NX] + v[p]) * (f[p - NX] + f[p]);
+      const double fpy = (v[p] + v[p + NX]) * (f[p] + f[p + NX]);
+      const double ty = cy * (fmy - fpy);
+      const double fmz = (w[p - NXY] + w[p]) * (f[p - NXY] + f[p]);
+      const double fpz = (w[p] + w[p + NXY]) * (f[p] + f[p + NXY]);
+      const double tz = cz * (fmz - fpz);
+      o[p] = (tx + ty) + tz;
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -248,6 +275,44 @@ int stencil_host_sweep2d_f64(double* in, double* out, int64_t nx, int64_t ny, co
   g_err.clear();
   if (int rc = check(nx, ny, 1, radius, coeffs, nthreads)) return rc;
   return sweep(in, out, Geom{nx, ny, 1, radius, false}, coeffs, iters, nthreads);
+}
+
+int stencil_host_advect_f64(const double* u, const double* v, const double* w, const double* const* q, int nq,
+                            double* const* s, int64_t nx, int64_t ny, int64_t nz, const double* c, int nthreads) {
+  g_err.clear();
+  if (!u || !v || !w || !s || !c) return fail("NULL pointer");
+  if (q && (nq < 1 || nq > 6)) return fail("nq must be in [1, 6]");
+  if (int rc = check(nx, ny, nz, 1, c, nthreads)) return rc;
+  for (int a = 0; a < 3; a++)
+    if (!std::isfinite(c[a])) return fail("non-finite coefficient");
+  const int nf = q ? nq : 3;
+  const double* fields[6];
+  double* outs[6];
+  for (int m = 0; m < nf; m++) {
+    fields[m] = q ? q[m] : (m == 0 ? u : (m == 1 ? v : w));
+    outs[m] = s[m];
+    if (!fields[m] || !outs[m]) return fail("NULL field or output");
+  }
+  const Geom g{nx, ny, nz, 1, true};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  auto overlaps = [&](const void* x, const void* y) {
+    const char *a = (const char*)x, *b = (const char*)y;
+    return a < b + bytes && b < a + bytes;
+  };
+  for (int m = 0; m < nf; m++) {
+    for (const double* in : {u, v, w})
+      if (overlaps(outs[m], in)) return fail("an output overlaps an input");
+    for (int k = 0; k < nf; k++)
+      if (overlaps(outs[m], fields[k]) || (k != m && overlaps(outs[m], outs[k])))
+        return fail("an output overlaps an input or another output");
+  }
+  const i64 rows = g.rows();
+  const int T = resolve_threads(nthreads, rows);
+  const i64 NX = g.NX(), NXY = g.NX() * g.NY();
+  return run_workers(T, [&](int t) {
+    const i64 q0 = rows * t / T, q1 = rows * (t + 1) / T;
+    for (i64 r = q0; r < q1; r++) advect_row(u, v, w, fields, outs, nf, g.row_start(r), nx, NX, NXY, c);
+  });
 }
 
 int stencil_host_residual_norm2d_f64(const double* u, const double* b, int64_t nx, int64_t ny,

@@ -1,9 +1,9 @@
 """The multi-core host path (libstencil_host.so) against the oracle, on CPU.
 
-Sweeps follow the canonical order, so they must equal the oracle bitwise for
-every thread count; residual norms sum per-row partials in row order, so they
-must be the same bits for every thread count and within the recursive
-summation bound of the oracle's own norm.
+Sweeps and advection tendencies follow the canonical order, so they must equal
+the oracle bitwise for every thread count; residual norms sum per-row partials
+in row order, so they must be the same bits for every thread count and within
+the recursive summation bound of the oracle's own norm.
 """
 import ctypes
 import os
@@ -135,3 +135,49 @@ def test_rejects_bad_arguments(host):
     assert so.stencil_host_residual_norm_f64(ptr, None, 3, 3, 3, cp, 1, None, 0) == -1
     assert so.stencil_host_residual_norm2d_f64(None, None, 3, 3, cp, 1, ctypes.byref(v), 0) == -1
     assert so.stencil_host_sweep2d_f64(ptr, optr, 3, 0, cp, 1, 1, 0) == -1
+
+
+def random_grid(nx, ny, nz, seed):
+    return np.random.default_rng(seed).uniform(-1, 1, size=(nz + 2, ny + 2, nx + 2))
+
+
+@pytest.mark.parametrize("shape", [(37, 19, 11), (1, 1, 1), (64, 3, 2), (5, 40, 9)])
+def test_advect_self_and_tracers_bitwise_for_every_thread_count(host, shape):
+    """The host advection gives the oracle's bits (every value of every grid,
+    halos included, random) in both modes, for any thread count; only the
+    interior of each output is written."""
+    nx, ny, nz = shape
+    u, v, w = (random_grid(nx, ny, nz, 80 + m) for m in range(3))
+    c = (0.25, 0.125, 0.375)
+    ref_self = [oracle.advect(u, v, w, f, c) for f in (u, v, w)]
+    tracers = [random_grid(nx, ny, nz, 90 + m) for m in range(5)]
+    ref_tr = [oracle.advect(u, v, w, f, c) for f in tracers]
+    for T in (1, 2, 3, 16):
+        outs = [np.full_like(u, 7.0) for _ in range(3)]
+        host.stencil_host_advect_f64(u, v, w, outs, c, nthreads=T)
+        for o, ref in zip(outs, ref_self):
+            assert bitwise(o[1:-1, 1:-1, 1:-1].copy(), ref[1:-1, 1:-1, 1:-1].copy())
+            halo = np.ones(o.shape, dtype=bool)
+            halo[1:-1, 1:-1, 1:-1] = False
+            assert np.all(o[halo] == 7.0)
+        outs = [np.zeros_like(u) for _ in tracers]
+        host.stencil_host_advect_f64(u, v, w, outs, c, q=tracers, nthreads=T)
+        for o, ref in zip(outs, ref_tr):
+            assert bitwise(o, ref)
+
+
+def test_advect_rejects_bad_arguments(host):
+    u = np.zeros((4, 5, 6))
+    v, w, q = np.zeros_like(u), np.zeros_like(u), np.zeros_like(u)
+    s = [np.zeros_like(u) for _ in range(3)]
+    c = (0.25, 0.25, 0.25)
+    with pytest.raises(host.HostStencilError):
+        host.stencil_host_advect_f64(u, v, w, s, c, q=[q] * 7)  # nq > 6
+    with pytest.raises(host.HostStencilError):
+        host.stencil_host_advect_f64(u, v, w, [u, s[1], s[2]], c)  # output = an input
+    with pytest.raises(host.HostStencilError):
+        host.stencil_host_advect_f64(u, v, w, [s[0], s[0], s[2]], c)  # two outputs alias
+    with pytest.raises(host.HostStencilError):
+        host.stencil_host_advect_f64(u, v, w, s, (0.25, float("nan"), 0.25))
+    so = host.lib()
+    assert so.stencil_host_advect_f64(None, None, None, None, 0, None, 4, 3, 2, None, 0) == -1
