@@ -94,11 +94,12 @@ def test_batched_rejects_host_grids(lib, cuda):
 
 def test_batched_radius2_with_center_term_matches_oracle(lib, cuda, engine):
     """A radius-2 star with a centre coefficient (c0 + 6 c1 + 6 c2 = 0.85, a
-    contraction) on problems of both scheduler tile shapes: the 16 x 16, 48 x 9
-    and 12 x 30 problems take 16 x 16 tiles, 64 x 20 and 30 x 3 take 32 x 8;
-    bitwise the oracle's solve, with its sweep count."""
+    contraction) on problems of every scheduler tile shape: the 16 x 16, 48 x 9
+    and 12 x 30 problems take 16 x 16 tiles, 64 x 20 and 30 x 3 take 32 x 8,
+    8 x 60 and 7 x 33 take 8 x 32; bitwise the oracle's solve, with its sweep
+    count."""
     c = (0.1, 0.1, 0.025)
-    sizes = [(16, 16, 6), (48, 9, 7), (12, 30, 5), (64, 20, 4), (30, 3, 9)]
+    sizes = [(16, 16, 6), (48, 9, 7), (12, 30, 5), (64, 20, 4), (30, 3, 9), (8, 60, 5), (7, 33, 6)]
     rhs = [si.normal_interior(nx, ny, nz, 2, seed=40 + i) for i, (nx, ny, nz) in enumerate(sizes)]
     tol, K, maxit = 1e-10, 7, 5000
     d_u = [to_dev(np.zeros_like(b)) for b in rhs]
