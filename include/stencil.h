@@ -108,7 +108,8 @@ int stencil_release_workspace(void);
  *                   kernel (whole rows of a block's planes stream through a
  *                   shared-memory ring filled by asynchronous 16-byte copies;
  *                   grids whose rows are too long for the ring use another).
- *   "star_chunks":  0 automatic (default), else the number of k chunks each
+ *   "star_chunks":  0 automatic (default: the tuning cache's entry, else the
+ *                   built-in plan), else the number of k chunks each
  *                   column of tiles is split into (one block per tile and
  *                   chunk; clamped to chunks of >= 4 planes).  Changes the
  *                   grid, never the iterates; the residual's partial sums
@@ -135,8 +136,9 @@ int stencil_release_workspace(void);
  *                   copy when a row's interior is a multiple of 16 bytes (1,
  *                   default) or always through registers (0).
  *   "temporal_depth": sweeps fused per pass over HBM in stencil_sweep_*
- *                   (temporal blocking): 0 automatic (currently 1), 1 off,
- *                   2..4 (double radius 2: at most 3).
+ *                   (temporal blocking): 0 automatic (the tuning cache's
+ *                   entry for the extents, else 1), 1 off, 2..4 (double
+ *                   radius 2: at most 3).
  *   "solve_graph":  jacobi_solve_f64 iterates inside a CUDA graph whose while
  *                   node repeats {check_every sweeps, device-side convergence
  *                   decision} with no host round trip (1, default), or in a
