@@ -1053,6 +1053,7 @@ def run_batched(args):
         "converged": conv,
         "sweeps_max": int(iters.max()), "sweeps_median": float(np.median(iters)),
         "clocks": clk.summary(),
+        "host": host_info(),
     }
     if rank == 0:
         if not args.no_cpu_baseline and not refined:
@@ -1344,6 +1345,7 @@ def run_serving(args):
                 "h2d_bytes_per_step": int(sum(b.nbytes for b in rhss)) * 2,
                 "d2h_bytes_per_step": int(sum(b.nbytes for b in rhss))},
         "clocks": clk.summary(),
+        "host": host_info(),
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
