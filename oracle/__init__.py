@@ -23,8 +23,10 @@ variable-coefficient operator.  The constant-coefficient refinement
 (``refined_solve``) is pinned step by step in an exact dyadic regime (one
 outer step equals numpy's dense iteration bitwise) and by its end state.  The
 variable-coefficient refinement driver (``varcoef_refined_solve``) is pinned
-only through its end state (the double residual it reports is recomputed
-independently) -- its inner steps are "parity unpinned".
+the same ways: one outer step bitwise where every Jacobi diagonal is a power
+of two, each outer step against the closed form rho -> (N D^-1)^m rho
+(A = D - N, m inner sweeps), and its end state.  No function is left
+"parity unpinned".
 """
 from __future__ import annotations
 

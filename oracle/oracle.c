@@ -382,8 +382,10 @@ int oracle_varcoef_jacobi_solve_f64(const double* a, const double* f, double* u,
  *   update(double): u = u + s * double(e)
  * Returns 0 if converged within max_outer steps, 1 if not.  Reports the outer
  * steps taken and the final double relative residual.
- * Pinned by its end state only (residual recomputed from the dense operator,
- * solution against a direct solve); the inner steps are parity unpinned.
+ * Pinned by its end state (residual recomputed from the dense operator,
+ * solution against a direct solve), by one outer step bitwise on coefficient
+ * fields whose Jacobi diagonals are powers of two (float exact there), and by
+ * the closed form rho -> (N D^-1)^m rho per outer step (A = D - N).
  * ------------------------------------------------------------------------- */
 int oracle_varcoef_refined_solve(const double* a, const double* f, double* u, i64 nx, i64 ny,
                                  i64 nz, const double* w, int R, double tol, i64 inner_sweeps,

@@ -386,6 +386,101 @@ def test_refinement_contracts_an_eigenmode_by_lambda_to_the_inner_sweeps(m):
         assert np.max(np.abs(interior(u, r) - series * inner)) <= m * 8 * 2.0 ** -24 * series * np.max(np.abs(inner))
 
 
+def dyadic_varcoef(nx, ny, nz, R):
+    """A coefficient field on the padded grid whose Jacobi diagonals are all
+    powers of two.  Radius 1, w = (0, 1): a = 1, 3 alternating along i, so the
+    six face weights kappa = (a(p)+a(q))/2 sum to 8 or 16.  Radius 2,
+    w = (0, 1, 1): a = 1 or 3 by the parity of i + j (constant along k), so the
+    twelve face weights sum to 16 or 32."""
+    k, j, i = np.indices(si.padded_shape(nx, ny, nz, R))
+    if R == 1:
+        return np.where(i % 2 == 0, 1.0, 3.0), (0.0, 1.0)
+    return np.where((i + j) % 2 == 0, 1.0, 3.0), (0.0, 1.0, 1.0)
+
+
+def jacobi_split(a, nx, ny, nz, R, w):
+    """A = D - N on the interior, from the dense operator."""
+    mask = interior_mask(nx, ny, nz, R)
+    Ai = dense_varcoef_operator(a, nx, ny, nz, R, w)[:, mask]
+    D = np.diag(Ai).copy()
+    return Ai, D, np.diag(D) - Ai, mask
+
+
+@pytest.mark.parametrize("R,inner", [(1, 1), (1, 2), (1, 3), (1, 4), (2, 1), (2, 2), (2, 3)])
+def test_varcoef_refinement_step_is_exact_on_dyadic_data(R, inner):
+    """One outer step of the variable-coefficient refinement, pinned step by
+    step where float arithmetic is exact: every Jacobi diagonal a power of
+    two, face weights in {1, 2, 3}, f of small dyadic values with max |f| = 1
+    (scale 1, float(rho / s) = f).  The inner float iterate is then the exact
+    e_m = sum_{j<m} (D^-1 N)^j D^-1 f, the update gives u_1 = e_m bitwise, and
+    the new residual f - A u_1 is exactly (N D^-1)^m f (A = D - N gives
+    A e_m = f - (N D^-1)^m f)."""
+    nx, ny, nz = 5, 4, 3
+    a, w = dyadic_varcoef(nx, ny, nz, R)
+    Ai, D, N, mask = jacobi_split(a, nx, ny, nz, R, w)
+    assert set(np.unique(D)) <= {8.0, 16.0, 32.0}
+    rng = np.random.default_rng(71 + inner)
+    f = np.zeros(si.padded_shape(nx, ny, nz, R))
+    f[R:-R, R:-R, R:-R] = rng.integers(-8, 9, size=(nz, ny, nx)) / 8.0
+    f[R, R, R] = -1.0  # max |f| = 1
+    fi = f.ravel()[mask]
+    e = np.zeros_like(fi)
+    for _ in range(inner):
+        # the exactness regime: every partial sum of the float sweep is a
+        # multiple of the finest bit of e and f, bounded by |f| + sum t |e|
+        finest = min(2.0 ** -(significant_bits(v) - 1 - math.floor(math.log2(abs(v)))) if v else 1.0
+                     for v in np.concatenate([e, fi]))
+        bound = 1.0 + D.max() * np.max(np.abs(e))
+        assert bound / finest < 2.0 ** 24, (bound, finest)
+        e = (fi + N @ e) / D
+    u, outer, rel, st = oracle.varcoef_refined_solve(a, f, np.zeros_like(f), w, R, 0.0, inner, 1)
+    assert outer == 1 and st == 1
+    assert np.array_equal(u.ravel()[mask], e)  # u_1 = 1 * e_m, bitwise
+    assert not u.ravel()[~mask].any()  # the halo is untouched
+    rho = fi - Ai @ u.ravel()[mask]
+    closed = fi.copy()
+    for _ in range(inner):
+        closed = N @ (closed / D)
+    assert np.array_equal(rho, closed)
+    want = np.linalg.norm(closed) / np.linalg.norm(fi)
+    assert abs(rel - want) <= 1e-14 * want
+
+
+@pytest.mark.parametrize("m", [4, 11])
+def test_varcoef_refinement_maps_the_residual_by_N_D_inverse_to_the_m(m):
+    """Closed form for the variable-coefficient refinement's outer steps on
+    random coefficients: with A = D - N, one step of m inner Jacobi sweeps from
+    e = 0 takes the residual rho to (N D^-1)^m rho, up to the float rounding
+    of the inner sweeps and of a and w.  Each sweep rounds about 12R+2
+    operations per value and the sweeps contract (N D^-1 does not expand in
+    the 1-norm), so the deviation stays near m (12R+2) 2^-24 of ||rho||_1;
+    the test allows four times that.  Each outer step k is checked against
+    the oracle's own residual after step k-1, recomputed from the dense
+    operator; one inner sweep too many is checked to land at least ten times
+    outside the allowance, so an off-by-one count, a lost scale or a wrong
+    face weight fails."""
+    nx, ny, nz, R, w = 5, 4, 6, 2, si.VARCOEF_W
+    a = si.uniform_full(nx, ny, nz, R, seed=13)
+    f = si.normal_interior(nx, ny, nz, R, seed=14)
+    Ai, D, N, mask = jacobi_split(a, nx, ny, nz, R, w)
+    fi = f.ravel()[mask]
+    prev = fi
+    for k in (1, 2, 3):
+        u, outer, rel, st = oracle.varcoef_refined_solve(a, f, np.zeros_like(f), w, R, 0.0, m, k)
+        assert outer == k and st == 1
+        rho = fi - Ai @ u.ravel()[mask]
+        closed = prev.copy()
+        for _ in range(m):
+            closed = N @ (closed / D)
+        err = np.abs(rho - closed).sum() / np.abs(prev).sum()
+        allow = 4 * m * (12 * R + 2) * 2.0 ** -24
+        assert err <= allow, (k, err)
+        # and the mistake the pin is meant to catch is far outside it
+        assert np.abs(N @ (closed / D) - closed).sum() / np.abs(prev).sum() > 10 * allow
+        assert abs(rel - np.linalg.norm(rho) / np.linalg.norm(fi)) <= 1e-12 * rel
+        prev = rho
+
+
 def test_constant_refined_solve_reaches_tolerance():
     """Constant-coefficient refinement end state: its reported double residual is
     recomputed from the dense operator, and u matches the direct solve of
