@@ -51,7 +51,13 @@
  * Every entry point returns an int status.  It never aborts, exits or traps.
  * On a negative status nothing asynchronous was left running by the call;
  * outputs are unspecified.  stencil_last_error() gives a message for the last
- * failing call on the calling thread.
+ * failing call on the calling thread.  Extents are accepted up to 2^28 each,
+ * but a 3-D kernel launch holds at most 65535 tiles of rows (j) and 65535
+ * chunks of planes (k).  The sweeps, norms, solvers and advection return
+ * STN_EINVAL, before launching anything, for extents beyond that: ny above
+ * 65535 times the kernel's tile height (4 to 64 rows, so from 262140 rows
+ * up), or nz above 65535 chunks of 64 planes for advection.
+ * stencil_plan_query tells in advance for the sweeps.
  */
 #ifndef STENCIL_H_
 #define STENCIL_H_
@@ -242,6 +248,32 @@ int stencil_tune_cache_save(const char* path);
  * STN_EINVAL for a NULL path, an unreadable file or a malformed entry (then
  * nothing is added). */
 int stencil_tune_cache_load(const char* path);
+
+/* The launch one sweep of these extents would make on the current device,
+ * computed on the host by the same planners the sweeps use (the knobs and the
+ * tuning cache apply); nothing is launched or allocated.  Without a device
+ * the planners assume 152 SMs and a fixed number of resident blocks per SM.
+ * op: "sweep" (stencil_sweep_f64/_f32: variant as the star_variant knob,
+ * 0..3) or "varcoef_sweep" (the variable-coefficient sweep: variant 0 the
+ * plane kernel, 1 the column kernel).  Block (x, y, z) covers the interior
+ * columns [x tile_w, (x+1) tile_w), rows [y tile_h, (y+1) tile_h) and planes
+ * [z kchunk, (z+1) kchunk), clipped to the grid.  The staged kernel (variant
+ * 3 of "sweep") streams whole rows through a ring of 2r+2 stages of
+ * stage_elems elements, smem_bytes of dynamic shared memory in all.
+ * Errors: STN_EINVAL (NULL op or out, unknown op, bad extents, esize or
+ * radius, or a plan beyond CUDA's launch-grid limits: the sweep itself
+ * rejects those extents the same way). */
+typedef struct stn_launch_plan {
+  int32_t variant;
+  int32_t grid_x, grid_y, grid_z; /* blocks */
+  int32_t block_threads;
+  int32_t tile_w, tile_h;         /* interior columns (i) and rows (j) per block */
+  int32_t kchunk;                 /* interior planes per block */
+  int32_t stage_elems;            /* staged kernel: elements per ring stage, else 0 */
+  int32_t smem_bytes;             /* dynamic shared memory per block */
+} stn_launch_plan;
+int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int esize, int radius,
+                       stn_launch_plan* out);
 
 /*
  * stencil_sweep_f64 / _f32 -- `iters` Jacobi sweeps of the constant-

@@ -89,6 +89,14 @@ class TuneEntry(ctypes.Structure):
         return d
 
 
+class LaunchPlan(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("variant", "grid_x", "grid_y", "grid_z", "block_threads", "tile_w",
+                                              "tile_h", "kchunk", "stage_elems", "smem_bytes")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
                       "(python -c 'import __graft_entry__ as g; g.build()')")
@@ -116,6 +124,7 @@ SIGNATURES = {
     "stencil_tune_cache_clear": (_int, []),
     "stencil_tune_cache_save": (_int, [ctypes.c_char_p]),
     "stencil_tune_cache_load": (_int, [ctypes.c_char_p]),
+    "stencil_plan_query": (_int, [ctypes.c_char_p, _i64, _i64, _i64, _int, _int, ctypes.POINTER(LaunchPlan)]),
     "stencil_sweep_f64": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_sweep_f32": (_int, [_vp, _vp, _i64, _i64, _i64, _dp, _int, _i64, _vp]),
     "stencil_apply_f64": (_int, [_vp, _vp, _vp, _i64, _i64, _i64, _dp, _int, _vp]),
@@ -518,6 +527,14 @@ def stencil_tune_cache_save(path: str):
 
 def stencil_tune_cache_load(path: str) -> int:
     return _check(_lib.stencil_tune_cache_load(os.fsencode(path)))
+
+
+def stencil_plan_query(op: str, nx: int, ny: int, nz: int, esize: int, radius: int) -> dict:
+    """The launch one sweep of these extents would make (host-side planning;
+    nothing launched): variant, grid, block, tile, k chunk and ring sizes."""
+    q = LaunchPlan()
+    _check(_lib.stencil_plan_query(op.encode(), nx, ny, nz, esize, radius, ctypes.byref(q)))
+    return q.as_dict()
 
 
 class Server:

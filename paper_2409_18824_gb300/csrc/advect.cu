@@ -140,6 +140,7 @@ int launch_advect_t(const T* u, const T* v, const T* w, const AdvPtrs<T>& io, co
   // chunks of 64 planes: many blocks, each long enough to amortise its first planes
   const int kchunk = (int)std::min<i64>(g.nz, 64);
   const int chunks = (int)((g.nz + kchunk - 1) / kchunk);
+  if (int rc = check_launch_grid(tiles_x, tiles_y, chunks)) return rc;
   advect_kernel<T, NQ, SELF, TJ><<<dim3(tiles_x, tiles_y, chunks), dim3(32, ADV_WARPS), 0, s>>>(
       u, v, w, io, (int)g.nx, (int)g.ny, (int)g.nz, (int)g.NX(), (int)g.NY(), kchunk, (T)c[0], (T)c[1],
       (T)c[2]);

@@ -26,6 +26,17 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::stn::cuda_fail(_e, #expr); \
   } while (0)
 
+// CUDA's limits on a launch grid: gridDim.x < 2^31, gridDim.y and .z <= 65535.
+// A launcher whose plan would exceed them (extents with more than 65535 tiles
+// of rows, or of k chunks) returns STN_EINVAL before launching anything.
+inline int check_launch_grid(i64 gx, i64 gy, i64 gz) {
+  if (gx < 1 || gy < 1 || gz < 1 || gx >= ((i64)1 << 31) || gy > 65535 || gz > 65535) {
+    set_error("invalid argument: extents too large for one launch grid (more than 65535 row tiles or k chunks)");
+    return STN_EINVAL;
+  }
+  return STN_OK;
+}
+
 // Geometry of one padded grid.
 struct Grid {
   i64 nx, ny, nz;  // interior extents
@@ -109,6 +120,18 @@ bool tune_cache_lookup(const Grid& g, size_t esize, StarChoice* out);
 int device_sms();
 // Number of per-block partials launch_star writes for these arguments.
 i64 star_blocks(const Grid& g, size_t esize, const void* u, const void* b, const void* out);
+
+// Host-side description of the launch one sweep makes (nothing is launched):
+// the kernel variant, grid and block, the interior columns (i) and rows (j)
+// one block covers, planes per k chunk, and the staged kernel's ring.
+struct LaunchPlan {
+  int variant = 0;
+  int grid_x = 0, grid_y = 0, grid_z = 0, block_threads = 0;
+  int tile_w = 0, tile_h = 0, kchunk = 0;
+  int stage_elems = 0, smem = 0;
+};
+LaunchPlan sweep_launch_plan(const Grid& g, size_t esize);
+LaunchPlan var_launch_plan(const Grid& g, size_t esize);
 // One launch: out = S u + b over the interior; in residual modes also the
 // per-block partial sums of rho^2 into `partials` (ZPlan::blocks() entries).
 template <typename T>

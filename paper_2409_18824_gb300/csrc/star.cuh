@@ -618,6 +618,8 @@ template <typename T, int R, bool HAS_B, bool HAS_C0>
 int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
                   SweepMode mode, double* partials, cudaStream_t s, int variant) {
   const ZPlan p = plan_star(g, variant, sizeof(T));
+  variant = p.variant;  // the plan's own: a staged request whose ring does not fit runs the plane kernel
+  if (int rc = check_launch_grid(p.tiles_x, p.tiles_y, p.chunks)) return rc;
   star_last().variant = variant;
   star_last().chunks = p.chunks;
   StarCoeffs<T, R> cf;

@@ -263,4 +263,31 @@ i64 star_blocks(const Grid& g, size_t esize, const void* u, const void* b, const
   return plan_star(g, star_variant(g, esize, u, b, out), esize).blocks();
 }
 
+LaunchPlan sweep_launch_plan(const Grid& g, size_t esize) {
+  const ZPlan p = plan_star(g, star_variant(g, esize, nullptr, nullptr, nullptr), esize);
+  LaunchPlan q;
+  q.variant = p.variant;
+  q.grid_x = p.tiles_x;
+  q.grid_y = p.tiles_y;
+  q.grid_z = p.chunks;
+  q.kchunk = p.kchunk;
+  if (p.variant == kStarStaged) {
+    // whole rows: one warp per 32-wide i segment, at most SG_WARPS (launch_star_t)
+    q.block_threads = 32 * (int)std::min<i64>((g.nx + 31) / 32, SG_WARPS);
+    q.tile_w = (int)g.nx;
+    q.tile_h = p.rg;
+    q.stage_elems = p.stage_elems;
+    q.smem = p.smem;
+  } else if (p.variant == kStarColumn) {
+    q.block_threads = 32 * SC_WARPS;
+    q.tile_w = 32 - 2 * g.r;
+    q.tile_h = SC_WARPS * SC_TJ;
+  } else {
+    q.block_threads = TX * TY;
+    q.tile_w = TX;
+    q.tile_h = TY;
+  }
+  return q;
+}
+
 }  // namespace stn

@@ -199,6 +199,7 @@ int launch_tb_t(const T* u, T* out, const Grid& g, const double* coeffs, cudaStr
     return STN_ECUDA;
   }
   const ZPlan p = plan_temporal(g, TL, resident);
+  if (int rc = check_launch_grid(p.tiles_x, p.tiles_y, p.chunks)) return rc;
   kern<<<dim3(p.tiles_x, p.tiles_y, p.chunks), TB_THREADS, smem, s>>>(
       u, out, (int)g.nx, (int)g.ny, (int)g.nz, (int)g.NX(), (int)g.NY(), p.kchunk, cf);
   STN_CUDA_TRY(cudaGetLastError());

@@ -510,4 +510,33 @@ int stencil_tune_cache_load(const char* path) {
   return (int)got.size();
 }
 
+int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int esize, int radius,
+                       stn_launch_plan* out) {
+  clear_error();
+  if (!op || !out) return tune_einval("NULL op or out");
+  if (int rc = check_key(nx, ny, nz, esize, radius)) return rc;
+  const double cells = (double)(nx + 2 * radius) * (double)(ny + 2 * radius) * (double)(nz + 2 * radius);
+  if (cells > 9.0e15) return tune_einval("grid too large");
+  const Grid g{nx, ny, nz, radius};
+  LaunchPlan q;
+  if (strcmp(op, "sweep") == 0)
+    q = sweep_launch_plan(g, (size_t)esize);
+  else if (strcmp(op, "varcoef_sweep") == 0)
+    q = var_launch_plan(g, (size_t)esize);
+  else
+    return tune_einval(std::string("unknown op ") + op);
+  if (int rc = check_launch_grid(q.grid_x, q.grid_y, q.grid_z)) return rc;
+  out->variant = q.variant;
+  out->grid_x = q.grid_x;
+  out->grid_y = q.grid_y;
+  out->grid_z = q.grid_z;
+  out->block_threads = q.block_threads;
+  out->tile_w = q.tile_w;
+  out->tile_h = q.tile_h;
+  out->kchunk = q.kchunk;
+  out->stage_elems = q.stage_elems;
+  out->smem_bytes = q.smem;
+  return STN_OK;
+}
+
 }  // extern "C"

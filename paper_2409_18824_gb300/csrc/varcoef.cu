@@ -378,6 +378,7 @@ template <typename T, int R, int TJ>
 int launch_var_col_t(const T* u, const T* a, const T* f, T* out, const Grid& g, const double* w,
                      VarMode mode, double* partials, double* partials_max, cudaStream_t s) {
   const ZPlan p = plan_var(g, sizeof(T));
+  if (int rc = check_launch_grid(p.tiles_x, p.tiles_y, p.chunks)) return rc;
   VarW<T, R> hw;
   for (int d = 0; d <= R; d++) hw.w[d] = (T)(0.5 * w[d]);  // exact: halving
   dim3 grid(p.tiles_x, p.tiles_y, p.chunks), block(32, VC_WARPS);
@@ -400,6 +401,7 @@ template <typename T, int R>
 int launch_var_t(const T* u, const T* a, const T* f, T* out, const Grid& g, const double* w,
                  VarMode mode, double* partials, double* partials_max, cudaStream_t s) {
   const ZPlan p = plan_star(g, kStarScalar, 8);
+  if (int rc = check_launch_grid(p.tiles_x, p.tiles_y, p.chunks)) return rc;
   VarW<T, R> wt;
   for (int d = 0; d <= R; d++) wt.w[d] = (T)w[d];
   dim3 grid(p.tiles_x, p.tiles_y, p.chunks), block(TX, TY);
@@ -455,6 +457,28 @@ ZPlan plan_var(const Grid& g, size_t esize) {
   p.kchunk = (int)((g.nz + chunks - 1) / chunks);
   p.chunks = (int)((g.nz + p.kchunk - 1) / p.kchunk);
   return p;
+}
+
+LaunchPlan var_launch_plan(const Grid& g, size_t esize) {
+  const ZPlan p = plan_var(g, esize);
+  LaunchPlan q;
+  q.grid_x = p.tiles_x;
+  q.grid_y = p.tiles_y;
+  q.grid_z = p.chunks;
+  q.kchunk = p.kchunk;
+  if (var_use_column(g, esize)) {
+    const int tj = esize == 4 ? VarColTJ<float>::value : VarColTJ<double>::value;
+    q.variant = 1;
+    q.block_threads = 32 * VC_WARPS;
+    q.tile_w = 32 - 2 * g.r;
+    q.tile_h = VC_WARPS * tj;
+  } else {
+    q.variant = 0;
+    q.block_threads = TX * TY;
+    q.tile_w = TX;
+    q.tile_h = TY;
+  }
+  return q;
 }
 
 template <typename T>

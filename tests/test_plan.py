@@ -1,0 +1,215 @@
+"""Launch plans of the sweeps, checked on the CPU (no GPU: the planners then
+assume 152 SMs and a fixed residency per SM).
+
+`stencil_plan_query` returns the grid, block, tile and ring that a sweep of
+given extents would launch, from the same host code the sweeps call.  For a
+wide set of extents (cubes, the benchmark shapes, ragged and degenerate ones,
+rows too long for the staged ring, extents at the library's limits) every
+plan must cover each interior point exactly once with no empty block, stay
+within CUDA's grid and block limits and the shared memory of an SM, and keep
+the 32-bit offsets of the column kernels in range.  The staged kernel's copy
+arithmetic (16-byte asynchronous copies of the span a plane contributes, with
+element copies at the grid's ends) is replayed here for every alignment of
+the grid's base address, the first and last row group and the first and last
+k chunk: every copy must read inside the grid's bytes and land inside its
+ring stage, and every ring element the update reads must be one the copy
+wrote.
+"""
+import itertools
+
+import pytest
+
+SMEM_PER_BLOCK_MAX = 227 * 1024  # sm_103a, opt-in dynamic shared memory
+STAGED_SMEM_MAX = 220 * 1024     # the staged kernel's ring budget
+SG_PF = 1                        # planes in flight beyond the 2R+1 in use
+
+SHAPES = [(512, 512, 512), (768, 768, 384), (320, 320, 320), (64, 64, 64), (1, 1, 1), (2, 3, 5), (33, 17, 9),
+          (97, 61, 250), (1000, 7, 3), (5, 1000, 7), (3, 7, 1000), (100000, 2, 3), (60000, 40, 4),
+          (26000, 64, 64), (2047, 2049, 31), (128, 96, 72), (4096, 4096, 16), (1 << 28, 1, 1), (1, 1 << 28, 1),
+          (1, 1, 1 << 28)]
+
+
+def cases():
+    for (nx, ny, nz), esize, r in itertools.product(SHAPES, (4, 8), (1, 2)):
+        yield nx, ny, nz, esize, r
+
+
+def ceil_div(a, b):
+    return -(-a // b)
+
+
+def check_common(q, nx, ny, nz, r):
+    assert q["block_threads"] % 32 == 0 and 32 <= q["block_threads"] <= 1024
+    assert 1 <= q["grid_x"] < 2 ** 31 and 1 <= q["grid_y"] <= 65535 and 1 <= q["grid_z"] <= 65535
+    # every interior point in exactly one block, and no block without points
+    for n, tile, blocks in ((nx, q["tile_w"], q["grid_x"]), (ny, q["tile_h"], q["grid_y"]),
+                            (nz, q["kchunk"], q["grid_z"])):
+        assert tile >= 1 and blocks == ceil_div(n, tile), (n, tile, blocks)
+    assert 0 <= q["smem_bytes"] <= SMEM_PER_BLOCK_MAX
+
+
+def plan_or_rejected(lib, op, nx, ny, nz, esize, r):
+    """The plan, or None when the extents need more than 65535 row tiles or k
+    chunks in one launch (then the query, like the sweep, says so)."""
+    from paper_2409_18824_gb300 import StencilError
+    try:
+        return lib.stencil_plan_query(op, nx, ny, nz, esize, r)
+    except StencilError as e:
+        assert e.code == -1 and "launch grid" in lib.last_error()
+        return None
+
+
+@pytest.mark.parametrize("nx,ny,nz,esize,r", list(cases()))
+def test_sweep_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r):
+    q = plan_or_rejected(lib, "sweep", nx, ny, nz, esize, r)
+    if q is None:
+        # only extents no tile height of any kernel (at most 64 rows) fits
+        assert ny > 65535 * 8, (nx, ny, nz)
+        return
+    check_common(q, nx, ny, nz, r)
+    NX = nx + 2 * r
+    v = q["variant"]
+    assert v in (0, 1, 2, 3)
+    if v == 3:
+        assert q["grid_x"] == 1 and q["tile_w"] == nx
+        assert q["block_threads"] == 32 * min(ceil_div(nx, 32), 16)
+        assert 1 <= q["tile_h"] <= min(64, ny)
+        S = 2 * r + 1 + SG_PF
+        assert q["smem_bytes"] == S * q["stage_elems"] * esize <= STAGED_SMEM_MAX
+        # a stage holds the span's misalignment (< 16 bytes), its rows and the
+        # rounding of the last 16-byte chunk
+        assert q["stage_elems"] * esize >= (q["tile_h"] + 2 * r) * NX * esize + 32
+    else:
+        assert q["stage_elems"] == 0 and q["smem_bytes"] == 0
+        if v == 1:
+            assert (q["tile_w"], q["tile_h"], q["block_threads"]) == (32 - 2 * r, 32, 128)
+            assert (8 + 2 * r) * NX < 2 ** 31  # the column kernel's 32-bit row offsets
+        else:
+            assert (q["tile_w"], q["tile_h"], q["block_threads"]) == (32, 8, 256)
+
+
+@pytest.mark.parametrize("nx,ny,nz,esize,r", list(cases()))
+def test_varcoef_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r):
+    q = plan_or_rejected(lib, "varcoef_sweep", nx, ny, nz, esize, r)
+    if q is None:
+        assert ny > 65535 * 4, (nx, ny, nz)
+        return
+    check_common(q, nx, ny, nz, r)
+    assert q["smem_bytes"] == 0 and q["stage_elems"] == 0
+    if q["variant"] == 1:
+        tj = 4 if esize == 4 else 2
+        assert (q["tile_w"], q["tile_h"], q["block_threads"]) == (32 - 2 * r, 2 * tj, 64)
+        assert (tj + 2 * r) * (nx + 2 * r) < 2 ** 31
+        # at most ceil(nz / 8) k chunks, and at most 32768 blocks unless the
+        # (i, j) tiles alone are more
+        assert q["grid_z"] <= ceil_div(nz, 8)
+        assert q["grid_x"] * q["grid_y"] * q["grid_z"] <= max(32768, q["grid_x"] * q["grid_y"])
+    else:
+        assert q["variant"] == 0 and (q["tile_w"], q["tile_h"], q["block_threads"]) == (32, 8, 256)
+
+
+def staged_copies_stay_in_bounds(nx, ny, nz, esize, r, q, base_misalign):
+    """Replays the staged kernel's addressing for one grid base alignment:
+    the planes a block stages, the 16-byte chunks it copies asynchronously
+    (only chunks wholly inside the grid's bytes), the element copies of the
+    first and last chunk (only elements inside the grid), where they land in
+    the ring stage, and the ring elements the update reads."""
+    NX, NY, NZ = nx + 2 * r, ny + 2 * r, nz + 2 * r
+    epc = 16 // esize
+    psz = NX * NY
+    gbase = 4096 + base_misalign  # any address with this alignment
+    gend = gbase + NX * NY * NZ * esize
+    rg, kchunk, stage = q["tile_h"], q["kchunk"], q["stage_elems"]
+    S = 2 * r + 1 + SG_PF
+    for by in sorted({0, q["grid_y"] - 1}):
+        for bz in sorted({0, q["grid_z"] - 1}):
+            j0 = r + by * rg
+            rows = min(rg, ny + r - j0)
+            assert rows >= 1
+            k0 = r + bz * kchunk
+            k1 = min(k0 + kchunk, nz + r)
+            assert k0 < k1
+            pfirst, plast = k0 - r, k1 - 1 + r
+            assert 0 <= pfirst and plast <= NZ - 1
+            assert j0 - r >= 0 and j0 + rows + r - 1 <= NY - 1
+            n_el = (rows + 2 * r) * NX
+            first = lambda p: (p * NY + (j0 - r)) * NX  # noqa: E731
+            shift0 = ((gbase + first(pfirst) * esize) & 15) // esize
+            pstep = psz & (epc - 1)
+            # only the first S + 2 planes and the last ones matter for the
+            # bounds (the others are interior spans); cap the loop
+            planes = list(range(pfirst, min(plast, pfirst + S + 2) + 1)) + list(range(max(pfirst, plast - S), plast + 1))
+            for p in sorted(set(planes)):
+                addr = gbase + first(p) * esize
+                a0 = addr & ~15
+                nch = (addr - a0 + n_el * esize + 15) >> 4
+                c_lo = 1 if a0 < gbase else 0
+                c_hi = nch - 1 if a0 + (nch << 4) > gend else nch
+                # asynchronous chunks: whole 16 bytes inside the grid
+                if c_hi > c_lo:
+                    assert a0 + 16 * c_lo >= gbase and a0 + 16 * c_hi <= gend
+                # the ring stage receives nch chunks
+                assert nch * 16 <= stage * esize
+                # the copy puts the span at shift elements into the stage
+                shift = (shift0 + (p - pfirst) * pstep) & (epc - 1)
+                assert shift == ((addr - a0) // esize)
+                # the update reads elements shift + row * NX + i (i in
+                # [0, NX)), rows 0 .. rows + 2r - 1 of the span: all copied,
+                # and all inside the stage
+                lo, hi = shift, shift + n_el - 1
+                assert 0 <= lo and hi < stage and hi < nch * epc
+
+
+@pytest.mark.parametrize("nx,ny,nz,esize,r", [c for c in cases() if c[3] == 4])
+def test_staged_ring_copies_and_reads_stay_in_bounds(lib, nx, ny, nz, esize, r):
+    lib.stencil_tune_set("star_variant", 3)  # the staged kernel on these extents, if its ring fits
+    try:
+        q = plan_or_rejected(lib, "sweep", nx, ny, nz, esize, r)
+    finally:
+        lib.stencil_tune_set("star_variant", -1)
+    if q is None:
+        assert ny > 65535 * 8
+        return
+    if q["variant"] != 3:
+        # one row and its halo do not fit the ring: the plan falls back
+        assert (1 + 2 * r) * (nx + 2 * r) * esize + 32 > STAGED_SMEM_MAX // (2 * r + 2)
+        return
+    for mis in range(0, 16, esize):
+        staged_copies_stay_in_bounds(nx, ny, nz, esize, r, q, mis)
+
+
+def test_variant_rules_and_precedence(lib):
+    """Float grids of >= 3e7 points take the staged kernel, smaller float grids
+    the column kernel (radius 1) or the two-plane kernel (radius 2), double
+    grids the plane kernel; a knob asking for a kernel that cannot run on the
+    extents does not get it; a cache entry steers the plan."""
+    q = lib.stencil_plan_query
+    assert q("sweep", 512, 512, 512, 4, 1)["variant"] == 3
+    assert q("sweep", 64, 64, 64, 4, 1)["variant"] == 1
+    assert q("sweep", 64, 64, 64, 4, 2)["variant"] == 2
+    assert q("sweep", 512, 512, 512, 8, 1)["variant"] == 0
+    built_in = q("sweep", 60000, 600, 4, 4, 1)
+    assert built_in["variant"] != 3  # rows too long for the ring
+    lib.stencil_tune_set("star_variant", 3)
+    try:
+        assert q("sweep", 60000, 600, 4, 4, 1) == built_in  # the knob cannot have it: the built-in rule
+        assert q("sweep", 64, 64, 64, 8, 1)["variant"] == 3
+    finally:
+        lib.stencil_tune_set("star_variant", -1)
+    lib.stencil_tune_cache_clear()
+    try:
+        lib.stencil_tune_cache_put(70, 45, 100, 4, 1, 2, 13, 1)
+        p = q("sweep", 70, 45, 100, 4, 1)
+        assert p["variant"] == 2 and p["grid_z"] == 13
+        assert q("sweep", 70, 45, 101, 4, 1)["variant"] == 1  # other extents: the built-in rule
+    finally:
+        lib.stencil_tune_cache_clear()
+
+
+def test_plan_query_rejects_bad_arguments(lib):
+    from paper_2409_18824_gb300 import StencilError
+    for args in (("sweep", 0, 4, 4, 8, 1), ("sweep", 4, 4, 4, 2, 1), ("sweep", 4, 4, 4, 8, 3),
+                 ("stencil", 4, 4, 4, 8, 1), ("varcoef_sweep", 4, -1, 4, 4, 2), ("sweep", 1 << 29, 1, 1, 8, 1)):
+        with pytest.raises(StencilError):
+            lib.stencil_plan_query(*args)
+    assert "invalid argument" in lib.last_error()
