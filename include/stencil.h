@@ -254,12 +254,20 @@ int stencil_tune_cache_load(const char* path);
  * tuning cache apply); nothing is launched or allocated.  Without a device
  * the planners assume 152 SMs and a fixed number of resident blocks per SM.
  * op: "sweep" (stencil_sweep_f64/_f32: variant as the star_variant knob,
- * 0..3) or "varcoef_sweep" (the variable-coefficient sweep: variant 0 the
- * plane kernel, 1 the column kernel).  Block (x, y, z) covers the interior
- * columns [x tile_w, (x+1) tile_w), rows [y tile_h, (y+1) tile_h) and planes
- * [z kchunk, (z+1) kchunk), clipped to the grid.  The staged kernel (variant
- * 3 of "sweep") streams whole rows through a ring of 2r+2 stages of
- * stage_elems elements, smem_bytes of dynamic shared memory in all.
+ * 0..3), "varcoef_sweep" (the variable-coefficient sweep: variant 0 the
+ * plane kernel, 1 the column kernel) or "sweep2d" (stencil_sweep2d_f64/_f32,
+ * nz = 1: variant 1 the shared-memory-resident kernel, 0 one launch per
+ * sweep).  Block (x, y, z) covers the interior columns [x tile_w,
+ * (x+1) tile_w), rows [y tile_h, (y+1) tile_h) and planes [z kchunk,
+ * (z+1) kchunk), clipped to the grid; the per-sweep 2-D kernel loops over
+ * its 32 x 8 tiles with grid_x blocks, and the resident one gives band b the
+ * rows [b ny / grid_x, (b+1) ny / grid_x), at most tile_h.  The staged kernel
+ * (variant 3 of "sweep") streams whole rows through a ring of 2r+2 stages of
+ * stage_elems elements, smem_bytes of dynamic shared memory in all.  The
+ * resident 2-D kernel keeps two copies of its band's rows with row stride
+ * row_stride elements, padded column c at row_pad + c; bulk_copy = 1 when
+ * the halo rows arrive by bulk copy; it needs scratch_bytes of global scratch
+ * with the exchange slots from xchg_offset on.
  * Errors: STN_EINVAL (NULL op or out, unknown op, bad extents, esize or
  * radius, or a plan beyond CUDA's launch-grid limits: the sweep itself
  * rejects those extents the same way). */
@@ -271,6 +279,11 @@ typedef struct stn_launch_plan {
   int32_t kchunk;                 /* interior planes per block */
   int32_t stage_elems;            /* staged kernel: elements per ring stage, else 0 */
   int32_t smem_bytes;             /* dynamic shared memory per block */
+  int32_t row_stride, row_pad;    /* resident 2-D kernel: shared-memory row layout, else 0 */
+  int32_t bulk_copy;              /* resident 2-D kernel: halo rows by bulk copy (1) or not (0) */
+  int32_t reserved;
+  int64_t scratch_bytes;          /* resident 2-D kernel: global scratch, else 0 */
+  int64_t xchg_offset;            /* resident 2-D kernel: offset of the exchange slots in it */
 } stn_launch_plan;
 int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int esize, int radius,
                        stn_launch_plan* out);

@@ -91,10 +91,12 @@ class TuneEntry(ctypes.Structure):
 
 class LaunchPlan(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in ("variant", "grid_x", "grid_y", "grid_z", "block_threads", "tile_w",
-                                              "tile_h", "kchunk", "stage_elems", "smem_bytes")]
+                                              "tile_h", "kchunk", "stage_elems", "smem_bytes", "row_stride",
+                                              "row_pad", "bulk_copy", "reserved")] + [
+        ("scratch_bytes", ctypes.c_int64), ("xchg_offset", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 if not os.path.exists(LIB_PATH):

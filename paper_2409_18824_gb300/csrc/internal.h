@@ -129,6 +129,10 @@ struct LaunchPlan {
   int grid_x = 0, grid_y = 0, grid_z = 0, block_threads = 0;
   int tile_w = 0, tile_h = 0, kchunk = 0;
   int stage_elems = 0, smem = 0;
+  // the resident 2-D sweep: shared-memory row stride and pad, halo rows by
+  // bulk copy, global scratch and the offset of its exchange slots
+  int row_stride = 0, row_pad = 0, bulk_copy = 0;
+  i64 scratch = 0, xchg_off = 0;
 };
 LaunchPlan sweep_launch_plan(const Grid& g, size_t esize);
 LaunchPlan var_launch_plan(const Grid& g, size_t esize);
@@ -164,6 +168,7 @@ struct Plan2d {
 };
 Plan2d plan_resident2d(const Grid2& g, size_t esize);
 bool use_resident2d(const Plan2d& p);
+LaunchPlan sweep2d_launch_plan(const Grid2& g, size_t esize);
 // One launch of the per-sweep kernel: out = S u + b over the interior; in
 // residual modes one partial per block (star2d_blocks(g) entries).
 template <typename T>

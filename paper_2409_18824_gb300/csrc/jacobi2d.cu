@@ -473,7 +473,10 @@ Plan2d plan_resident2d(const Grid2& g, size_t esize) {
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
     (void)cudaGetLastError();
-    return p;  // ok = false
+    // no device (planning only): GB300's SMs and shared memory
+    sms = 152;
+    optin = 227 * 1024;
+    per_sm = 228 * 1024;
   }
   // `ctas` bands per SM (the knob), fewer when their shared memory does not fit
   for (int ctas = g_ctas2d; ctas >= 1; ctas--) {
@@ -505,6 +508,36 @@ Plan2d plan_resident2d(const Grid2& g, size_t esize) {
 }
 
 bool use_resident2d(const Plan2d& p) { return p.ok && g_resident2d != 0; }
+
+LaunchPlan sweep2d_launch_plan(const Grid2& g, size_t esize) {
+  const Plan2d p = plan_resident2d(g, esize);
+  LaunchPlan q;
+  q.grid_y = q.grid_z = 1;
+  if (use_resident2d(p)) {
+    // one cooperative launch: band b owns rows [b ny / nblk, (b+1) ny / nblk)
+    q.variant = 1;
+    q.grid_x = p.nblk;
+    q.block_threads = p.threads;
+    q.tile_w = (int)g.nx;
+    q.tile_h = p.nbmax;
+    q.kchunk = 1;
+    q.smem = (int)p.smem;
+    q.row_stride = p.ns;
+    q.row_pad = p.pad;
+    q.bulk_copy = p.tma ? 1 : 0;
+    q.scratch = (i64)p.scratch;
+    q.xchg_off = (i64)p.xchg_off;
+  } else {
+    // one launch per sweep, a grid-stride loop over 32 x 8 tiles
+    q.variant = 0;
+    q.grid_x = (int)star2d_blocks(g);
+    q.block_threads = 256;
+    q.tile_w = 32;
+    q.tile_h = 8;
+    q.kchunk = 1;
+  }
+  return q;
+}
 
 template <typename T>
 int launch_star2d(const T* u, const T* b, T* out, const Grid2& g, const double* coeffs,

@@ -519,12 +519,16 @@ int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int e
   if (cells > 9.0e15) return tune_einval("grid too large");
   const Grid g{nx, ny, nz, radius};
   LaunchPlan q;
-  if (strcmp(op, "sweep") == 0)
+  if (strcmp(op, "sweep") == 0) {
     q = sweep_launch_plan(g, (size_t)esize);
-  else if (strcmp(op, "varcoef_sweep") == 0)
+  } else if (strcmp(op, "varcoef_sweep") == 0) {
     q = var_launch_plan(g, (size_t)esize);
-  else
+  } else if (strcmp(op, "sweep2d") == 0) {
+    if (nz != 1) return tune_einval("sweep2d plans take nz = 1");
+    q = sweep2d_launch_plan(Grid2{nx, ny, radius}, (size_t)esize);
+  } else {
     return tune_einval(std::string("unknown op ") + op);
+  }
   if (int rc = check_launch_grid(q.grid_x, q.grid_y, q.grid_z)) return rc;
   out->variant = q.variant;
   out->grid_x = q.grid_x;
@@ -536,6 +540,12 @@ int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int e
   out->kchunk = q.kchunk;
   out->stage_elems = q.stage_elems;
   out->smem_bytes = q.smem;
+  out->row_stride = q.row_stride;
+  out->row_pad = q.row_pad;
+  out->bulk_copy = q.bulk_copy;
+  out->reserved = 0;
+  out->scratch_bytes = q.scratch;
+  out->xchg_offset = q.xchg_off;
   return STN_OK;
 }
 

@@ -213,3 +213,80 @@ def test_plan_query_rejects_bad_arguments(lib):
         with pytest.raises(StencilError):
             lib.stencil_plan_query(*args)
     assert "invalid argument" in lib.last_error()
+
+
+SHAPES2D = [(1024, 1024), (1001, 1024), (1000, 37), (1, 1), (5, 3), (2, 7), (33, 2), (4096, 4096), (300, 5000),
+            (16, 100000), (20000, 20000), (512, 152), (512, 153), (64, 64), (8, 1 << 20)]
+J2_COLS = 4  # interior columns per thread when halo rows come through registers
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+@pytest.mark.parametrize("nx,ny", SHAPES2D)
+@pytest.mark.parametrize("esize,r", [(8, 1), (4, 1), (8, 2), (4, 2)])
+def test_sweep2d_plan_bands_layout_and_bulk_copies(lib, nx, ny, esize, r, ctas):
+    """The paper's 2-D jacobi.  Resident plan: bands partition the rows (each
+    at least r rows when there are several, at most tile_h), two copies of a
+    band fit the shared memory, every row's interior starts on a 16-byte
+    boundary, and each halo-row bulk copy (source in the exchange slots,
+    destination in either copy of the band) is 16-byte aligned, a multiple of
+    16 bytes long and inside its buffer; without bulk copies the registers
+    cover the row.  Per-sweep plan: a grid-stride loop over 32 x 8 tiles."""
+    lib.stencil_tune_set("sweep2d_ctas_per_sm", ctas)
+    try:
+        q = plan_or_rejected(lib, "sweep2d", nx, ny, 1, esize, r)
+    finally:
+        lib.stencil_tune_set("sweep2d_ctas_per_sm", 1)
+    assert q is not None
+    NX = nx + 2 * r
+    assert q["grid_y"] == q["grid_z"] == 1 and q["block_threads"] % 32 == 0 and q["block_threads"] <= 1024
+    if q["variant"] == 0:
+        assert q["block_threads"] == 256 and (q["tile_w"], q["tile_h"]) == (32, 8)
+        assert q["grid_x"] == min(ceil_div(nx, 32) * ceil_div(ny, 8), 152 * 8)
+        assert q["smem_bytes"] == 0 and q["scratch_bytes"] == 0
+        # resident is refused only when even bands of ceil(ny / (152 ctas))
+        # rows do not fit, or the rows are too wide for registers
+        nblk = min(max(ny // r, 1), 152 * ctas)
+        ns = ceil_div(NX + 16 // esize, 16 // esize) * (16 // esize)
+        small = 2 * (ceil_div(ny, nblk) + 2 * r) * ns * esize + 1024 <= SMEM_PER_BLOCK_MAX
+        assert not small or (nx * esize % 16 and nx > J2_COLS * 1024 // ctas)
+        return
+    nblk, nbmax, ns, pad, thr = q["grid_x"], q["tile_h"], q["row_stride"], q["row_pad"], q["block_threads"]
+    assert q["tile_w"] == nx and 1 <= nblk <= max(1, min(ny // r, 152 * ctas))
+    assert nbmax == ceil_div(ny, nblk)
+    bands = [((b + 1) * ny) // nblk - (b * ny) // nblk for b in range(nblk)]
+    assert sum(bands) == ny and max(bands) <= nbmax and (nblk == 1 or min(bands) >= r)
+    per16 = 16 // esize
+    assert ns >= pad + NX and (ns * esize) % 16 == 0 and ((pad + r) * esize) % 16 == 0 and 0 <= pad < per16
+    rows = nbmax + 2 * r
+    assert q["smem_bytes"] == 2 * rows * ns * esize and q["smem_bytes"] + 1024 <= SMEM_PER_BLOCK_MAX
+    assert rows * ns < 2 ** 31
+    # the SM's 1024 threads are shared by its bands (the knob asks for `ctas`
+    # per SM; the planner takes fewer when that many do not fit)
+    per_sm = ceil_div(nblk, 152)
+    assert per_sm <= ctas and 32 <= thr <= 1024 // per_sm and thr <= ceil_div(nbmax * nx, 32) * 32
+    # global scratch: nblk 64-bit flags, the status word, then the exchange
+    # slots: 2 parities x nblk bands x 2 sides x r rows of nx values
+    xo, scratch = q["xchg_offset"], q["scratch_bytes"]
+    assert xo >= 8 * nblk + 4 and xo % 256 == 0
+    assert scratch == xo + 2 * nblk * 2 * r * nx * esize
+    if not q["bulk_copy"]:
+        assert nx <= J2_COLS * thr
+        return
+    assert (nx * esize) % 16 == 0
+    nbytes = nx * esize
+    buf = rows * ns * esize  # one copy of the band
+    slot = r * nx            # one side's rows in an exchange slot, elements
+    for b in sorted({0, 1, nblk // 2, nblk - 2, nblk - 1} & set(range(nblk))):
+        up, down = b > 0, b + 1 < nblk
+        for par in (0, 1):
+            for t in (0, 1):
+                for rr in range(r):
+                    for side, ok, src_slot, dst_row in (("up", up, 2 * (b - 1) + 1, rr),
+                                                        ("down", down, 2 * (b + 1), r + bands[b] + rr)):
+                        if not ok:
+                            continue
+                        src = xo + ((par * nblk * 2 + src_slot) * slot + rr * nx) * esize
+                        dst = t * buf + (dst_row * ns + pad + r) * esize
+                        assert src % 16 == 0 and dst % 16 == 0 and nbytes % 16 == 0, (side, b)
+                        assert xo <= src and src + nbytes <= scratch
+                        assert t * buf <= dst and dst + nbytes <= (t + 1) * buf
