@@ -493,3 +493,26 @@ def test_refined_solve_matches_oracle(lib, cuda, var_variant, repeat_graph):
     assert_bitwise(got, u_ref)
     # independent double residual of the returned u
     assert oracle.varcoef_residual_norm(got, a, f, VW, R) / oracle.interior_norm(f, R) <= tol
+
+
+def test_extents_beyond_the_launch_grid_are_rejected_before_launch(lib, cuda):
+    """A double sweep of 1 x ny x 1 runs the plane kernel, 8 rows per tile:
+    ny = 65535 x 8 needs exactly CUDA's 65535 blocks in y and runs (bitwise
+    the oracle); one row more would need 65536 and is STN_EINVAL, from the
+    sweep and from the plan query alike, before anything is launched."""
+    ny = 65535 * 8
+    u0 = si.uniform_interior(1, ny, 1, 1, seed=41)
+    d_out = to_dev(np.zeros_like(u0))
+    lib.stencil_sweep_f64(to_dev(u0), d_out, L7, 1, 2)
+    assert_bitwise(to_host(d_out), oracle.stencil_sweep(u0, L7, 1, 2))
+    assert lib.stencil_plan_query("sweep", 1, ny, 1, 8, 1)["grid_y"] == 65535
+    u1 = si.uniform_interior(1, ny + 1, 1, 1, seed=42)
+    d1 = to_dev(np.zeros_like(u1))
+    with pytest.raises(lib.StencilError) as e:
+        lib.stencil_sweep_f64(to_dev(u1), d1, L7, 1, 1)
+    assert e.value.code == -1 and "launch grid" in lib.last_error()
+    with pytest.raises(lib.StencilError):
+        lib.stencil_plan_query("sweep", 1, ny + 1, 1, 8, 1)
+    # the context is unaffected
+    lib.stencil_sweep_f64(to_dev(u0), d_out, L7, 1, 1)
+    assert_bitwise(to_host(d_out), oracle.stencil_sweep(u0, L7, 1, 1))
