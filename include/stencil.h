@@ -255,9 +255,13 @@ int stencil_tune_cache_load(const char* path);
  * the planners assume 152 SMs and a fixed number of resident blocks per SM.
  * op: "sweep" (stencil_sweep_f64/_f32: variant as the star_variant knob,
  * 0..3), "varcoef_sweep" (the variable-coefficient sweep: variant 0 the
- * plane kernel, 1 the column kernel) or "sweep2d" (stencil_sweep2d_f64/_f32,
+ * plane kernel, 1 the column kernel), "sweep2d" (stencil_sweep2d_f64/_f32,
  * nz = 1: variant 1 the shared-memory-resident kernel, 0 one launch per
- * sweep).  Block (x, y, z) covers the interior columns [x tile_w,
+ * sweep) or "batch_unit" (how the batched solvers and the server split one
+ * problem into work units, radius-independent: variant = tile shape, 0
+ * 32 x 8, 1 16 x 16, 2 8 x 32 columns; grid_x x grid_y tiles times grid_z
+ * chunks of kchunk planes are the units; stage_elems = the elements of the
+ * shared plane every shape fits; extents at most 2^20).  Block (x, y, z) covers the interior columns [x tile_w,
  * (x+1) tile_w), rows [y tile_h, (y+1) tile_h) and planes [z kchunk,
  * (z+1) kchunk), clipped to the grid; the per-sweep 2-D kernel loops over
  * its 32 x 8 tiles with grid_x blocks, and the resident one gives band b the

@@ -944,14 +944,24 @@ static int batch_impl(const stn_problem* probs, i64 count, const double* coeffs,
   if (!(inner_tol >= 0.0)) return einval("inner_tol must be >= 0");
   if (max_outer < 0) return einval("max_outer < 0");
   if (count > (1 << 30)) return einval("too many problems");
+  // the solvers' scratch (a double grid per problem, three float grids when
+  // refined, one partial per work unit), bounded before any size arithmetic
+  double scratch = 0.0;
   for (i64 i = 0; i < count; i++) {
     const stn_problem& p = probs[i];
     if (int rc = check_grid(p.nx, p.ny, p.nz, radius)) return rc;
     if (p.nx > (1 << 20) || p.ny > (1 << 20) || p.nz > (1 << 20))
       return einval("batched problem extent too large");
     if (!p.u) return einval("NULL problem grid");
+    const i64 units = sched_units(p.nx, p.ny, p.nz);
+    if (units > INT32_MAX) return einval("batched problem needs more than 2^31 - 1 work units");
     const size_t bytes = (size_t)Grid{p.nx, p.ny, p.nz, radius}.count() * sizeof(double);
     if (p.rhs && overlap(p.rhs, p.u, bytes)) return einval("problem rhs overlaps its u");
+    scratch += (double)Grid{p.nx, p.ny, p.nz, radius}.count() * (refined ? 20.0 : 8.0) + 8.0 * (double)units;
+  }
+  if (scratch > 1.0e15) {
+    set_error("batched problems need more scratch than any device holds");
+    return STN_ENOMEM;
   }
   if (count == 0) return STN_OK;
   for (i64 i = 0; i < count; i++) {

@@ -136,6 +136,9 @@ struct LaunchPlan {
 };
 LaunchPlan sweep_launch_plan(const Grid& g, size_t esize);
 LaunchPlan var_launch_plan(const Grid& g, size_t esize);
+// The work units of one batched problem (the scheduler's split: tile shape,
+// tiles, k chunks); the same on the host and in the scheduler kernel.
+LaunchPlan batch_unit_plan(i64 nx, i64 ny, i64 nz);
 // One launch: out = S u + b over the interior; in residual modes also the
 // per-block partial sums of rho^2 into `partials` (ZPlan::blocks() entries).
 template <typename T>

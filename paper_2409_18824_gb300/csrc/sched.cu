@@ -683,7 +683,27 @@ int sched_ctas(int radius, bool has_c0, bool refined) {
   return per_sm * sms;
 }
 
-i64 sched_units(i64 nx, i64 ny, i64 nz) { return make_geo((int)nx, (int)ny, (int)nz).n; }
+LaunchPlan batch_unit_plan(i64 nx, i64 ny, i64 nz) {
+  const Geo g = make_geo((int)nx, (int)ny, (int)nz);
+  LaunchPlan q;
+  q.variant = g.shape;
+  q.grid_x = g.tiles_x;
+  q.grid_y = g.tiles_y;
+  q.grid_z = g.kc;
+  q.block_threads = BT;
+  q.tile_w = tile_width(g.shape);
+  q.tile_h = BT / q.tile_w;
+  q.kchunk = g.klen;
+  q.stage_elems = kPlaneElems;
+  return q;
+}
+
+// The exact count (each factor fits an int for extents <= 2^20; their product
+// need not, and the batched entry points reject problems above 2^31 - 1).
+i64 sched_units(i64 nx, i64 ny, i64 nz) {
+  const Geo g = make_geo((int)nx, (int)ny, (int)nz);
+  return (i64)g.tiles_x * g.tiles_y * g.kc;
+}
 
 SchedFaults& sched_faults() {
   static SchedFaults f;

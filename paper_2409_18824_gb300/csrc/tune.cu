@@ -523,13 +523,19 @@ int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int e
     q = sweep_launch_plan(g, (size_t)esize);
   } else if (strcmp(op, "varcoef_sweep") == 0) {
     q = var_launch_plan(g, (size_t)esize);
+  } else if (strcmp(op, "batch_unit") == 0) {
+    if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20)) return tune_einval("batched problem extent too large");
+    q = batch_unit_plan(nx, ny, nz);
+    if ((i64)q.grid_x * q.grid_y * q.grid_z > INT32_MAX)
+      return tune_einval("batched problem needs more than 2^31 - 1 work units");
   } else if (strcmp(op, "sweep2d") == 0) {
     if (nz != 1) return tune_einval("sweep2d plans take nz = 1");
     q = sweep2d_launch_plan(Grid2{nx, ny, radius}, (size_t)esize);
   } else {
     return tune_einval(std::string("unknown op ") + op);
   }
-  if (int rc = check_launch_grid(q.grid_x, q.grid_y, q.grid_z)) return rc;
+  if (strcmp(op, "batch_unit") != 0)
+    if (int rc = check_launch_grid(q.grid_x, q.grid_y, q.grid_z)) return rc;
   out->variant = q.variant;
   out->grid_x = q.grid_x;
   out->grid_y = q.grid_y;

@@ -290,3 +290,56 @@ def test_sweep2d_plan_bands_layout_and_bulk_copies(lib, nx, ny, esize, r, ctas):
                         assert src % 16 == 0 and dst % 16 == 0 and nbytes % 16 == 0, (side, b)
                         assert xo <= src and src + nbytes <= scratch
                         assert t * buf <= dst and dst + nbytes <= (t + 1) * buf
+
+
+def test_batched_unit_split_covers_each_problem_once(lib):
+    """The batched solvers' and the server's split of a problem into work
+    units (tile shape x k chunk), over the benchmark's 2048-problem mix
+    (sizes log-uniform in [16, 128]), the serving mix ([32, 256]) and edge
+    extents: the tiles and chunks cover the interior exactly once with no
+    empty unit, the shape is the one with the fewest tiles (ties to the wider
+    rows), chunks are 32-64 planes (fewer only when nz is), and every shape's
+    shared plane (tile plus a halo of 2 on each side) fits the kernel's one
+    plane buffer.  The shape counts over the 2048 mix are those the
+    scheduler's measurements were taken with: 1050, 420 and 578."""
+    import stencil_inputs as si
+    mix = [tuple(int(v) for v in s) for s in si.log_uniform_sizes(2048, 16, 128, 4)]
+    serve = [tuple(int(v) for v in s) for s in si.log_uniform_sizes(48, 32, 256, 6)]
+    edge = [(1, 1, 1), (1, 1000, 3), (1000, 1, 3), (8, 32, 64), (9, 33, 65), (4096, 4096, 4096), (1 << 20, 1, 1)]
+    shapes = [0, 0, 0]
+    widths = {0: 32, 1: 16, 2: 8}
+    for k, (nx, ny, nz) in enumerate(mix + serve + edge):
+        q = lib.stencil_plan_query("batch_unit", nx, ny, nz, 8, 1)
+        tw, th = q["tile_w"], q["tile_h"]
+        assert q["block_threads"] == tw * th == 256 and tw == widths[q["variant"]]
+        assert (q["grid_x"], q["grid_y"], q["grid_z"]) == (ceil_div(nx, tw), ceil_div(ny, th), ceil_div(nz, q["kchunk"]))
+        tiles = {s: ceil_div(nx, w) * ceil_div(ny, 256 // w) for s, w in widths.items()}
+        assert tiles[q["variant"]] == min(tiles.values())
+        assert all(tiles[s] > tiles[q["variant"]] for s in range(q["variant"]))  # ties to the wider shape
+        assert q["kchunk"] <= 64 and (q["kchunk"] >= 32 or q["kchunk"] == nz)
+        for w in widths.values():
+            assert (256 // w + 4) * (w + 4) <= q["stage_elems"]
+        if k < len(mix):
+            shapes[q["variant"]] += 1
+    assert shapes == [1050, 420, 578]
+
+
+def test_batched_entry_rejects_problems_beyond_its_counters(lib):
+    """Checked on the host before any allocation or launch: a problem whose
+    units overflow a 32-bit count, and a batch whose scratch exceeds any
+    device's memory, are refused (no CUDA call is made, so this runs on the
+    CPU); the plan query refuses the former too."""
+    import ctypes
+    from paper_2409_18824_gb300 import Problem, StencilError
+    so = lib._lib
+    coeffs = (ctypes.c_double * 2)(0.0, 1.0 / 6.0)
+    fake = 1 << 40  # never dereferenced: the calls fail validation first
+    big = (Problem * 1)(Problem(1 << 20, 1 << 20, 8, None, fake))
+    assert so.jacobi_solve_batched_f64(big, 1, coeffs, 1, 1e-8, 10, 1, None, None) == -1
+    assert "work units" in lib.last_error()
+    with pytest.raises(StencilError):
+        lib.stencil_plan_query("batch_unit", 1 << 20, 1 << 20, 8, 8, 1)
+    # 400 problems of 2^20 x 2^16 x 8: each within its limits, 2.2e15 bytes in all
+    many = (Problem * 400)(*[Problem(1 << 20, 1 << 16, 8, None, fake + i * 4096) for i in range(400)])
+    assert so.jacobi_solve_batched_f64(many, 400, coeffs, 1, 1e-8, 10, 1, None, None) == -2
+    assert "scratch" in lib.last_error()
