@@ -362,7 +362,15 @@ def run_cuda(args, wl):
     }
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sweeps)
+            base, ref_out, ref_norm = cpu_baseline(wl, args.cpu_sweeps, keep=True)
+            out["cpu_baseline"] = base
+            try:
+                allc = cpu_all_cores(wl, args.cpu_sweeps, ref_out, ref_norm)
+            except Exception as e:  # context only: never costs the line
+                allc = {"error": f"{type(e).__name__}: {e}"}
+            if allc is not None:
+                out["cpu_all_cores"] = allc
+            del ref_out
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -1352,7 +1360,7 @@ def run_serving(args):
 
 
 # ------------------------------------------------------------ oracle (CPU) --
-def cpu_sample(wl, sweeps):
+def cpu_sample(wl, sweeps, keep=False):
     import oracle
     nx, ny, nz, r = wl["nx"], wl["ny"], wl["nz"], wl["r"]
     npdt = np.float64 if wl["dtype"] == "f64" else np.float32
@@ -1360,16 +1368,46 @@ def cpu_sample(wl, sweeps):
     oracle.build()
     t0 = time.perf_counter()
     out = oracle.stencil_sweep(u0, si.LAPLACE7, r, sweeps)
-    oracle.residual_norm(out, si.LAPLACE7, r)
+    norm = oracle.residual_norm(out, si.LAPLACE7, r)
     t = time.perf_counter() - t0
-    return float(nx) * ny * nz * sweeps / t / 1e9, t
+    val = float(nx) * ny * nz * sweeps / t / 1e9
+    return (val, t, out, norm) if keep else (val, t)
 
 
-def cpu_baseline(wl, sweeps):
-    val, t = cpu_sample(wl, sweeps)
-    return {"value": val, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sweeps} sweeps + 1 residual norm of the same {wl['nx']}x{wl['ny']}x{wl['nz']} "
-                      f"grid, plain C oracle, single thread ({t:.1f} s)"}
+def cpu_baseline(wl, sweeps, keep=False):
+    val, t, *rest = cpu_sample(wl, sweeps, keep=True)
+    d = {"value": val, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+         "sample": f"{sweeps} sweeps + 1 residual norm of the same {wl['nx']}x{wl['ny']}x{wl['nz']} "
+                   f"grid, plain C oracle, single thread ({t:.1f} s)"}
+    return (d, *rest) if keep else d
+
+
+def cpu_all_cores(wl, sweeps, ref_out=None, ref_norm=None):
+    """The single-thread oracle's sample on every host core, through the
+    multi-core host library (libstencil_host.so), whose sweeps are bitwise the
+    oracle's for any thread count: checked here against the oracle's output
+    when it is given.  Context beside the oracle baseline; FP64 workloads
+    only (None otherwise)."""
+    if wl["dtype"] != "f64":
+        return None
+    import paper_2409_18824_gb300.host as host
+    nx, ny, nz, r = wl["nx"], wl["ny"], wl["nz"], wl["r"]
+    u0 = si.uniform_interior(nx, ny, nz, r, seed=wl["seed"])
+    out = np.zeros_like(u0)
+    threads = host.threads()
+    t0 = time.perf_counter()
+    host.stencil_host_sweep_f64(u0, out, si.LAPLACE7, r, sweeps, nthreads=threads)
+    norm = host.stencil_host_residual_norm_f64(out, si.LAPLACE7, r, nthreads=threads)
+    t = time.perf_counter() - t0
+    d = {"value": float(nx) * ny * nz * sweeps / t / 1e9, "unit": "GLUP/s", "cores": threads,
+         "kind": "host library (the oracle's arithmetic, multi-threaded)",
+         "sample": f"{sweeps} sweeps + 1 residual norm of the same {nx}x{ny}x{nz} grid on {threads} threads "
+                   f"({t:.2f} s)"}
+    if ref_out is not None:
+        d["bitwise_oracle"] = bool(np.array_equal(out.view(np.uint64), ref_out.view(np.uint64)))
+    if ref_norm is not None:
+        d["norm_rel_diff_oracle"] = abs(norm - ref_norm) / ref_norm if ref_norm else 0.0
+    return d
 
 
 def run_reference(args, wl):

@@ -80,3 +80,16 @@ def test_step_stats():
 
     st = bench.step_stats([Ev(0.0), Ev(2.0), Ev(5.0), Ev(6.0)])
     assert st["n"] == 3 and st["min"] == 1.0 and st["median"] == 2.0 and abs(st["mean"] - 2.0) < 1e-12
+
+
+def test_all_cores_baseline_is_the_oracles_sample_bitwise():
+    """The bench's all-cores figure runs the oracle baseline's own sample
+    (same seeded grid, sweeps and norm) through the multi-core host library:
+    the result must be the oracle's bits, and float workloads get none."""
+    wl = {"nx": 40, "ny": 33, "nz": 27, "r": 1, "dtype": "f64", "seed": 2}
+    base, ref_out, ref_norm = bench.cpu_baseline(wl, 5, keep=True)
+    assert base["kind"] == "oracle" and base["cores"] == 1 and base["value"] > 0
+    d = bench.cpu_all_cores(wl, 5, ref_out, ref_norm)
+    assert d["bitwise_oracle"] is True and d["norm_rel_diff_oracle"] <= 40 * 33 * 27 * 2.0 ** -53
+    assert d["cores"] >= 1 and d["value"] > 0 and d["unit"] == "GLUP/s"
+    assert bench.cpu_all_cores(dict(wl, dtype="f32"), 5) is None
