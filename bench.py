@@ -74,11 +74,22 @@ def load_peaks():
 # by its 32.8 M updates; summaries under profiles/).  Set to None whenever the
 # kernel changes until it is captured again.
 TRAFFIC_BYTES_PER_LUP = {
-    ("f64", 0): 491.5e6 / 320 ** 3,   # plane kernel (star_kernel<double,1>, 16-plane chunks)
-    ("f32", 1): 225.6e6 / 320 ** 3,   # column kernel (star_col_kernel<float,1>, 2 planes prefetched)
-    ("f32", 3): 232.9e6 / 320 ** 3,   # staged kernel (star_staged_kernel<float,1>, 152 blocks)
-    ("f32", -1): 232.9e6 / 320 ** 3,  # automatic: the staged kernel for these large float grids
+    ("f64", 0): (271.3e6 + 220.2e6) / 320 ** 3,  # plane kernel (star_kernel<double,1>, 16-plane chunks)
+    ("f32", 1): (143.0e6 + 82.2e6) / 320 ** 3,  # column kernel (star_col_kernel<float,1>, 2 planes prefetched)
+    ("f32", 3): (151.5e6 + 81.4e6) / 320 ** 3,  # staged kernel (star_staged_kernel<float,1>, 152 blocks)
+    ("f32", -1): (151.5e6 + 81.4e6) / 320 ** 3,  # automatic: the staged kernel for these large float grids
 }
+
+# DRAM bytes (read + write) of the other timed kernels, from their ncu
+# captures, per unit the launch processes: the 2-D resident launch (1024^2,
+# bulk-copy build), the dot product per element pair and the sum per element
+# (2^27 elements), the self-advection per cell (512 x 512 x 256), and the
+# variable-coefficient float sweep per update (512 x 512 x 256)
+TRAFFIC_J2D_LAUNCH = 8.44e6 + 6.7e3
+TRAFFIC_DOT_PER_PAIR = (2.1476e9 + 2.9e6) / 2 ** 27
+TRAFFIC_SUM_PER_ELEMENT = (1.0738e9 + 3.1e6) / 2 ** 27
+TRAFFIC_ADVECT_PER_CELL = (1.733e9 + 1.575e9) / (512 * 512 * 256)
+TRAFFIC_VARCOEF_F32_PER_LUP = (830.4e6 + 253.1e6) / (512 * 512 * 256)
 
 # FP64 issue rate of this GPU measured with a throughput probe: 2 double
 # fused-multiply-add instructions per clock per SM (every double add and
@@ -489,10 +500,11 @@ def run_jacobi2d(args):
         "e2e": {"value": lups / e2e_s / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": 2 * u0.nbytes,
                 "d2h_bytes_per_step": u0.nbytes + 8},
         "gpu_launches": args.steps * launches_per_step,
-        # DRAM bytes of one resident launch (ncu on this grid): the grid read once
-        # (8.45 MB) and 7.7 KB written before the kernel ends (the rest leaves L2 later)
+        # DRAM bytes of one resident launch (ncu on this grid, the bulk-copy build):
+        # the grid read once (8.44 MB) and 6.7 KB written before the kernel ends
+        # (the rest leaves L2 later)
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": 8.45e6 + 7.7e3, "traffic_unit": "bytes per launch",
+                     "frac": achieved / fp64_peak, "traffic": TRAFFIC_J2D_LAUNCH, "traffic_unit": "bytes per launch",
                      "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
                      "kernel": "j2d_resident_kernel<double,1>", "kernel_ms": kern_ms,
                      "kernel_sweeps": k_sweeps},
@@ -718,15 +730,15 @@ def run_intrinsic(args, kind):
         # DRAM bytes of one launch: ncu on a 2^27-element case read 8.02 B per
         # element (no re-reads), scaled by the elements
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": 8.02 * n, "traffic_unit": "bytes per launch",
+                    "frac": achieved / fp64_peak, "traffic": TRAFFIC_SUM_PER_ELEMENT * n, "traffic_unit": "bytes per launch",
                     "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
                     "hbm_achieved_gbs": nbytes / sec / 1e9, "hbm_peak_gbs": hbm_peak,
                     "hbm_frac": nbytes / sec / 1e9 / hbm_peak, "hbm_peak_kind": peak_kind,
                     "kernel": "sum_kernel", "kernel_ms": ms / args.steps, "note": note}
     else:
-        # ncu on the full 2^27-element dot: 2.1476 GB read, 16.0 B per element
+        # ncu on the full 2^27-element dot: 2.1476 GB read, 2.9 MB written
         roofline = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": nbytes / sec / 1e9 / hbm_peak, "traffic": 2.1476e9 / 2 ** 27 * n,
+                    "frac": nbytes / sec / 1e9 / hbm_peak, "traffic": TRAFFIC_DOT_PER_PAIR * n,
                     "traffic_unit": "bytes per launch",
                     "peak_kind": peak_kind, "kernel": "vec_reduce_kernel<true>", "kernel_ms": ms / args.steps,
                     "note": note}
@@ -907,7 +919,7 @@ def run_advect(args):
         # ncu on a 512 x 512 x 256 case: 3.308 GB for 67.1 M cells = 49.3 B per
         # cell (5 % halo re-reads), scaled by the cells of this launch
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": 49.3 * cells, "traffic_unit": "bytes per launch",
+                     "frac": achieved / fp64_peak, "traffic": TRAFFIC_ADVECT_PER_CELL * cells, "traffic_unit": "bytes per launch",
                      "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
                      "ops_per_cell": ADVECT_FP64_OPS, "hbm_achieved_gbs": cells * ADVECT_BYTES / sec / 1e9,
                      "hbm_peak_gbs": hbm_peak, "hbm_frac": cells * ADVECT_BYTES / sec / 1e9 / hbm_peak,
@@ -1194,7 +1206,7 @@ def run_varcoef(args):
     # ncu on a 512 x 512 x 256 float sweep: 830.4 MB read + 253.1 MB written for
     # 67.1 M updates = 16.15 B per update, scaled to the full grid
     roofline = {"bound": "hbm", "achieved": fs["f32_sweep_hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": fs["f32_sweep_hbm_gbs"] / hbm_peak, "traffic": 16.15 * 768 * 768 * 384,
+                "frac": fs["f32_sweep_hbm_gbs"] / hbm_peak, "traffic": TRAFFIC_VARCOEF_F32_PER_LUP * 768 * 768 * 384,
                 "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
                 "kernel": "var_col_kernel<float,2> (one float sweep at 768 x 768 x 384)",
                 "kernel_ms": fs["f32_sweep_ms"]}
