@@ -1498,22 +1498,25 @@ def main():
         ap.error("steps >= 1, warmup >= 0")
     if args.workload == "varcoef":
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "variable-coefficient workload: CPU oracle arm "
-                              "only implemented for the sweep workloads"}))
+            print(json.dumps({"impl": "reference", "unavailable": "variable-coefficient workload: the oracle's "
+                              "solve of the 768x768x384 grid to 1e-10 takes days of one core; the tests check "
+                              "the GPU against it at 96x96x48 and on sampled windows"}))
             return
         run_varcoef(args)
         return
     if args.workload == "serve":
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "serving workload: CPU oracle arm only "
-                              "implemented for the sweep workloads"}))
+            print(json.dumps({"impl": "reference", "unavailable": "serving workload: the oracle's solves of "
+                              "48 grids of up to 256^3 take about an hour of one core per step; the tests check served results "
+                              "against the batched path and it against the oracle"}))
             return
         run_serving(args)
         return
     if args.workload == "batch":
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "batched workload: CPU oracle arm only "
-                              "implemented for the sweep workloads"}))
+            print(json.dumps({"impl": "reference", "unavailable": "batched workload: the oracle's 2048 solves "
+                              "take hours of one core per step; the tests check sampled solves bitwise and the "
+                              "default line's cpu_baseline projects the rate"}))
             return
         run_batched(args)
         return

@@ -93,3 +93,29 @@ def test_all_cores_baseline_is_the_oracles_sample_bitwise():
     assert d["bitwise_oracle"] is True and d["norm_rel_diff_oracle"] <= 40 * 33 * 27 * 2.0 ** -53
     assert d["cores"] >= 1 and d["value"] > 0 and d["unit"] == "GLUP/s"
     assert bench.cpu_all_cores(dict(wl, dtype="f32"), 5) is None
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.parametrize("workload,extra", [("jacobi2d", ["--cpu-sweeps2d", "20"]), ("advect", [])])
+def test_other_reference_arms(workload, extra):
+    """The 2-D jacobi and advection reference arms: the oracle on a bounded
+    sample, one JSON line with the contract's keys."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", workload, "--steps", "1",
+                        "--warmup", "0", *extra], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["config"]["workload"]
+
+
+@pytest.mark.parametrize("workload", ["batch", "serve", "varcoef"])
+def test_reference_arms_that_cannot_run_say_why(workload):
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", workload, "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["impl"] == "reference" and "oracle" in d["unavailable"]
