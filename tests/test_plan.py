@@ -343,3 +343,32 @@ def test_batched_entry_rejects_problems_beyond_its_counters(lib):
     many = (Problem * 400)(*[Problem(1 << 20, 1 << 16, 8, None, fake + i * 4096) for i in range(400)])
     assert so.jacobi_solve_batched_f64(many, 400, coeffs, 1, 1e-8, 10, 1, None, None) == -2
     assert "scratch" in lib.last_error()
+
+
+def random_extents(n, seed, dims, hi):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return [tuple(int(v) for v in np.exp(rng.uniform(0.0, np.log(hi), size=dims)).round().clip(1, None))
+            for _ in range(n)]
+
+
+def test_random_extents_all_plans(lib):
+    """The same checks on 300 seeded random extents (log-uniform in
+    [1, 4000] per axis) for both types and radii, with the staged kernel's
+    copy replay forced on wherever its ring fits."""
+    import numpy as np
+    rng = np.random.default_rng(91)
+    for (nx, ny, nz) in random_extents(300, 90, 3, 4000):
+        esize, r = int(rng.choice([4, 8])), int(rng.choice([1, 2]))
+        test_sweep_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r)
+        test_varcoef_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r)
+        if esize == 4:
+            test_staged_ring_copies_and_reads_stay_in_bounds(lib, nx, ny, nz, esize, r)
+
+
+def test_random_extents_2d_plans(lib):
+    import numpy as np
+    rng = np.random.default_rng(93)
+    for (nx, ny) in random_extents(150, 92, 2, 20000):
+        esize, r = int(rng.choice([4, 8])), int(rng.choice([1, 2]))
+        test_sweep2d_plan_bands_layout_and_bulk_copies(lib, nx, ny, esize, r, 1)
