@@ -90,7 +90,9 @@ __host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
   if (klen > nz) klen = nz;
   g.klen = (int)klen;
   g.kc = (nz + g.klen - 1) / g.klen;
-  g.n = g.tiles_x * g.tiles_y * g.kc;
+  // unsigned: wraps instead of overflowing for extents the entry points
+  // reject (they use the exact 64-bit count); equal to the product otherwise
+  g.n = (int)((unsigned)g.tiles_x * (unsigned)g.tiles_y * (unsigned)g.kc);
   return g;
 }
 

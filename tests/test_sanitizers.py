@@ -60,3 +60,52 @@ def test_oracle_and_host_library_are_clean_under_asan_and_ubsan(tmp_path):
                        cwd=work, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
     assert "passed" in r.stdout and "failed" not in r.stdout
+
+
+@pytest.mark.slow
+def test_gpu_librarys_host_code_is_clean_under_asan_and_ubsan(tmp_path):
+    """The host code of libstencil.so that runs without a GPU (argument
+    checks, knobs, the launch planners and the plan query, the tuning cache
+    and its JSON reader and writer) rebuilt with the sanitizers through nvcc
+    (device code unchanged), and the ABI and plan tests run against it.  This
+    found a signed overflow in the work-unit count for rejected extents."""
+    import concurrent.futures as cf
+    asan, ubsan = runtime("libasan.so"), runtime("libubsan.so")
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if not (asan and ubsan and nvcc):
+        pytest.skip("nvcc or gcc sanitizer runtimes not available")
+    work = tmp_path / "w"
+    work.mkdir()
+    for d in ("oracle", "stencil_inputs", "include"):
+        shutil.copytree(os.path.join(ROOT, d), work / d, ignore=shutil.ignore_patterns("__pycache__"))
+    pkg = work / "paper_2409_18824_gb300"
+    shutil.copytree(os.path.join(ROOT, "paper_2409_18824_gb300"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "_build", "libstencil.so"))
+    (work / "tests").mkdir()
+    for f in ("conftest.py", "test_abi.py", "test_plan.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), work / "tests" / f)
+    flags = ["-gencode", "arch=compute_103a,code=sm_103a", "-O1", "-std=c++17", "--expt-relaxed-constexpr",
+             "-Xcompiler", "-fPIC", "-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+             "-Xcompiler", "-fno-omit-frame-pointer", "-I", str(work / "include"), "-I", str(pkg / "csrc")]
+    srcs = sorted(p for p in (pkg / "csrc").iterdir() if p.suffix == ".cu")
+    objs = [tmp_path / (p.stem + ".o") for p in srcs]
+
+    def compile_one(pair):
+        src, obj = pair
+        return subprocess.run([nvcc, *flags, "-c", str(src), "-o", str(obj)], capture_output=True, text=True)
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+        for res in ex.map(compile_one, zip(srcs, objs)):
+            assert res.returncode == 0, res.stderr[-3000:]
+    link = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-Xcompiler",
+                           "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined", "-o",
+                           str(pkg / "libstencil.so"), *map(str, objs), "-lpthread"], capture_output=True, text=True)
+    assert link.returncode == 0, link.stderr[-3000:]
+    env = dict(os.environ, LD_PRELOAD=f"{asan}:{ubsan}",
+               ASAN_OPTIONS="detect_leaks=0:abort_on_error=1:protect_shadow_gap=0",
+               UBSAN_OPTIONS="halt_on_error=1:print_stacktrace=1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-s", "-p", "no:cacheprovider", "-m", "not gpu",
+                        "tests/test_abi.py", "tests/test_plan.py"],
+                       cwd=work, env=env, capture_output=True, text=True, timeout=1200)
+    assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
+    assert "passed" in r.stdout and "runtime error" not in r.stdout + r.stderr
