@@ -372,3 +372,18 @@ def test_random_extents_2d_plans(lib):
     for (nx, ny) in random_extents(150, 92, 2, 20000):
         esize, r = int(rng.choice([4, 8])), int(rng.choice([1, 2]))
         test_sweep2d_plan_bands_layout_and_bulk_copies(lib, nx, ny, esize, r, 1)
+
+
+@pytest.mark.parametrize("op,esize,r", [("sweep", 8, 1), ("sweep", 8, 2), ("sweep", 4, 1), ("sweep", 4, 2),
+                                        ("varcoef_sweep", 8, 2), ("varcoef_sweep", 4, 2)])
+def test_rejection_starts_one_row_past_65535_tiles(lib, op, esize, r):
+    """For a 1-column, 1-plane grid, the planned tile height h fixes the
+    limit: ny = 65535 h plans exactly 65535 blocks in y and is accepted,
+    ny = 65535 h + 1 is refused (unless the planner then picks a kernel with
+    taller tiles, in which case that plan must be within the limit)."""
+    h = lib.stencil_plan_query(op, 1, 1000, 1, esize, r)["tile_h"]
+    q = lib.stencil_plan_query(op, 1, 65535 * h, 1, esize, r)
+    if q["tile_h"] == h:
+        assert q["grid_y"] == 65535
+    after = plan_or_rejected(lib, op, 1, 65535 * h + 1, 1, esize, r)
+    assert after is None or (after["grid_y"] <= 65535 and after["tile_h"] > h)
