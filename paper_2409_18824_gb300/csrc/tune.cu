@@ -4,6 +4,7 @@
 // temporal depth are picked by timing candidates on the device, per grid
 // extents, and kept in a process-wide cache that the planners consult and
 // that can be saved to and loaded from a JSON file.
+#include <ctype.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -90,76 +91,151 @@ void put_locked(const Key& k, const Val& v) {
 }
 
 // ---- JSON (the cache's own flat format) ---------------------------------------
-// One object per entry with string "device" and numeric fields; no nesting.
-bool json_string(const std::string& obj, const char* key, std::string* out) {
-  const std::string pat = std::string("\"") + key + "\"";
-  size_t p = obj.find(pat);
-  if (p == std::string::npos) return false;
-  p = obj.find(':', p + pat.size());
-  if (p == std::string::npos) return false;
-  p = obj.find('"', p + 1);
-  if (p == std::string::npos) return false;
+// Entries are flat objects: string or number values, no nesting.  Objects are
+// read key by key in order (never by searching the text, so a key's name
+// inside a string value cannot be mistaken for the key).
+
+// Reads the string starting at t[*i] == '"' (escapes decoded; \uXXXX only for
+// code points below 256, which is all the writer emits) and moves *i past it.
+bool json_read_string(const std::string& t, size_t* i, std::string* out) {
   std::string v;
-  for (size_t i = p + 1; i < obj.size(); i++) {
-    const char c = obj[i];
-    if (c == '\\' && i + 1 < obj.size()) {
-      v += obj[++i];
-    } else if (c == '"') {
+  for (size_t k = *i + 1; k < t.size(); k++) {
+    const char c = t[k];
+    if (c == '"') {
       *out = v;
+      *i = k + 1;
       return true;
-    } else {
+    }
+    if ((unsigned char)c < 0x20) return false;  // raw control characters are not JSON
+    if (c != '\\') {
       v += c;
+      continue;
+    }
+    if (++k >= t.size()) return false;
+    switch (t[k]) {
+      case '"': v += '"'; break;
+      case '\\': v += '\\'; break;
+      case '/': v += '/'; break;
+      case 'b': v += '\b'; break;
+      case 'f': v += '\f'; break;
+      case 'n': v += '\n'; break;
+      case 'r': v += '\r'; break;
+      case 't': v += '\t'; break;
+      case 'u': {
+        if (k + 4 >= t.size()) return false;
+        unsigned cp = 0;
+        for (int h = 1; h <= 4; h++) {
+          const char x = t[k + h];
+          cp <<= 4;
+          if (x >= '0' && x <= '9') cp |= (unsigned)(x - '0');
+          else if (x >= 'a' && x <= 'f') cp |= (unsigned)(x - 'a' + 10);
+          else if (x >= 'A' && x <= 'F') cp |= (unsigned)(x - 'A' + 10);
+          else return false;
+        }
+        if (cp > 0xff) return false;
+        v += (char)cp;
+        k += 4;
+        break;
+      }
+      default: return false;
     }
   }
   return false;
 }
 
-bool json_number(const std::string& obj, const char* key, double* out) {
-  const std::string pat = std::string("\"") + key + "\"";
-  size_t p = obj.find(pat);
-  if (p == std::string::npos) return false;
-  p = obj.find(':', p + pat.size());
-  if (p == std::string::npos) return false;
-  const char* s = obj.c_str() + p + 1;
+struct JsonValue {
+  bool is_str = false;
+  std::string text;  // the decoded string, or the number's characters
+};
+
+void json_skip_ws(const std::string& t, size_t* i) {
+  while (*i < t.size() && (t[*i] == ' ' || t[*i] == '\t' || t[*i] == '\n' || t[*i] == '\r')) ++*i;
+}
+
+// Reads the flat object starting at t[*i] == '{' into `f` (a repeated key
+// keeps its last value) and moves *i past its '}'; false on any syntax error.
+bool json_read_object(const std::string& t, size_t* i, std::map<std::string, JsonValue>* f) {
+  size_t k = *i + 1;
+  json_skip_ws(t, &k);
+  if (k < t.size() && t[k] == '}') {
+    *i = k + 1;
+    return true;
+  }
+  for (;;) {
+    json_skip_ws(t, &k);
+    if (k >= t.size() || t[k] != '"') return false;
+    std::string key;
+    if (!json_read_string(t, &k, &key)) return false;
+    json_skip_ws(t, &k);
+    if (k >= t.size() || t[k] != ':') return false;
+    ++k;
+    json_skip_ws(t, &k);
+    if (k >= t.size()) return false;
+    JsonValue v;
+    if (t[k] == '"') {
+      v.is_str = true;
+      if (!json_read_string(t, &k, &v.text)) return false;
+    } else {
+      const size_t s0 = k;
+      while (k < t.size() && (isdigit((unsigned char)t[k]) || t[k] == '-' || t[k] == '+' || t[k] == '.' ||
+                              t[k] == 'e' || t[k] == 'E'))
+        k++;
+      if (k == s0) return false;
+      v.text = t.substr(s0, k - s0);
+    }
+    (*f)[key] = v;
+    json_skip_ws(t, &k);
+    if (k >= t.size()) return false;
+    if (t[k] == ',') {
+      k++;
+      continue;
+    }
+    if (t[k] != '}') return false;
+    *i = k + 1;
+    return true;
+  }
+}
+
+bool json_field_number(const std::map<std::string, JsonValue>& f, const char* key, double* out) {
+  const auto it = f.find(key);
+  if (it == f.end() || it->second.is_str) return false;
+  const char* s = it->second.text.c_str();
   char* end = nullptr;
   const double v = strtod(s, &end);
-  if (end == s || !isfinite(v)) return false;
+  if (end != s + it->second.text.size() || !isfinite(v)) return false;
   *out = v;
   return true;
 }
 
-bool json_int(const std::string& obj, const char* key, i64* out) {
+bool json_field_int(const std::map<std::string, JsonValue>& f, const char* key, i64* out) {
   double v;
-  if (!json_number(obj, key, &v) || v != floor(v) || fabs(v) > 9.0e15) return false;
+  if (!json_field_number(f, key, &v) || v != floor(v) || fabs(v) > 9.0e15) return false;
   *out = (i64)v;
   return true;
 }
 
-// Index of the '}' closing the object that starts at text[o] (braces inside
-// strings skipped), or npos.
-size_t json_object_end(const std::string& text, size_t o) {
-  bool in_str = false;
-  for (size_t i = o + 1; i < text.size(); i++) {
-    const char c = text[i];
-    if (in_str) {
-      if (c == '\\') i++;
-      else if (c == '"') in_str = false;
-    } else if (c == '"') {
-      in_str = true;
-    } else if (c == '}') {
-      return i;
-    } else if (c == '{') {
-      return std::string::npos;  // no nesting in this format
-    }
-  }
-  return std::string::npos;
+bool json_field_string(const std::map<std::string, JsonValue>& f, const char* key, std::string* out) {
+  const auto it = f.find(key);
+  if (it == f.end() || !it->second.is_str) return false;
+  *out = it->second.text;
+  return true;
 }
 
+// JSON string body of s: quotes and backslashes escaped, control bytes as
+// \u00XX, every other byte as it is.
 std::string json_escape(const std::string& s) {
   std::string o;
   for (char c : s) {
-    if (c == '"' || c == '\\') o += '\\';
-    if ((unsigned char)c >= 0x20) o += c;
+    if (c == '"' || c == '\\') {
+      o += '\\';
+      o += c;
+    } else if ((unsigned char)c < 0x20) {
+      char u[8];
+      snprintf(u, sizeof u, "\\u%04x", (unsigned)(unsigned char)c);
+      o += u;
+    } else {
+      o += c;
+    }
   }
   return o;
 }
@@ -444,7 +520,7 @@ int stencil_tune_cache_save(const char* path) {
     std::lock_guard<std::mutex> lk(g_mu);
     size_t i = 0;
     for (const auto& kv : g_cache) {
-      char buf[768];
+      char buf[1024];
       snprintf(buf, sizeof buf,
                "  {\"device\": \"%s\", \"esize\": %d, \"radius\": %d, \"nx\": %lld, \"ny\": %lld, \"nz\": %lld, "
                "\"variant\": %d, \"chunks\": %d, \"depth\": %d, \"glups\": %.17g, \"default_glups\": %.17g}%s\n",
@@ -482,28 +558,44 @@ int stencil_tune_cache_load(const char* path) {
   p = text.find('[', p);
   if (p == std::string::npos) return tune_einval("tuning cache without an entry list");
   std::vector<std::pair<Key, Val>> got;
+  size_t i = p + 1;
+  json_skip_ws(text, &i);
+  bool first = true;
   for (;;) {
-    const size_t o = text.find_first_of("{]", p + 1);
-    if (o == std::string::npos) return tune_einval("unterminated entry list");
-    if (text[o] == ']') break;
-    const size_t c = json_object_end(text, o);
-    if (c == std::string::npos) return tune_einval("unterminated entry");
-    const std::string obj = text.substr(o, c - o + 1);
+    if (i >= text.size()) return tune_einval("unterminated entry list");
+    if (text[i] == ']') break;
+    if (!first) {
+      if (text[i] != ',') return tune_einval("malformed entry list");
+      i++;
+      json_skip_ws(text, &i);
+    }
+    first = false;
+    if (i >= text.size() || text[i] != '{') return tune_einval("malformed entry list");
+    const size_t o = i;
+    std::map<std::string, JsonValue> fields;
+    if (!json_read_object(text, &i, &fields)) return tune_einval("malformed tuning cache entry");
+    const std::string obj = text.substr(o, std::min<size_t>(i - o, 200));
     std::string dev;
     i64 esize, r, nx, ny, nz, variant, chunks, depth;
     double glups = 0, dglups = 0;
-    if (!json_string(obj, "device", &dev) || !json_int(obj, "esize", &esize) || !json_int(obj, "radius", &r) ||
-        !json_int(obj, "nx", &nx) || !json_int(obj, "ny", &ny) || !json_int(obj, "nz", &nz) ||
-        !json_int(obj, "variant", &variant) || !json_int(obj, "chunks", &chunks) || !json_int(obj, "depth", &depth))
+    if (!json_field_string(fields, "device", &dev) || !json_field_int(fields, "esize", &esize) ||
+        !json_field_int(fields, "radius", &r) || !json_field_int(fields, "nx", &nx) ||
+        !json_field_int(fields, "ny", &ny) || !json_field_int(fields, "nz", &nz) ||
+        !json_field_int(fields, "variant", &variant) || !json_field_int(fields, "chunks", &chunks) ||
+        !json_field_int(fields, "depth", &depth))
       return tune_einval("malformed tuning cache entry: " + obj);
-    (void)json_number(obj, "glups", &glups);
-    (void)json_number(obj, "default_glups", &dglups);
+    if (fields.count("glups") && !json_field_number(fields, "glups", &glups))
+      return tune_einval("malformed tuning cache entry: " + obj);
+    if (fields.count("default_glups") && !json_field_number(fields, "default_glups", &dglups))
+      return tune_einval("malformed tuning cache entry: " + obj);
+    if (dev.size() >= sizeof(((stn_tune_entry*)nullptr)->device))
+      return tune_einval("tuning cache entry with a device name of 64 bytes or more");
     if (esize > 8 || r > 2 || variant > 3 || chunks > 65535 || depth > 4)
       return tune_einval("tuning cache entry out of range: " + obj);
     if (int rc = check_key(nx, ny, nz, (int)esize, (int)r)) return rc;
     if (int rc = check_val((int)variant, (int)chunks, (int)depth)) return rc;
     got.push_back({Key{dev, (int)esize, (int)r, nx, ny, nz}, Val{(int)variant, (int)chunks, (int)depth, glups, dglups}});
-    p = c;
+    json_skip_ws(text, &i);
   }
   std::lock_guard<std::mutex> lk(g_mu);
   for (const auto& kv : got) put_locked(kv.first, kv.second);

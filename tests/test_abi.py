@@ -307,3 +307,88 @@ def test_server_rejects_bad_options(lib):
     o.hbm_budget = 0
     assert not lib.lib().stn_server_create(ctypes.byref(o))
     assert not lib.lib().stn_server_create(None)
+
+
+def _fuzz_cases():
+    """Seeded mutations of a valid cache file (truncations, byte flips,
+    inserted structural characters, deep nesting) and random text."""
+    import random
+    good = ('{"stencil_tune_cache": 1, "entries": [{"device": "d \\"q\\" {x}", "nx": 8, "ny": 9, "nz": 10, '
+            '"esize": 8, "radius": 1, "variant": 2, "chunks": 3, "depth": 1, "glups": 1.5e2, '
+            '"default_glups": -0.0}]}')
+    rng = random.Random(20261204)
+    cases = [good[:n] for n in range(0, len(good), 7)]
+    alphabet = '{}[]":,\\ \n\t0123456789.-+eE' + "abcdefxyz" + "\x00\x7f\xff"
+    for _ in range(300):
+        s = list(good)
+        for _ in range(rng.randint(1, 6)):
+            op, pos = rng.randint(0, 2), rng.randrange(len(s) + 1)
+            if op == 0 and s:
+                del s[min(pos, len(s) - 1)]
+            elif op == 1:
+                s.insert(pos, rng.choice(alphabet))
+            elif s:
+                s[min(pos, len(s) - 1)] = rng.choice(alphabet)
+        cases.append("".join(s))
+    cases += ["".join(rng.choice(alphabet) for _ in range(rng.randint(0, 200))) for _ in range(100)]
+    cases += ["[" * 5000, "{" * 5000, '"' + "\\" * 4999, '{"entries": ' + "[" * 3000]
+    return cases
+
+
+def test_tune_cache_reader_survives_malformed_files(lib, empty_cache, tmp_path):
+    """The cache file reader never crashes and never half-loads: every input
+    either loads whole (returns the entry count) or is refused with
+    STN_EINVAL and adds nothing."""
+    path = tmp_path / "fuzz.json"
+    so = lib.lib()
+    for i, text in enumerate(_fuzz_cases()):
+        path.write_bytes(text.encode("latin-1", errors="replace"))
+        lib.stencil_tune_cache_clear()
+        rc = so.stencil_tune_cache_load(os.fsencode(str(path)))
+        assert rc == lib.STN_EINVAL or rc >= 0, (i, rc)
+        if rc == lib.STN_EINVAL:
+            assert lib.stencil_tune_cache_size() == 0, i
+        else:
+            assert lib.stencil_tune_cache_size() == rc, i
+    lib.stencil_tune_cache_clear()
+
+
+def test_tune_cache_round_trips_random_entries(lib, empty_cache, tmp_path):
+    import random
+    rng = random.Random(7)
+    entries = {}
+    for _ in range(200):
+        key = (rng.randint(1, 1 << 28), rng.randint(1, 1 << 28), rng.randint(1, 1 << 28), rng.choice([4, 8]),
+               rng.choice([1, 2]))
+        dev = "".join(rng.choice('ab "\\{}[],:xyz\t') for _ in range(rng.randint(0, 40)))
+        val = (rng.randint(0, 3), rng.randint(1, 65535), rng.randint(1, 4), rng.uniform(0, 1e4))
+        lib.stencil_tune_cache_put(*key, *val[:3], device=dev, glups=val[3])
+        entries[(dev,) + key] = val
+    path = str(tmp_path / "rt.json")
+    lib.stencil_tune_cache_save(path)
+    lib.stencil_tune_cache_clear()
+    assert lib.stencil_tune_cache_load(path) == len(entries)
+    for (dev, *key), (v, c, d, g) in entries.items():
+        e = lib.stencil_tune_cache_get(*key, device=dev)
+        assert (e["variant"], e["chunks"], e["depth"]) == (v, c, d) and e["glups"] == g
+
+
+def test_tune_cache_device_names_that_look_like_fields(lib, empty_cache, tmp_path):
+    """A device name ending in '"nx' is written as ...\\"nx" -- the text '"nx"'
+    appears inside the string.  The reader takes fields in order, so such
+    names (and ones holding whole fake fields, tabs or newlines) load back
+    exactly, with every number intact."""
+    names = ['gpu"nx', 'a"esize', 'x", "nx": 1, "y', 'tab\there', 'nl\nx', 'q\\"depth"', '"variant": 3}']
+    for k, dev in enumerate(names):
+        lib.stencil_tune_cache_put(100 + k, 200 + k, 300 + k, 8, 2, 1, 7 + k, 2, device=dev, glups=1.25 * k)
+    path = str(tmp_path / "names.json")
+    lib.stencil_tune_cache_save(path)
+    import json
+    assert [e["device"] for e in json.load(open(path))["entries"]] == sorted(names)  # valid JSON, names exact
+    lib.stencil_tune_cache_clear()
+    assert lib.stencil_tune_cache_load(path) == len(names)
+    for k, dev in enumerate(names):
+        e = lib.stencil_tune_cache_get(100 + k, 200 + k, 300 + k, 8, 2, device=dev)
+        assert e is not None, dev
+        assert (e["nx"], e["ny"], e["nz"], e["variant"], e["chunks"], e["depth"], e["glups"]) == (
+            100 + k, 200 + k, 300 + k, 1, 7 + k, 2, 1.25 * k)
