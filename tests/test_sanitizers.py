@@ -109,3 +109,29 @@ def test_gpu_librarys_host_code_is_clean_under_asan_and_ubsan(tmp_path):
                        cwd=work, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
     assert "passed" in r.stdout and "runtime error" not in r.stdout + r.stderr
+
+
+@pytest.mark.slow
+def test_host_library_threads_are_race_free_under_tsan(tmp_path):
+    """The multi-core host path's workers and their barrier under gcc's
+    ThreadSanitizer: the host-path tests (1 to 64 threads) run against an
+    instrumented build, any data race fatal."""
+    tsan = runtime("libtsan.so")
+    if not (tsan and shutil.which("g++")):
+        pytest.skip("gcc thread sanitizer runtime not available")
+    work = tmp_path / "w"
+    work.mkdir()
+    for d in ("oracle", "stencil_inputs", "include", "paper_2409_18824_gb300"):
+        shutil.copytree(os.path.join(ROOT, d), work / d, ignore=shutil.ignore_patterns("__pycache__", "_build"))
+    (work / "tests").mkdir()
+    for f in ("conftest.py", "test_host_path.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), work / "tests" / f)
+    subprocess.run(["g++", "-O1", "-g", "-fsanitize=thread", "-ffp-contract=off", "-pthread", "-fPIC", "-shared",
+                    "-std=c++17", "-I", str(work / "include"), "-o",
+                    str(work / "paper_2409_18824_gb300" / "libstencil_host.so"),
+                    str(work / "paper_2409_18824_gb300" / "host" / "stencil_host.cpp")], check=True)
+    env = dict(os.environ, LD_PRELOAD=tsan, TSAN_OPTIONS="halt_on_error=1:report_signal_unsafe=0")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-s", "-p", "no:cacheprovider",
+                        "tests/test_host_path.py"], cwd=work, env=env, capture_output=True, text=True, timeout=1200)
+    assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
+    assert "passed" in r.stdout and "ThreadSanitizer" not in r.stdout + r.stderr
