@@ -185,8 +185,19 @@ def version() -> str:
 
 
 # ------------------------------------------------------------- marshalling --
-def _addr(x):
-    """Address of a grid argument (torch tensor, numpy array, int or None)."""
+def _buffer_check(is_float, itemsize, n, esize, count):
+    if esize is not None and (not is_float or itemsize != esize):
+        raise TypeError(f"grid of {itemsize}-byte {'floats' if is_float else 'non-floats'}: this call takes "
+                        f"{esize}-byte floats")
+    if count is not None and n < count:
+        raise ValueError(f"grid holds {n} elements, the extents need {count}")
+
+
+def _addr(x, esize=None, count=None):
+    """Address of a grid argument (torch tensor, numpy array, int or None).
+    Arrays and tensors must be contiguous, hold floats of `esize` bytes and at
+    least `count` elements, so that the kernels never run past them; a raw
+    address (int) is the caller's to vouch for."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -194,12 +205,22 @@ def _addr(x):
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
             raise ValueError("grid arrays must be C-contiguous (Fortran column-major u(i,j,k))")
+        _buffer_check(x.dtype.kind == "f", x.itemsize, x.size, esize, count)
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("grid tensors must be contiguous (Fortran column-major u(i,j,k))")
+        _buffer_check(x.is_floating_point(), x.element_size(), x.numel(), esize, count)
         return x.data_ptr()
     raise TypeError(f"unsupported grid argument {type(x)}")
+
+
+def _n3(nx, ny, nz, r):
+    return (nx + 2 * r) * (ny + 2 * r) * (nz + 2 * r)
+
+
+def _n2(nx, ny, r):
+    return (nx + 2 * r) * (ny + 2 * r)
 
 
 def _stream(stream, *grids):
@@ -247,28 +268,28 @@ def _check(rc):
 def stencil_sweep_f64(in_, out, coeffs, radius, iters, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(in_, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_sweep_f64(_addr(in_), _addr(out), nx, ny, nz, cp, radius, iters,
+    return _check(_lib.stencil_sweep_f64(_addr(in_, 8, _n3(nx, ny, nz, radius)), _addr(out, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, iters,
                                          _stream(stream, in_, out)))
 
 
 def stencil_sweep_f32(in_, out, coeffs, radius, iters, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(in_, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_sweep_f32(_addr(in_), _addr(out), nx, ny, nz, cp, radius, iters,
+    return _check(_lib.stencil_sweep_f32(_addr(in_, 4, _n3(nx, ny, nz, radius)), _addr(out, 4, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, iters,
                                          _stream(stream, in_, out)))
 
 
 def stencil_apply_f64(u, out, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_apply_f64(_addr(u), _addr(b), _addr(out), nx, ny, nz, cp, radius,
+    return _check(_lib.stencil_apply_f64(_addr(u, 8, _n3(nx, ny, nz, radius)), _addr(b, 8, _n3(nx, ny, nz, radius)), _addr(out, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius,
                                          _stream(stream, u, out, b)))
 
 
 def stencil_apply_f32(u, out, coeffs, radius, b=None, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_apply_f32(_addr(u), _addr(b), _addr(out), nx, ny, nz, cp, radius,
+    return _check(_lib.stencil_apply_f32(_addr(u, 4, _n3(nx, ny, nz, radius)), _addr(b, 4, _n3(nx, ny, nz, radius)), _addr(out, 4, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius,
                                          _stream(stream, u, out, b)))
 
 
@@ -276,7 +297,7 @@ def residual_norm_f64(u, coeffs, radius, b=None, nx=None, ny=None, nz=None, stre
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
     out = ctypes.c_double(0.0)
-    _check(_lib.residual_norm_f64(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
+    _check(_lib.residual_norm_f64(_addr(u, 8, _n3(nx, ny, nz, radius)), _addr(b, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, ctypes.byref(out),
                                   _stream(stream, u, b)))
     return out.value
 
@@ -285,7 +306,7 @@ def residual_norm_f32(u, coeffs, radius, b=None, nx=None, ny=None, nz=None, stre
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
     out = ctypes.c_double(0.0)
-    _check(_lib.residual_norm_f32(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
+    _check(_lib.residual_norm_f32(_addr(u, 4, _n3(nx, ny, nz, radius)), _addr(b, 4, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, ctypes.byref(out),
                                   _stream(stream, u, b)))
     return out.value
 
@@ -295,7 +316,7 @@ def residual_norm_f64_noalloc(u, coeffs, radius, b=None, nx=None, ny=None, nz=No
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
     out = ctypes.c_double(0.0)
-    _check(_lib.residual_norm_f64_noalloc(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(out),
+    _check(_lib.residual_norm_f64_noalloc(_addr(u, 8, _n3(nx, ny, nz, radius)), _addr(b, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, ctypes.byref(out),
                                           _stream(stream, u, b)))
     return out.value
 
@@ -306,39 +327,42 @@ def _numel(a, n):
     return int(a.numel()) if hasattr(a, "numel") else int(a.size)
 
 
-def _advect(fn, u, v, w, s, c, q, nx, ny, nz, stream):
+def _advect(fn, esize, u, v, w, s, c, q, nx, ny, nz, stream):
     nx, ny, nz = _extents(u, 1, nx, ny, nz)
+    n = _n3(nx, ny, nz, 1)
     cp, _keep = _coeffs(c)
-    outs = (_vp * len(s))(*[_addr(x) for x in s])
+    outs = (_vp * len(s))(*[_addr(x, esize, n) for x in s])
     if q is None:
         qs, nq = None, 3
     else:
-        qs = (_vp * len(q))(*[_addr(x) for x in q])
+        qs = (_vp * len(q))(*[_addr(x, esize, n) for x in q])
         nq = len(q)
-    return _check(fn(_addr(u), _addr(v), _addr(w), qs, nq, outs, nx, ny, nz, cp, _stream(stream, u, v, w)))
+    return _check(fn(_addr(u, esize, n), _addr(v, esize, n), _addr(w, esize, n), qs, nq, outs, nx, ny, nz, cp, _stream(stream, u, v, w)))
 
 
 def advect_f64(u, v, w, s, c, q=None, nx=None, ny=None, nz=None, stream=None):
     """Tendencies s[m] of fields q[m] under the velocity (u, v, w) (flux-form
     centred advection); q=None: the velocity components advect themselves."""
-    return _advect(_lib.advect_f64, u, v, w, s, c, q, nx, ny, nz, stream)
+    return _advect(_lib.advect_f64, 8, u, v, w, s, c, q, nx, ny, nz, stream)
 
 
 def advect_f32(u, v, w, s, c, q=None, nx=None, ny=None, nz=None, stream=None):
-    return _advect(_lib.advect_f32, u, v, w, s, c, q, nx, ny, nz, stream)
+    return _advect(_lib.advect_f32, 4, u, v, w, s, c, q, nx, ny, nz, stream)
 
 
 def reduce_sum_f64(x, n=None, stream=None) -> float:
     """Sum of the n contiguous doubles of x (the sum intrinsic)."""
     out = ctypes.c_double(0.0)
-    _check(_lib.reduce_sum_f64(_addr(x), _numel(x, n), ctypes.byref(out), _stream(stream, x)))
+    n = _numel(x, n)
+    _check(_lib.reduce_sum_f64(_addr(x, 8, n), n, ctypes.byref(out), _stream(stream, x)))
     return out.value
 
 
 def dot_f64(x, y, n=None, stream=None) -> float:
     """Dot product of two contiguous double vectors (the dotproduct intrinsic)."""
     out = ctypes.c_double(0.0)
-    _check(_lib.dot_f64(_addr(x), _addr(y), _numel(x, n), ctypes.byref(out), _stream(stream, x, y)))
+    n = _numel(x, n)
+    _check(_lib.dot_f64(_addr(x, 8, n), _addr(y, 8, n), n, ctypes.byref(out), _stream(stream, x, y)))
     return out.value
 
 
@@ -346,14 +370,14 @@ def stencil_sweep2d_f64(in_, out, coeffs, radius, iters, nx=None, ny=None, strea
     """`iters` 2-D sweeps of a padded (ny+2r, nx+2r) grid (synchronising)."""
     nx, ny = _extents2d(in_, radius, nx, ny)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_sweep2d_f64(_addr(in_), _addr(out), nx, ny, cp, radius, iters,
+    return _check(_lib.stencil_sweep2d_f64(_addr(in_, 8, _n2(nx, ny, radius)), _addr(out, 8, _n2(nx, ny, radius)), nx, ny, cp, radius, iters,
                                            _stream(stream, in_, out)))
 
 
 def stencil_sweep2d_f32(in_, out, coeffs, radius, iters, nx=None, ny=None, stream=None):
     nx, ny = _extents2d(in_, radius, nx, ny)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_sweep2d_f32(_addr(in_), _addr(out), nx, ny, cp, radius, iters,
+    return _check(_lib.stencil_sweep2d_f32(_addr(in_, 4, _n2(nx, ny, radius)), _addr(out, 4, _n2(nx, ny, radius)), nx, ny, cp, radius, iters,
                                            _stream(stream, in_, out)))
 
 
@@ -361,7 +385,7 @@ def residual_norm2d_f64(u, coeffs, radius, b=None, nx=None, ny=None, stream=None
     nx, ny = _extents2d(u, radius, nx, ny)
     cp, _keep = _coeffs(coeffs)
     out = ctypes.c_double(0.0)
-    _check(_lib.residual_norm2d_f64(_addr(u), _addr(b), nx, ny, cp, radius, ctypes.byref(out),
+    _check(_lib.residual_norm2d_f64(_addr(u, 8, _n2(nx, ny, radius)), _addr(b, 8, _n2(nx, ny, radius)), nx, ny, cp, radius, ctypes.byref(out),
                                     _stream(stream, u, b)))
     return out.value
 
@@ -370,7 +394,7 @@ def residual_norm2d_f32(u, coeffs, radius, b=None, nx=None, ny=None, stream=None
     nx, ny = _extents2d(u, radius, nx, ny)
     cp, _keep = _coeffs(coeffs)
     out = ctypes.c_double(0.0)
-    _check(_lib.residual_norm2d_f32(_addr(u), _addr(b), nx, ny, cp, radius, ctypes.byref(out),
+    _check(_lib.residual_norm2d_f32(_addr(u, 4, _n2(nx, ny, radius)), _addr(b, 4, _n2(nx, ny, radius)), nx, ny, cp, radius, ctypes.byref(out),
                                     _stream(stream, u, b)))
     return out.value
 
@@ -381,7 +405,7 @@ def jacobi_solve_f64(rhs, u, coeffs, radius, tol, max_iters, check_every=50, nx=
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
     info = SolveInfo()
-    rc = _check(_lib.jacobi_solve_f64(_addr(rhs), _addr(u), nx, ny, nz, cp, radius, tol, max_iters,
+    rc = _check(_lib.jacobi_solve_f64(_addr(rhs, 8, _n3(nx, ny, nz, radius)), _addr(u, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, tol, max_iters,
                                       check_every, ctypes.byref(info), _stream(stream, u, rhs)))
     return rc, info.as_dict()
 
@@ -392,7 +416,7 @@ def jacobi_solve_refined_f64(rhs, u, coeffs, radius, tol, inner_sweeps, inner_to
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     cp, _keep = _coeffs(coeffs)
     info = SolveInfo()
-    rc = _check(_lib.jacobi_solve_refined_f64(_addr(rhs), _addr(u), nx, ny, nz, cp, radius, tol, inner_sweeps,
+    rc = _check(_lib.jacobi_solve_refined_f64(_addr(rhs, 8, _n3(nx, ny, nz, radius)), _addr(u, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, cp, radius, tol, inner_sweeps,
                                               inner_tol, check_every, max_outer, ctypes.byref(info),
                                               _stream(stream, u, rhs)))
     return rc, info.as_dict()
@@ -404,8 +428,8 @@ def _problems(us, rhss, radius):
     for i, (u, b) in enumerate(zip(us, rhss)):
         nx, ny, nz = _extents(u, radius, None, None, None)
         arr[i].nx, arr[i].ny, arr[i].nz = nx, ny, nz
-        arr[i].rhs = _addr(b)
-        arr[i].u = _addr(u)
+        arr[i].rhs = _addr(b, 8, _n3(nx, ny, nz, radius))
+        arr[i].u = _addr(u, 8, _n3(nx, ny, nz, radius))
     return arr, n
 
 
@@ -432,21 +456,21 @@ def jacobi_solve_batched_refined(us, rhss, coeffs, radius, tol, inner_sweeps, in
 def varcoef_apply_f64(u, a, out, w, radius, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     wp, _keep = _coeffs(w)
-    return _check(_lib.varcoef_apply_f64(_addr(u), _addr(a), _addr(out), nx, ny, nz, wp, radius,
+    return _check(_lib.varcoef_apply_f64(_addr(u, 8, _n3(nx, ny, nz, radius)), _addr(a, 8, _n3(nx, ny, nz, radius)), _addr(out, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, wp, radius,
                                          _stream(stream, u, a, out)))
 
 
 def varcoef_sweep_f64(in_, out, a, f, w, radius, iters, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(in_, radius, nx, ny, nz)
     wp, _keep = _coeffs(w)
-    return _check(_lib.varcoef_sweep_f64(_addr(in_), _addr(out), _addr(a), _addr(f), nx, ny, nz, wp, radius,
+    return _check(_lib.varcoef_sweep_f64(_addr(in_, 8, _n3(nx, ny, nz, radius)), _addr(out, 8, _n3(nx, ny, nz, radius)), _addr(a, 8, _n3(nx, ny, nz, radius)), _addr(f, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, wp, radius,
                                          iters, _stream(stream, in_, out, a, f)))
 
 
 def varcoef_sweep_f32(in_, out, a, f, w, radius, iters, nx=None, ny=None, nz=None, stream=None):
     nx, ny, nz = _extents(in_, radius, nx, ny, nz)
     wp, _keep = _coeffs(w)
-    return _check(_lib.varcoef_sweep_f32(_addr(in_), _addr(out), _addr(a), _addr(f), nx, ny, nz, wp, radius,
+    return _check(_lib.varcoef_sweep_f32(_addr(in_, 4, _n3(nx, ny, nz, radius)), _addr(out, 4, _n3(nx, ny, nz, radius)), _addr(a, 4, _n3(nx, ny, nz, radius)), _addr(f, 4, _n3(nx, ny, nz, radius)), nx, ny, nz, wp, radius,
                                          iters, _stream(stream, in_, out, a, f)))
 
 
@@ -454,7 +478,7 @@ def varcoef_residual_norm_f64(u, a, f, w, radius, nx=None, ny=None, nz=None, str
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     wp, _keep = _coeffs(w)
     out = ctypes.c_double(0.0)
-    _check(_lib.varcoef_residual_norm_f64(_addr(u), _addr(a), _addr(f), nx, ny, nz, wp, radius,
+    _check(_lib.varcoef_residual_norm_f64(_addr(u, 8, _n3(nx, ny, nz, radius)), _addr(a, 8, _n3(nx, ny, nz, radius)), _addr(f, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, wp, radius,
                                           ctypes.byref(out), _stream(stream, u, a, f)))
     return out.value
 
@@ -464,7 +488,7 @@ def jacobi_solve_varcoef_f64(a, f, u, w, radius, tol, max_iters, check_every=50,
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     wp, _keep = _coeffs(w)
     info = SolveInfo()
-    rc = _check(_lib.jacobi_solve_varcoef_f64(_addr(a), _addr(f), _addr(u), nx, ny, nz, wp, radius, tol,
+    rc = _check(_lib.jacobi_solve_varcoef_f64(_addr(a, 8, _n3(nx, ny, nz, radius)), _addr(f, 8, _n3(nx, ny, nz, radius)), _addr(u, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, wp, radius, tol,
                                               max_iters, check_every, ctypes.byref(info),
                                               _stream(stream, u, a, f)))
     return rc, info.as_dict()
@@ -475,7 +499,7 @@ def jacobi_solve_varcoef_refined(a, f, u, w, radius, tol, inner_sweeps, max_oute
     nx, ny, nz = _extents(u, radius, nx, ny, nz)
     wp, _keep = _coeffs(w)
     info = SolveInfo()
-    rc = _check(_lib.jacobi_solve_varcoef_refined(_addr(a), _addr(f), _addr(u), nx, ny, nz, wp, radius, tol,
+    rc = _check(_lib.jacobi_solve_varcoef_refined(_addr(a, 8, _n3(nx, ny, nz, radius)), _addr(f, 8, _n3(nx, ny, nz, radius)), _addr(u, 8, _n3(nx, ny, nz, radius)), nx, ny, nz, wp, radius, tol,
                                                   inner_sweeps, max_outer, ctypes.byref(info),
                                                   _stream(stream, u, a, f)))
     return rc, info.as_dict()
@@ -562,8 +586,14 @@ class Server:
 
     def submit(self, rhs: np.ndarray, u0: np.ndarray | None = None) -> int:
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        if rhs.ndim != 3:
+            raise ValueError("rhs must be a 3D grid")
         nz, ny, nx = (s - 2 * self.radius for s in rhs.shape)
-        req = Request(nx, ny, nz, rhs.ctypes.data, None if u0 is None else np.ascontiguousarray(u0).ctypes.data)
+        # converted copies stay referenced until the call has copied them
+        u0c = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+        if u0c is not None and u0c.shape != rhs.shape:
+            raise ValueError(f"u0 of shape {u0c.shape}, rhs of shape {rhs.shape}")
+        req = Request(nx, ny, nz, rhs.ctypes.data, None if u0c is None else u0c.ctypes.data)
         t = ctypes.c_uint64(0)
         _check(_lib.stn_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
         return t.value

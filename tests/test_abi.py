@@ -392,3 +392,42 @@ def test_tune_cache_device_names_that_look_like_fields(lib, empty_cache, tmp_pat
         assert e is not None, dev
         assert (e["nx"], e["ny"], e["nz"], e["variant"], e["chunks"], e["depth"], e["glups"]) == (
             100 + k, 200 + k, 300 + k, 1, 7 + k, 2, 1.25 * k)
+
+
+def test_binding_refuses_grids_the_kernels_would_overrun(lib):
+    """The binding checks every array and tensor it passes: floats of the
+    call's element size, contiguous, and at least as many elements as the
+    extents need (explicit extents included), before the library sees it.
+    These raise without reaching the library, so they run on the CPU."""
+    import numpy as np
+    import torch
+    u64 = np.zeros((6, 7, 8))
+    u32 = np.zeros((6, 7, 8), dtype=np.float32)
+    c = (0.0, 1.0 / 6.0)
+    with pytest.raises(TypeError, match="4-byte"):
+        lib.stencil_sweep_f32(u64, u64.copy(), c, 1, 1)
+    with pytest.raises(TypeError, match="8-byte"):
+        lib.stencil_sweep_f64(u32, u32.copy(), c, 1, 1)
+    with pytest.raises(TypeError):
+        lib.stencil_sweep_f64(np.zeros((6, 7, 8), dtype=np.int64), u64, c, 1, 1)
+    with pytest.raises(ValueError, match="holds 336 elements"):
+        lib.stencil_sweep_f64(u64, u64.copy(), c, 1, 1, nx=7, ny=5, nz=4)  # needs 9 x 7 x 6 = 378
+    with pytest.raises(ValueError, match="contiguous"):
+        lib.stencil_sweep_f64(np.zeros((8, 7, 6)).transpose(2, 1, 0), u64, c, 1, 1)
+    t = torch.zeros(1, 1, 8, dtype=torch.float64).expand(6, 7, 8)  # stride-0 view of 8 doubles
+    with pytest.raises(ValueError, match="contiguous"):
+        lib.stencil_sweep_f64(t, u64, c, 1, 1)
+    with pytest.raises(TypeError):
+        lib.dot_f64(np.zeros(16), np.zeros(16, dtype=np.float32))
+    with pytest.raises(ValueError):
+        lib.reduce_sum_f64(np.zeros(16), n=17)
+    with pytest.raises(ValueError):
+        lib.stencil_sweep2d_f64(np.zeros((5, 6)), np.zeros((5, 6)), (0.0, 0.25), 1, 1, nx=4, ny=4)
+    with pytest.raises(TypeError):
+        lib.advect_f64(u64, u64, u32, [u64, u64, u64], (0.1, 0.1, 0.1))
+    with pytest.raises(ValueError):
+        lib.jacobi_solve_batched_f64([np.zeros((6, 6, 6))], [np.zeros((6, 6, 5))], c, 1, 1e-8, 10)
+    # a grid of the right kind gets past the binding to the library (which
+    # has no GPU here: it reports the failed staging, not a binding error)
+    with pytest.raises(lib.StencilError):
+        lib.stencil_sweep_f64(u64, u64.copy(), c, 1, 2)
