@@ -57,13 +57,18 @@ def _check(rc):
     return rc
 
 
-def _addr(x):
+def _addr(x, shape=None):
+    """Address of a host grid: a C-contiguous float64 array, of `shape` when
+    given (every grid of a call has the shape of its first), or a raw address
+    the caller vouches for."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
     if not (isinstance(x, np.ndarray) and x.flags.c_contiguous and x.dtype == np.float64):
         raise TypeError("host grids are C-contiguous float64 numpy arrays")
+    if shape is not None and x.shape != tuple(shape):
+        raise ValueError(f"grid of shape {x.shape}, the call's grids are {tuple(shape)}")
     return x.ctypes.data
 
 
@@ -79,14 +84,14 @@ def threads() -> int:
 def stencil_host_sweep_f64(in_, out, coeffs, radius, iters, nthreads=0):
     nz, ny, nx = (d - 2 * radius for d in in_.shape)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_host_sweep_f64(_addr(in_), _addr(out), nx, ny, nz, cp, radius, iters, nthreads))
+    return _check(_lib.stencil_host_sweep_f64(_addr(in_), _addr(out, in_.shape), nx, ny, nz, cp, radius, iters, nthreads))
 
 
 def stencil_host_residual_norm_f64(u, coeffs, radius, b=None, nthreads=0) -> float:
     nz, ny, nx = (d - 2 * radius for d in u.shape)
     cp, _keep = _coeffs(coeffs)
     v = ctypes.c_double(0.0)
-    _check(_lib.stencil_host_residual_norm_f64(_addr(u), _addr(b), nx, ny, nz, cp, radius, ctypes.byref(v),
+    _check(_lib.stencil_host_residual_norm_f64(_addr(u), _addr(b, u.shape), nx, ny, nz, cp, radius, ctypes.byref(v),
                                                nthreads))
     return v.value
 
@@ -94,14 +99,14 @@ def stencil_host_residual_norm_f64(u, coeffs, radius, b=None, nthreads=0) -> flo
 def stencil_host_sweep2d_f64(in_, out, coeffs, radius, iters, nthreads=0):
     ny, nx = (d - 2 * radius for d in in_.shape)
     cp, _keep = _coeffs(coeffs)
-    return _check(_lib.stencil_host_sweep2d_f64(_addr(in_), _addr(out), nx, ny, cp, radius, iters, nthreads))
+    return _check(_lib.stencil_host_sweep2d_f64(_addr(in_), _addr(out, in_.shape), nx, ny, cp, radius, iters, nthreads))
 
 
 def stencil_host_residual_norm2d_f64(u, coeffs, radius, b=None, nthreads=0) -> float:
     ny, nx = (d - 2 * radius for d in u.shape)
     cp, _keep = _coeffs(coeffs)
     v = ctypes.c_double(0.0)
-    _check(_lib.stencil_host_residual_norm2d_f64(_addr(u), _addr(b), nx, ny, cp, radius, ctypes.byref(v),
+    _check(_lib.stencil_host_residual_norm2d_f64(_addr(u), _addr(b, u.shape), nx, ny, cp, radius, ctypes.byref(v),
                                                  nthreads))
     return v.value
 
@@ -111,7 +116,7 @@ def stencil_host_advect_f64(u, v, w, s, c, q=None, nthreads=0):
     list s; halo-1 grids of shape (nz+2, ny+2, nx+2)."""
     nz, ny, nx = (d - 2 for d in u.shape)
     cp, _keep = _coeffs(c)
-    qa = None if q is None else (_vp * len(q))(*[_addr(x) for x in q])
-    sa = (_vp * len(s))(*[_addr(x) for x in s])
-    return _check(_lib.stencil_host_advect_f64(_addr(u), _addr(v), _addr(w), qa, 0 if q is None else len(q), sa,
+    qa = None if q is None else (_vp * len(q))(*[_addr(x, u.shape) for x in q])
+    sa = (_vp * len(s))(*[_addr(x, u.shape) for x in s])
+    return _check(_lib.stencil_host_advect_f64(_addr(u), _addr(v, u.shape), _addr(w, u.shape), qa, 0 if q is None else len(q), sa,
                                                nx, ny, nz, cp, nthreads))

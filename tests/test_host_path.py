@@ -181,3 +181,21 @@ def test_advect_rejects_bad_arguments(host):
         host.stencil_host_advect_f64(u, v, w, s, (0.25, float("nan"), 0.25))
     so = host.lib()
     assert so.stencil_host_advect_f64(None, None, None, None, 0, None, 4, 3, 2, None, 0) == -1
+
+
+def test_binding_refuses_mismatched_grids(host):
+    """Every grid of a call must have the first grid's shape (the extents come
+    from it): a smaller output, source term or field is refused before the
+    library could run past it."""
+    u = np.zeros((6, 7, 8))
+    c = (0.0, 1.0 / 6.0)
+    with pytest.raises(ValueError):
+        host.stencil_host_sweep_f64(u, np.zeros((6, 7, 7)), c, 1, 2)
+    with pytest.raises(ValueError):
+        host.stencil_host_residual_norm_f64(u, c, 1, b=np.zeros((5, 7, 8)))
+    with pytest.raises(ValueError):
+        host.stencil_host_sweep2d_f64(np.zeros((6, 7)), np.zeros((7, 6)), (0.0, 0.25), 1, 1)
+    with pytest.raises(ValueError):
+        host.stencil_host_advect_f64(u, u.copy(), np.zeros((6, 7, 9)), [np.zeros_like(u)] * 3, (0.1, 0.1, 0.1))
+    with pytest.raises(TypeError):
+        host.stencil_host_sweep_f64(u, np.zeros((6, 7, 8), dtype=np.float32), c, 1, 2)
