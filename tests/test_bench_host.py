@@ -93,6 +93,9 @@ def test_all_cores_baseline_is_the_oracles_sample_bitwise():
     assert d["bitwise_oracle"] is True and d["norm_rel_diff_oracle"] <= 40 * 33 * 27 * 2.0 ** -53
     assert d["cores"] >= 1 and d["value"] > 0 and d["unit"] == "GLUP/s"
     assert bench.cpu_all_cores(dict(wl, dtype="f32"), 5) is None
+    # both go into the bench's JSON line as they are
+    line = json.loads(json.dumps({"cpu_baseline": base, "cpu_all_cores": d}))
+    assert line["cpu_all_cores"]["bitwise_oracle"] is True
 
 
 import pytest  # noqa: E402
