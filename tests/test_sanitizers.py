@@ -19,7 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SAN = ["-O1", "-g", "-fsanitize=address,undefined", "-fno-omit-frame-pointer", "-fno-sanitize-recover=undefined",
        "-ffp-contract=off", "-fPIC", "-shared"]
 TESTS = ["test_oracle.py", "test_oracle_2d.py", "test_oracle_advect.py", "test_oracle_reduce.py",
-         "test_host_path.py"]
+         "test_host_path.py", "test_properties.py"]
 
 
 def runtime(name):
