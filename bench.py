@@ -98,6 +98,20 @@ FP64_OPS_PER_CLK_SM = 2.0
 N_SM = 152
 
 
+def fp64_pipe(ops, kern_ms, peaks, what):
+    """The FP64-pipe fraction of a kernel whose roofline is HBM but whose double
+    operations cap it first: ops / kernel time against 2 FP64 instructions per
+    clock per SM (measured with a throughput probe) x 152 SMs x the maximum SM
+    clock."""
+    sm_clock = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = FP64_OPS_PER_CLK_SM * N_SM * sm_clock * 1e6 / 1e12  # Tops/s
+    achieved = ops / (kern_ms * 1e-3) / 1e12
+    return {"fp64_pipe_achieved_tops": achieved, "fp64_pipe_peak_tops": peak,
+            "fp64_pipe_frac": achieved / peak,
+            "fp64_pipe_peak_kind": f"derived: {FP64_OPS_PER_CLK_SM:g} FP64 ops/clk/SM (measured probe) x "
+                                   f"{N_SM} SMs x {sm_clock:g} MHz; {what}"}
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while running."""
 
@@ -326,16 +340,13 @@ def run_cuda(args, wl):
     hbm_gbs = bytes_alg / (kern_ms * 1e-3) / 1e9
     hbm_peak = float(peaks["hbm_gbs"])
     if f64:
-        # the double sweep is bound by the FP64 pipe: 6 double ops per update
-        ops = 6.0 * lups_kernel
-        sm_clock = float(peaks.get("sm_max_mhz", 2070.0))
-        fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * sm_clock * 1e6 / 1e12  # Tops/s
-        achieved = ops / (kern_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                    "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
-                    "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
-                    "hbm_peak_kind": peak_kind, "kernel_ms": kern_ms, "kernel_ms_in_step": launch_ms_in_step}
+        # The roofline of this workload is HBM (16 B per update, compulsory);
+        # the FP64 pipe caps the double sweep first (6 double ops per update
+        # at 2 per clock per SM), so its fraction is given beside it.
+        roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                    "peak_kind": peak_kind, "kernel_ms": kern_ms, "kernel_ms_in_step": launch_ms_in_step}
+        roofline.update(fp64_pipe(6.0 * lups_kernel, kern_ms, peaks, "6 double ops per update"))
     else:
         roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "bytes per launch",
@@ -503,7 +514,11 @@ def run_jacobi2d(args):
         # DRAM bytes of one resident launch (ncu on this grid, the bulk-copy build):
         # the grid read once (8.44 MB) and 6.7 KB written before the kernel ends
         # (the rest leaves L2 later)
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+        # The grid stays in shared memory for the whole launch, so HBM is touched
+        # once per launch (16 B per point) and bounds nothing: the bound is the
+        # FP64 pipe (4 double ops per update)
+        "roofline": {"bound": "alu", "alu": "FP64 pipe (grid resident in shared memory; no HBM traffic per sweep)",
+                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak, "traffic": TRAFFIC_J2D_LAUNCH, "traffic_unit": "bytes per launch",
                      "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
                      "kernel": "j2d_resident_kernel<double,1>", "kernel_ms": kern_ms,
@@ -724,17 +739,15 @@ def run_intrinsic(args, kind):
     hbm_peak = float(peaks["hbm_gbs"])
     note = "timed through the synchronous call: kernel + fixed-order finalize + 8-byte read"
     if kind == "sum":
-        # one double add per element: bound by the FP64 pipe, not HBM
-        fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-        achieved = n / sec / 1e12
-        # DRAM bytes of one launch: ncu on a 2^27-element case read 8.02 B per
-        # element (no re-reads), scaled by the elements
-        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": TRAFFIC_SUM_PER_ELEMENT * n, "traffic_unit": "bytes per launch",
-                    "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
-                    "hbm_achieved_gbs": nbytes / sec / 1e9, "hbm_peak_gbs": hbm_peak,
-                    "hbm_frac": nbytes / sec / 1e9 / hbm_peak, "hbm_peak_kind": peak_kind,
+        # HBM roofline (8 B per element); one double add per element makes the
+        # FP64 pipe the first cap, given beside it.  DRAM bytes of one launch:
+        # ncu on a 2^27-element case read 8.02 B per element (no re-reads),
+        # scaled by the elements
+        roofline = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": nbytes / sec / 1e9 / hbm_peak, "traffic": TRAFFIC_SUM_PER_ELEMENT * n,
+                    "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
                     "kernel": "sum_kernel", "kernel_ms": ms / args.steps, "note": note}
+        roofline.update(fp64_pipe(float(n), ms / args.steps, peaks, "one double add per element"))
     else:
         # ncu on the full 2^27-element dot: 2.1476 GB read, 2.9 MB written
         roofline = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -899,9 +912,18 @@ def run_advect(args):
         torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / 2
     peaks, peak_kind = load_peaks()
-    fp64_peak = FP64_OPS_PER_CLK_SM * N_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     hbm_peak = float(peaks["hbm_gbs"])
-    achieved = cells * ADVECT_FP64_OPS / sec / 1e12
+    hbm_gbs = cells * ADVECT_BYTES / sec / 1e9
+    # HBM roofline (3 fields in, 3 tendencies out); the FP64 pipe caps it
+    # first and its fraction is given beside it.  ncu on a 512 x 512 x 256
+    # case: 3.308 GB for 67.1 M cells = 49.3 B per cell (5 % halo re-reads),
+    # scaled by the cells of this launch
+    roofline = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+                "traffic": TRAFFIC_ADVECT_PER_CELL * cells, "traffic_unit": "bytes per launch",
+                "peak_kind": peak_kind, "bytes_per_cell": ADVECT_BYTES, "kernel": "advect_kernel<double,3,self>",
+                "kernel_ms": ms / args.steps}
+    roofline.update(fp64_pipe(cells * ADVECT_FP64_OPS, ms / args.steps, peaks,
+                              f"{ADVECT_FP64_OPS} double ops per cell"))
     out = {
         "metric": "Gcells/s (advection stand-in, pw-like, 2048 x 1024 x 1024 FP64)",
         "value": value, "unit": "Gcells/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -916,15 +938,7 @@ def run_advect(args):
                 "h2d_bytes_per_step": 3 * hv[0].numel() * 8, "d2h_bytes_per_step": 3 * hv[0].numel() * 8,
                 "grid": [ex, ey, ez]},
         "gpu_launches": args.steps,
-        # ncu on a 512 x 512 x 256 case: 3.308 GB for 67.1 M cells = 49.3 B per
-        # cell (5 % halo re-reads), scaled by the cells of this launch
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": TRAFFIC_ADVECT_PER_CELL * cells, "traffic_unit": "bytes per launch",
-                     "peak_kind": "derived: 2 FP64 FMA-pipe ops/clk/SM (measured probe) x 152 SMs x max SM clock",
-                     "ops_per_cell": ADVECT_FP64_OPS, "hbm_achieved_gbs": cells * ADVECT_BYTES / sec / 1e9,
-                     "hbm_peak_gbs": hbm_peak, "hbm_frac": cells * ADVECT_BYTES / sec / 1e9 / hbm_peak,
-                     "hbm_peak_kind": peak_kind, "kernel": "advect_kernel<double,3,self>",
-                     "kernel_ms": ms / args.steps},
+        "roofline": roofline,
         "step_ms": step_stats(evs),
         "clocks": clk.summary(),
         "host": host_info(),

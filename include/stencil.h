@@ -362,7 +362,10 @@ int residual_norm_f32(const float* u, const float* b, int64_t nx, int64_t ny, in
  * order).  Grids whose launch plan needs more than 65536 partial sums (one
  * per 64 x 8 or 32 x 8 tile of the (i, j) plane once the plane has enough
  * tiles to fill the GPU: nx*ny above roughly 17 to 34 million, e.g.
- * 8192 x 8192) are rejected with STN_EINVAL before any GPU work.  The first call on a device looks up the array's device address
+ * 8192 x 8192) are rejected with STN_EINVAL before any GPU work.  The limit
+ * is checked against the very plan the call then launches and reduces (formed
+ * once per call), so a tuning knob or tuning-cache entry set meanwhile on
+ * another host thread cannot push a launch past the array.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) for that device; make that first call before any
  * stream capture.  Every call on a device shares the one array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be

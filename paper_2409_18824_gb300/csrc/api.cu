@@ -369,8 +369,10 @@ static int residual_impl(const T* u, const T* b, i64 nx, i64 ny, i64 nz, const d
   const i64 nb = star_blocks(g, sizeof(T), du, db, nullptr);
   Workspace* ws;
   if (int rc = get_workspace(s, nb, 0, &ws)) return rc;
-  if (int rc = launch_star<T>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s)) return rc;
-  if (int rc = launch_finalize(ws->partials, nb, ws->scalars, nullptr, 0.0, s)) return rc;
+  i64 nl = 0;  // the launch's own partial count (its plan, checked against the workspace)
+  if (int rc = launch_star<T>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s, ws->partials_cap, &nl))
+    return rc;
+  if (int rc = launch_finalize(ws->partials, nl, ws->scalars, nullptr, 0.0, s)) return rc;
   if (int rc = read_scalars(ws, 0, 2, s)) return rc;
   *norm_out = ws->host_scalars[1];
   return st.finish();
@@ -593,7 +595,7 @@ static int graph_groups(double* a, double* bgrid, const double* db, const Grid& 
     double* nxt = bgrid;
     for (i64 k = 0; k < group && rc == STN_OK; k++) {
       rc = launch_star<double>(cur, db, nxt, g, coeffs, k == group - 1 ? kSweepResidual : kSweep,
-                               ws->partials, cs);
+                               ws->partials, cs, ws->partials_cap);
       std::swap(cur, nxt);
     }
     if (rc == STN_OK) rc = launch_decide(ws->partials, nparts, ws->scalars, tol, group, max_full, h, cs);
@@ -641,7 +643,6 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
     return rc;
   double* tmp = (double*)ws->grid;
   const i64 nb_sweep = star_blocks(g, sizeof(double), du, db, tmp);
-  const i64 nb_res = star_blocks(g, sizeof(double), du, db, nullptr);
   if (int rc = launch_copy_halo<double>(du, tmp, g, s)) return rc;
   double bn = 0.0;
   if (int rc = rhs_norm<double>(ws, db, g, s, &bn)) return rc;
@@ -661,7 +662,8 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
   double* nxt = tmp;
   if (!conv && done < max_iters) {
     auto step = [&](i64, bool last) -> int {
-      int rc = launch_star<double>(cur, db, nxt, g, coeffs, last ? kSweepResidual : kSweep, ws->partials, s);
+      int rc = launch_star<double>(cur, db, nxt, g, coeffs, last ? kSweepResidual : kSweep, ws->partials, s,
+                                   ws->partials_cap);
       std::swap(cur, nxt);
       return rc;
     };
@@ -672,8 +674,10 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
   }
   if (max_iters == 0) {
     // no sweep: measure the residual of the initial guess only
-    if (int rc = launch_star<double>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s)) return rc;
-    if (int rc = launch_finalize(ws->partials, nb_res, ws->scalars, ws->scalars + 9, tol, s)) return rc;
+    i64 nl = 0;
+    if (int rc = launch_star<double>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s, ws->partials_cap, &nl))
+      return rc;
+    if (int rc = launch_finalize(ws->partials, nl, ws->scalars, ws->scalars + 9, tol, s)) return rc;
     if (int rc = read_scalars(ws, 0, 4, s)) return rc;
     res = ws->host_scalars[1];
     rel = ws->host_scalars[2];

@@ -141,9 +141,14 @@ LaunchPlan var_launch_plan(const Grid& g, size_t esize);
 LaunchPlan batch_unit_plan(i64 nx, i64 ny, i64 nz);
 // One launch: out = S u + b over the interior; in residual modes also the
 // per-block partial sums of rho^2 into `partials` (ZPlan::blocks() entries).
+// The plan is formed once per call.  In residual modes a plan needing more
+// than `max_partials` partials (when >= 0) is refused with STN_EINVAL before
+// anything launches, and `nparts` (when not NULL) receives the number of
+// partials the launch writes: the count to reduce.
 template <typename T>
 int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
-                SweepMode mode, double* partials, cudaStream_t s);
+                SweepMode mode, double* partials, cudaStream_t s, i64 max_partials = -1,
+                i64* nparts = nullptr);
 // Copies the halo cells of `src` into `dst` (same geometry).
 template <typename T>
 int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s);

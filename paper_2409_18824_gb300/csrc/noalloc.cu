@@ -79,8 +79,9 @@ static int noalloc_residual(const double* u, const double* b, i64 nx, i64 ny, i6
     return STN_EINVAL;
   }
   const Grid g{nx, ny, nz, radius};
-  const i64 nb = star_blocks(g, sizeof(double), u, b, nullptr);
-  if (nb > kNoAllocPartials) {
+  // A first look at the plan, to refuse oversize grids before any CUDA call;
+  // launch_star checks the plan it actually launches against the same limit.
+  if (star_blocks(g, sizeof(double), u, b, nullptr) > kNoAllocPartials) {
     set_error("invalid argument: grid needs more than 65536 partial sums, the size of the "
               "no-allocation scratch (use residual_norm_f64)");
     return STN_EINVAL;
@@ -99,7 +100,14 @@ static int noalloc_residual(const double* u, const double* b, i64 nx, i64 ny, i6
   double* partials = scratch;
   double* slots = scratch + kNoAllocPartials;
   cudaStream_t s = (cudaStream_t)stream;
-  if (int rc = launch_star<double>(u, b, nullptr, g, coeffs, kResidualOnly, partials, s)) return rc;
+  // The plan is formed once inside launch_star: the partial count it checks
+  // against the array, the grid it launches and the count `nb` reduced below
+  // are the same, whatever another host thread does to the tuning knobs or
+  // the tuning cache meanwhile.
+  i64 nb = 0;
+  if (int rc = launch_star<double>(u, b, nullptr, g, coeffs, kResidualOnly, partials, s,
+                                   kNoAllocPartials, &nb))
+    return rc;
   if (int rc = launch_finalize(partials, nb, slots, nullptr, 0.0, s)) return rc;
   STN_CUDA_TRY(cudaMemcpyAsync(norm_out, slots + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   STN_CUDA_TRY(cudaStreamSynchronize(s));

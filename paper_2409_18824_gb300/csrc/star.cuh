@@ -616,10 +616,8 @@ __global__ void copy_halo_kernel(const T* __restrict__ src, T* __restrict__ dst,
 
 template <typename T, int R, bool HAS_B, bool HAS_C0>
 int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
-                  SweepMode mode, double* partials, cudaStream_t s, int variant) {
-  const ZPlan p = plan_star(g, variant, sizeof(T));
-  variant = p.variant;  // the plan's own: a staged request whose ring does not fit runs the plane kernel
-  if (int rc = check_launch_grid(p.tiles_x, p.tiles_y, p.chunks)) return rc;
+                  SweepMode mode, double* partials, cudaStream_t s, const ZPlan& p) {
+  const int variant = p.variant;  // the plan's own: a staged request whose ring does not fit runs the plane kernel
   star_last().variant = variant;
   star_last().chunks = p.chunks;
   StarCoeffs<T, R> cf;
@@ -674,9 +672,19 @@ int launch_star_t(const T* u, const T* b, T* out, const Grid& g, const double* c
 
 template <typename T>
 int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coeffs,
-                SweepMode mode, double* partials, cudaStream_t s) {
+                SweepMode mode, double* partials, cudaStream_t s, i64 max_partials, i64* nparts) {
   const bool hb = b != nullptr, hc0 = coeffs[0] != 0.0;
-  const int v = star_variant(g, sizeof(T), u, b, out);
+  // One plan for the whole launch: the knobs and the tuning cache may change
+  // on another thread, so the partial count checked here, the grid launched
+  // and the count returned for the reduction all come from this one plan.
+  const ZPlan v = plan_star(g, star_variant(g, sizeof(T), u, b, out), sizeof(T));
+  if (int rc = check_launch_grid(v.tiles_x, v.tiles_y, v.chunks)) return rc;
+  if (mode != kSweep && max_partials >= 0 && v.blocks() > max_partials) {
+    set_error("invalid argument: the launch plan needs " + std::to_string(v.blocks()) +
+              " partial sums, more than the " + std::to_string(max_partials) + " slots given");
+    return STN_EINVAL;
+  }
+  if (nparts) *nparts = v.blocks();
   if (g.r == 1) {
     if (hb) return hc0 ? launch_star_t<T, 1, true, true>(u, b, out, g, coeffs, mode, partials, s, v)
                        : launch_star_t<T, 1, true, false>(u, b, out, g, coeffs, mode, partials, s, v);

@@ -7,7 +7,9 @@
 
 namespace stn {
 
-static int g_star_variant_override = -1;
+// Process-wide knobs, read by planners on any host thread: atomic, so a
+// concurrent set is seen whole (each launch forms its plan once).
+static std::atomic<int> g_star_variant_override{-1};
 
 int tune_set_star_variant(int v) {
   if (v < -1 || v > 3) return STN_EINVAL;
@@ -16,7 +18,7 @@ int tune_set_star_variant(int v) {
 }
 int tune_get_star_variant() { return g_star_variant_override; }
 
-static int g_temporal_depth = 0;
+static std::atomic<int> g_temporal_depth{0};
 int tune_set_temporal_depth(int d) {
   if (d < 0 || d > 4) return STN_EINVAL;
   g_temporal_depth = d;
@@ -24,7 +26,7 @@ int tune_set_temporal_depth(int d) {
 }
 int tune_get_temporal_depth() { return g_temporal_depth; }
 
-static int g_star_chunks = 0;
+static std::atomic<int> g_star_chunks{0};
 int tune_set_star_chunks(int c) {
   if (c < 0 || c > 65535) return STN_EINVAL;
   g_star_chunks = c;
@@ -214,8 +216,8 @@ ZPlan plan_star(const Grid& g, int variant, size_t esize) {
   StarChoice tc;
   if (star_force().chunks > 0)
     chunks = star_force().chunks;
-  else if (g_star_chunks > 0)
-    chunks = g_star_chunks;
+  else if (const int kc = g_star_chunks.load(); kc > 0)
+    chunks = kc;
   else if (tune_cache_lookup(g, esize, &tc) && tc.variant == variant && tc.chunks > 0)
     chunks = tc.chunks;
   if (chunks > max_chunks) chunks = max_chunks;
@@ -236,8 +238,8 @@ int star_variant(const Grid& g, size_t esize, const void* a, const void* b, cons
   StarChoice tc;
   if (star_force().variant >= 0)
     v = star_force().variant;
-  else if (g_star_variant_override >= 0)
-    v = g_star_variant_override;
+  else if (const int ko = g_star_variant_override.load(); ko >= 0)
+    v = ko;
   else if (tune_cache_lookup(g, esize, &tc) && tc.variant >= 0)
     v = tc.variant;
   // the staged kernel needs a ring stage of at least one row and its halo

@@ -4,7 +4,7 @@
 namespace stn {
 
 template int launch_star<float>(const float*, const float*, float*, const Grid&, const double*, SweepMode,
-                             double*, cudaStream_t);
+                             double*, cudaStream_t, i64, i64*);
 template int launch_copy_halo<float>(const float*, float*, const Grid&, cudaStream_t);
 
 }  // namespace stn

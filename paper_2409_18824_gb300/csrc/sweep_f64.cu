@@ -4,7 +4,7 @@
 namespace stn {
 
 template int launch_star<double>(const double*, const double*, double*, const Grid&, const double*, SweepMode,
-                             double*, cudaStream_t);
+                             double*, cudaStream_t, i64, i64*);
 template int launch_copy_halo<double>(const double*, double*, const Grid&, cudaStream_t);
 
 }  // namespace stn
