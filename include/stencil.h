@@ -125,11 +125,17 @@ int stencil_release_workspace(void);
  *                   refined solver's inner sweeps) run as a CUDA graph whose
  *                   while node repeats 16 sweeps on the device; 0: one stream
  *                   launch per sweep.  Same kernels, same results.
- *   "var_variant":  variable-coefficient kernels: -1 automatic (default: the
+ *   "refined_engine": jacobi_solve_refined_f64: 1 (default) full-grid kernels
+ *                   per step; 0 a batch of one in the persistent scheduler.
+ *   "var_variant":  variable-coefficient kernels: -1 automatic (default: float
+ *                   radius-2 sweeps on grids whose padded rows are a multiple
+ *                   of 16 bytes, with u and a 16-byte and f and out 8-byte
+ *                   aligned, take the TMA-staged kernel; everything else the
  *                   register/shuffle column kernel that computes each face
  *                   coefficient once), 0 the shared-memory plane kernel, 1
- *                   column.  Bitwise the same results (face coefficients in
- *                   the normal floating-point range).
+ *                   column, 2 TMA-staged where it applies (column elsewhere).
+ *                   Bitwise the same results (face coefficients in the normal
+ *                   floating-point range).
  *   "sweep2d_resident": 2-D sweeps: -1 automatic (default: shared-memory
  *                   resident whenever the grid fits), 0 always through HBM,
  *                   1 resident whenever it fits.
@@ -405,9 +411,14 @@ int jacobi_solve_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64
  *                   last sweep changed e by <= inner_tol*||r32|| (inner_tol = 0:
  *                   never), or after inner_sweeps sweeps
  *   update(double): u = u + s * double(e)
- * up to max_outer outer steps.  Device grids only.  info->outer = outer
- * steps, info->iters = float sweeps, info->rel_res = last double relative
- * residual.  Synchronises.  Returns STN_OK or STN_NOT_CONVERGED.
+ * up to max_outer outer steps.  info->outer = outer steps, info->iters =
+ * float sweeps, info->rel_res = last double relative residual.  The steps
+ * run as full-grid kernels (the double sweep with its fused residual, the
+ * float sweeps of stencil_sweep_f32, small grids' inner loops as
+ * device-repeated CUDA graphs); knob "refined_engine" = 0 runs the request as
+ * a batch of one in the persistent scheduler instead (same arithmetic; with
+ * inner_tol > 0 the inner stopping sums may round differently).  Device or
+ * host grids.  Synchronises.  Returns STN_OK or STN_NOT_CONVERGED.
  */
 int jacobi_solve_refined_f64(const double* rhs, double* u, int64_t nx, int64_t ny, int64_t nz,
                              const double* coeffs, int radius, double tol, int64_t inner_sweeps,
@@ -531,7 +542,14 @@ int varcoef_apply_f64(const double* u, const double* a, double* out, int64_t nx,
 
 /* `iters` Jacobi sweeps for A u = f; in/out semantics as stencil_sweep_f64
  * (in's interior clobbered when iters > 1).  _f32 takes float a, f, grids;
- * weights rounded to float. */
+ * weights rounded to float.  Float sweeps of radius 2 whose padded rows are
+ * a multiple of 16 bytes (nx + 4 divisible by 4), with 16-byte-aligned in,
+ * out (both serve as u) and a and an 8-byte-aligned f, stage their tiles
+ * through shared memory by tensor-map copies (TMA); the results are the same
+ * bits as every other variant.  Their device-side waits are bounded: a wait
+ * that gave up (never expected) stops that sweep early and is reported as
+ * STN_ETIMEOUT by the next synchronising variable-coefficient call on the
+ * device (residual norm, solves). */
 int varcoef_sweep_f64(double* in, double* out, const double* a, const double* f, int64_t nx,
                       int64_t ny, int64_t nz, const double* w, int radius, int64_t iters,
                       void* stream);

@@ -567,16 +567,20 @@ int tune_get_solve_graph() { return g_solve_graph; }
 // device-side decision kernel and, for an odd group, a copy that brings the
 // iterate back to `a`.  Stops on convergence or when the next group would
 // pass max_full.  On return *it_out sweeps are done (a multiple of group) and
-// the iterate is in `a`.
-static int graph_groups(double* a, double* bgrid, const double* db, const Grid& g, const double* coeffs,
-                        Workspace* ws, i64 nparts, double tol, i64 group, i64 max_full,
-                        cudaStream_t s, i64* it_out, bool* conv_out) {
-  const size_t bytes = (size_t)g.count() * sizeof(double);
+// the iterate is in `a`.  The decision kernel writes its scalars at `dst`
+// (dst[9] holds the scale of the relative residual); `dst` lies in the
+// workspace's scalars.
+template <typename T>
+static int graph_groups(T* a, T* bgrid, const T* db, const Grid& g, const double* coeffs, Workspace* ws,
+                        double* dst, double tol, i64 group, i64 max_full, cudaStream_t s, i64* it_out,
+                        bool* conv_out) {
+  const size_t bytes = (size_t)g.count() * sizeof(T);
   cudaGraph_t graph = nullptr, body = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
   cudaError_t e;
   int rc = STN_OK;
+  const int first = (int)(dst - ws->scalars);
   do {
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) break;
     if ((e = cudaGraphCreate(&graph, 0))) break;
@@ -591,14 +595,15 @@ static int graph_groups(double* a, double* bgrid, const double* db, const Grid& 
     if ((e = cudaGraphAddNode(&wn, graph, nullptr, nullptr, 0, &cp))) break;
     body = cp.conditional.phGraph_out[0];
     if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
-    double* cur = a;
-    double* nxt = bgrid;
+    T* cur = a;
+    T* nxt = bgrid;
+    i64 nl = 0;  // partials the group's last (residual) sweep writes
     for (i64 k = 0; k < group && rc == STN_OK; k++) {
-      rc = launch_star<double>(cur, db, nxt, g, coeffs, k == group - 1 ? kSweepResidual : kSweep,
-                               ws->partials, cs, ws->partials_cap);
+      rc = launch_star<T>(cur, db, nxt, g, coeffs, k == group - 1 ? kSweepResidual : kSweep, ws->partials, cs,
+                          ws->partials_cap, &nl);
       std::swap(cur, nxt);
     }
-    if (rc == STN_OK) rc = launch_decide(ws->partials, nparts, ws->scalars, tol, group, max_full, h, cs);
+    if (rc == STN_OK) rc = launch_decide(ws->partials, nl, dst, tol, group, max_full, h, cs);
     if (rc == STN_OK && cur != a) e = cudaMemcpyAsync(a, cur, bytes, cudaMemcpyDeviceToDevice, cs);
     cudaGraph_t captured = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
@@ -606,11 +611,11 @@ static int graph_groups(double* a, double* bgrid, const double* db, const Grid& 
     if (e != cudaSuccess) break;
     if ((e = e2)) break;
     if ((e = cudaGraphInstantiate(&exec, graph, 0))) break;
-    if ((e = cudaMemsetAsync(ws->scalars + 5, 0, sizeof(double), s))) break;
+    if ((e = cudaMemsetAsync(dst + 5, 0, sizeof(double), s))) break;
     if ((e = cudaGraphLaunch(exec, s))) break;
-    if ((rc = read_scalars(ws, 0, 6, s))) break;
-    *it_out = (i64)ws->host_scalars[5];
-    *conv_out = ws->host_scalars[3] != 0.0;
+    if ((rc = read_scalars(ws, first, 6, s))) break;
+    *it_out = (i64)ws->host_scalars[first + 5];
+    *conv_out = ws->host_scalars[first + 3] != 0.0;
   } while (false);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -652,7 +657,8 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
   int status = STN_NOT_CONVERGED;
   const i64 max_full = (max_iters / check_every) * check_every;
   if (g_solve_graph && max_full >= check_every) {
-    if (int rc = graph_groups(du, tmp, db, g, coeffs, ws, nb_sweep, tol, check_every, max_full, s, &done, &conv))
+    if (int rc = graph_groups<double>(du, tmp, db, g, coeffs, ws, ws->scalars, tol, check_every, max_full, s, &done,
+                                      &conv))
       return rc;
     res = ws->host_scalars[1];
     rel = ws->host_scalars[2];
@@ -694,6 +700,157 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
     info->rhs_norm = bn;
     info->status = status;
   }
+  return status;
+}
+
+// ------------------------------------------ direct refinement (one problem) --
+// The constant-coefficient refinement of jacobi_solve_refined_f64 computed
+// with the full-grid kernels of the single-problem sweeps, step for step the
+// oracle's refinement:
+//   t = S u + b (double sweep with the fused sum of (t - u)^2), stop when
+//   ||t - u|| <= tol * ||b||;  s = max |t - u|;  r32 = float((t - u) / s);
+//   float sweeps e <- S e + r32 from e = 0 (coefficients rounded to float):
+//   inner_sweeps of them, or, with inner_tol > 0, groups of check_every until
+//   a group's last sweep changed e by <= inner_tol * ||r32||;  u += s * e.
+// Small grids run their inner loops as device-repeated CUDA graphs (the
+// decision on the device, one host wait per outer step).  Workspace scalars:
+// [0..3] outer norm, [4] s, [8..9] ||b||, [12] graph counter, [16..25] inner
+// decisions with [25] = ||r32||.
+static int g_refined_engine = 1;  // 1: direct full-grid kernels; 0: the scheduler, one problem
+int tune_set_refined_engine(int v) {
+  if (v < 0 || v > 1) return STN_EINVAL;
+  g_refined_engine = v;
+  return STN_OK;
+}
+int tune_get_refined_engine() { return g_refined_engine; }
+
+static int refined_direct(const double* db, double* du, const Grid& g, const double* coeffs, double tol,
+                          i64 inner_sweeps, double inner_tol, i64 check_every, i64 max_outer,
+                          stn_solve_info* info, cudaStream_t s) {
+  const i64 n = g.count();
+  const size_t b64 = (size_t)n * sizeof(double), b32 = (size_t)n * sizeof(float);
+  i64 cap = 2 * 152 * 16;  // interior reductions: one partial per block of at most 152 * 16
+  for (int v = 0; v < 4; v++) cap += plan_star(g, v, 8).blocks() + plan_star(g, v, 4).blocks();
+  Workspace* ws;
+  if (int rc = get_workspace(s, cap, b64, &ws)) return rc;
+  if (int rc = ensure_grid2(ws, 3 * b32)) return rc;
+  double* t = (double*)ws->grid;
+  float* r32 = (float*)ws->grid2;
+  float* e = r32 + n;
+  float* e2 = e + n;
+  // the correction's halo is zero (homogeneous Dirichlet): zero both buffers once
+  STN_CUDA_TRY(cudaMemsetAsync(e, 0, 2 * b32, s));
+  double bn = 0.0;
+  if (int rc = rhs_norm<double>(ws, db, g, s, &bn)) return rc;
+  i64 outer = 0, sweeps = 0;
+  double rel = INFINITY, res = INFINITY;
+  int status = STN_NOT_CONVERGED;
+  for (;;) {
+    i64 nl = 0, nm = 0;
+    if (int rc = launch_star<double>(du, db, t, g, coeffs, kSweepResidual, ws->partials, s, ws->partials_cap, &nl))
+      return rc;
+    if (int rc = launch_finalize(ws->partials, nl, ws->scalars, ws->scalars + 9, tol, s)) return rc;
+    if (int rc = launch_diff_max(t, du, g, ws->partials, &nm, s)) return rc;
+    if (int rc = launch_max_finalize(ws->partials, nm, ws->scalars + 4, s)) return rc;
+    if (int rc = read_scalars(ws, 0, 5, s)) return rc;
+    res = ws->host_scalars[1];
+    rel = ws->host_scalars[2];
+    if (ws->host_scalars[3] != 0.0) {
+      status = STN_OK;
+      break;
+    }
+    if (outer >= max_outer || ws->host_scalars[4] == 0.0) break;
+    if (int rc = launch_refine_scale_diff(t, du, r32, g, ws->scalars + 4, s)) return rc;
+    STN_CUDA_TRY(cudaMemsetAsync(e, 0, b32, s));  // e = 0 (e2's interior is overwritten first)
+    float* cur = e;
+    float* nxt = e2;
+    i64 done = 0;
+    if (inner_tol > 0.0) {
+      // groups of check_every sweeps, the last fused with ||e' - e||, until it
+      // is <= inner_tol * ||r32|| or inner_sweeps are done
+      i64 np = 0;
+      if (int rc = launch_interior_sumsq<float>(r32, g, ws->partials, &np, s)) return rc;
+      if (int rc = launch_finalize(ws->partials, np, ws->scalars + 24, nullptr, 0.0, s)) return rc;
+      const i64 max_full = (inner_sweeps / check_every) * check_every;
+      bool conv = false;
+      if (g_solve_graph && max_full >= check_every) {
+        if (int rc = graph_groups<float>(cur, nxt, r32, g, coeffs, ws, ws->scalars + 16, inner_tol, check_every,
+                                         max_full, s, &done, &conv))
+          return rc;
+      }
+      // host-driven groups: without graphs, or a last partial group
+      while (!conv && done < inner_sweeps) {
+        const i64 grp = std::min(check_every, inner_sweeps - done);
+        i64 gl = 0;
+        for (i64 k = 0; k < grp; k++) {
+          if (int rc = launch_star<float>(cur, r32, nxt, g, coeffs, k == grp - 1 ? kSweepResidual : kSweep,
+                                          ws->partials, s, ws->partials_cap, &gl))
+            return rc;
+          std::swap(cur, nxt);
+        }
+        done += grp;
+        if (int rc = launch_finalize(ws->partials, gl, ws->scalars + 16, ws->scalars + 25, inner_tol, s)) return rc;
+        if (int rc = read_scalars(ws, 16, 4, s)) return rc;
+        conv = ws->host_scalars[19] != 0.0;
+      }
+    } else {
+      if (use_repeat_graph(g, inner_sweeps)) {
+        const i64 reps = inner_sweeps / kRepeatBody;
+        int rc = graph_repeat(ws, reps, s, [&](cudaStream_t cs) -> int {
+          for (i64 k = 0; k < kRepeatBody; k++)
+            if (int r = launch_star<float>(k % 2 ? nxt : cur, r32, k % 2 ? cur : nxt, g, coeffs, kSweep, nullptr,
+                                           cs))
+              return r;
+          return STN_OK;
+        });
+        if (rc) return rc;
+        done = reps * kRepeatBody;
+      }
+      for (; done < inner_sweeps; done++) {
+        if (int rc = launch_star<float>(cur, r32, nxt, g, coeffs, kSweep, nullptr, s)) return rc;
+        std::swap(cur, nxt);
+      }
+    }
+    sweeps += done;
+    if (int rc = launch_refine_update(du, cur, g, ws->scalars + 4, s)) return rc;
+    outer++;
+  }
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = sweeps;
+    info->outer = outer;
+    info->rel_res = rel;
+    info->res_norm = res;
+    info->rhs_norm = bn;
+    info->status = status;
+  }
+  return status;
+}
+
+static int refined_direct_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, const double* coeffs,
+                               int radius, double tol, i64 inner_sweeps, double inner_tol, i64 check_every,
+                               i64 max_outer, stn_solve_info* info, void* stream) {
+  clear_error();
+  if (!u) return einval("NULL grid");
+  if (!coeffs) return einval("NULL coeffs");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (!(tol >= 0.0)) return einval("tol must be >= 0");
+  if (inner_sweeps < 0 || max_outer < 0) return einval("inner_sweeps or max_outer < 0");
+  if (check_every < 1) return einval("check_every < 1");
+  if (!(inner_tol >= 0.0)) return einval("inner_tol must be >= 0");
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  if (rhs && overlap(rhs, u, bytes)) return einval("rhs and u overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *db;
+  if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
+  if (int rc = st.add(rhs, bytes, true, false, (void**)&db)) return rc;
+  stn_solve_info loc{};
+  const int status = refined_direct(db, du, g, coeffs, tol, inner_sweeps, inner_tol, check_every, max_outer, &loc, s);
+  if (status < 0) return status;
+  if (int rc = st.finish()) return rc;
+  if (info) *info = loc;
   return status;
 }
 
@@ -767,6 +924,19 @@ static int var_apply_impl(const double* u, const double* a, double* out, i64 nx,
   return st.finish();
 }
 
+// A bounded wait of the TMA-staged float sweep that ran out (never expected:
+// the copies it waits for are its own) leaves a status word set; the
+// synchronising variable-coefficient calls report it once, as STN_ETIMEOUT.
+static int check_var_tma() {
+  int st = 0;
+  if (int rc = var_tma_status(true, &st)) return rc;
+  if (st != 0) {
+    set_error("a TMA-staged variable-coefficient sweep gave up waiting for its tile copies");
+    return STN_ETIMEOUT;
+  }
+  return STN_OK;
+}
+
 static int var_residual_impl(const double* u, const double* a, const double* f, i64 nx, i64 ny,
                              i64 nz, const double* w, int radius, double* norm_out, void* stream) {
   clear_error();
@@ -788,6 +958,7 @@ static int var_residual_impl(const double* u, const double* a, const double* f, 
   if (int rc = launch_finalize(ws->partials, p.blocks(), ws->scalars, nullptr, 0.0, s)) return rc;
   if (int rc = read_scalars(ws, 0, 2, s)) return rc;
   *norm_out = ws->host_scalars[1];
+  if (int rc = check_var_tma()) return rc;
   return st.finish();
 }
 
@@ -890,6 +1061,7 @@ static int refined_impl(const double* a, const double* f, double* u, i64 nx, i64
     if (int rc = launch_finalize(ws->partials, p.blocks(), ws->scalars, ws->scalars + 9, tol, s)) return rc;
     if (int rc = launch_max_finalize(pmax, p.blocks(), ws->scalars + 4, s)) return rc;
     if (int rc = read_scalars(ws, 0, 5, s)) return rc;
+    if (int rc = check_var_tma()) return rc;  // the float sweeps of the last step ran whole
     res = ws->host_scalars[1];
     rel = ws->host_scalars[2];
     if (ws->host_scalars[3] != 0.0) {
@@ -1018,7 +1190,7 @@ int stencil_tune_set(const char* knob, int64_t value) {
     return STN_OK;
   }
   if (strcmp(knob, "var_variant") == 0) {
-    if (tune_set_var_variant((int)value) != STN_OK) return einval("var_variant must be -1, 0 or 1");
+    if (tune_set_var_variant((int)value) != STN_OK) return einval("var_variant must be -1, 0, 1 or 2");
     return STN_OK;
   }
   if (strcmp(knob, "sweep2d_ctas_per_sm") == 0) {
@@ -1039,6 +1211,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
   }
   if (strcmp(knob, "solve_graph") == 0) {
     if (tune_set_solve_graph((int)value) != STN_OK) return einval("solve_graph must be 0 or 1");
+    return STN_OK;
+  }
+  if (strcmp(knob, "refined_engine") == 0) {
+    if (tune_set_refined_engine((int)value) != STN_OK) return einval("refined_engine must be 0 or 1");
     return STN_OK;
   }
   SchedFaults& f = sched_faults();
@@ -1109,6 +1285,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "solve_graph") == 0) {
     *value = tune_get_solve_graph();
+    return STN_OK;
+  }
+  if (strcmp(knob, "refined_engine") == 0) {
+    *value = tune_get_refined_engine();
     return STN_OK;
   }
   const SchedFaults& f = sched_faults();
@@ -1199,6 +1379,9 @@ int jacobi_solve_refined_f64(const double* rhs, double* u, int64_t nx, int64_t n
                              stn_solve_info* info, void* stream) {
   clear_error();
   if (!u) return einval("NULL grid");
+  if (g_refined_engine == 1)
+    return refined_direct_impl(rhs, u, nx, ny, nz, coeffs, radius, tol, inner_sweeps, inner_tol, check_every,
+                               max_outer, info, stream);
   stn_problem p;
   p.nx = nx;
   p.ny = ny;

@@ -275,6 +275,18 @@ template <typename T>
 int launch_var(const T* u, const T* a, const T* f, T* out, const Grid& g, const double* w,
                VarMode mode, double* partials, double* partials_max, cudaStream_t s);
 
+// TMA-staged float sweep of radius 2 (varcoef_tma.cu): applicable when the
+// rows are a multiple of 16 bytes and u, a are 16-byte and f, out 8-byte
+// aligned (NULL pointers: not checked, for planning).
+bool var_tma_applicable(const Grid& g, size_t esize, const void* u, const void* a, const void* f,
+                        const void* out);
+ZPlan plan_var_tma(const Grid& g);
+int launch_var_tma(const float* u, const float* a, const float* f, float* out, const Grid& g, const double* w,
+                   cudaStream_t s);
+// The status word of the TMA-staged sweeps: nonzero once a bounded wait ran
+// out (the sweep stopped early); `clear` resets it.  Synchronous.
+int var_tma_status(bool clear, int* status);
+
 // ---- refinement helpers (refine.cu) ----------------------------------------
 // r32 = float(rho / s), s = dst_scalar[0] (device); e = 0 on the interior.
 int launch_refine_scale(const double* rho, float* r32, const Grid& g, const double* smax,
@@ -283,6 +295,13 @@ int launch_refine_scale(const double* rho, float* r32, const Grid& g, const doub
 int launch_refine_update(double* u, const float* e, const Grid& g, const double* smax,
                          cudaStream_t s);
 int launch_max_finalize(const double* partials, i64 n, double* dst, cudaStream_t s);
+// Block maxima of |t - u| over the interior (at most 152 * 16 partials; the
+// count in *nparts), for the constant-coefficient refinement's scale.
+int launch_diff_max(const double* t, const double* u, const Grid& g, double* partials, i64* nparts,
+                    cudaStream_t s);
+// r32 = float((t - u) / s) on the interior, s = *smax (device).
+int launch_refine_scale_diff(const double* t, const double* u, float* r32, const Grid& g, const double* smax,
+                             cudaStream_t s);
 template <typename T, typename U>
 int launch_convert(const T* src, U* dst, i64 n, cudaStream_t s);
 

@@ -11,6 +11,8 @@
 // Same z-streaming structure as sweep.cu, with two staged fields (u and a):
 // register queues along k for both, shared-memory planes with an R halo for
 // the in-plane neighbours.
+#include <atomic>
+
 #include "arith.cuh"
 #include "internal.h"
 
@@ -421,10 +423,12 @@ int launch_var_t(const T* u, const T* a, const T* f, T* out, const Grid& g, cons
 
 }  // namespace
 
-static int g_var_variant = -1;  // -1 automatic (column), 0 plane, 1 column
+// -1 automatic (TMA-staged for aligned radius-2 float sweeps, else column),
+// 0 plane, 1 column, 2 TMA-staged where it applies (column elsewhere)
+static std::atomic<int> g_var_variant{-1};
 
 int tune_set_var_variant(int v) {
-  if (v < -1 || v > 1) return STN_EINVAL;
+  if (v < -1 || v > 2) return STN_EINVAL;
   g_var_variant = v;
   return STN_OK;
 }
@@ -434,7 +438,23 @@ static bool var_use_column(const Grid& g, size_t esize) {
   // 32-bit row offsets: TJ + 2R rows of NX elements
   const int tj = esize == 4 ? VarColTJ<float>::value : VarColTJ<double>::value;
   if ((i64)(tj + 2 * g.r) * g.NX() >= ((i64)1 << 31)) return false;
-  return g_var_variant != 0;
+  return g_var_variant.load() != 0;
+}
+
+// The TMA-staged kernel takes float sweeps of radius 2 on grids whose rows
+// are a multiple of 16 bytes, unless a knob asks for the plane or column
+// kernel.
+// Automatically only on grids with at least four waves of its 64 x 16-column,
+// 16-plane blocks: on fewer (96 x 96 x 48: 36 blocks) the column kernel's
+// finer grid is faster.
+static bool var_use_tma(const Grid& g, size_t esize, const void* u, const void* a, const void* f,
+                        const void* out) {
+  const int v = g_var_variant.load();
+  if (v != -1 && v != 2) return false;
+  if (!var_tma_applicable(g, esize, u, a, f, out)) return false;
+  if (v == 2) return true;
+  const i64 blocks = ((g.nx + 63) / 64) * ((g.ny + 15) / 16) * ((g.nz + 15) / 16);
+  return blocks >= 4 * 2 * (i64)device_sms();
 }
 
 ZPlan plan_var(const Grid& g, size_t esize) {
@@ -460,8 +480,21 @@ ZPlan plan_var(const Grid& g, size_t esize) {
 }
 
 LaunchPlan var_launch_plan(const Grid& g, size_t esize) {
-  const ZPlan p = plan_var(g, esize);
   LaunchPlan q;
+  if (var_use_tma(g, esize, nullptr, nullptr, nullptr, nullptr)) {
+    const ZPlan p = plan_var_tma(g);
+    q.variant = 2;
+    q.grid_x = p.tiles_x;
+    q.grid_y = p.tiles_y;
+    q.grid_z = p.chunks;
+    q.kchunk = p.kchunk;
+    q.block_threads = 256;
+    q.tile_w = 64;
+    q.tile_h = p.rg;
+    q.smem = p.smem;
+    return q;
+  }
+  const ZPlan p = plan_var(g, esize);
   q.grid_x = p.tiles_x;
   q.grid_y = p.tiles_y;
   q.grid_z = p.chunks;
@@ -485,6 +518,10 @@ template <typename T>
 int launch_var(const T* u, const T* a, const T* f, T* out, const Grid& g, const double* w,
                VarMode mode, double* partials, double* partials_max, cudaStream_t s) {
   constexpr int TJ = VarColTJ<T>::value;
+  if constexpr (sizeof(T) == 4) {
+    if (mode == kVarSweep && var_use_tma(g, sizeof(T), u, a, f, out))
+      return launch_var_tma(u, a, f, out, g, w, s);
+  }
   if (var_use_column(g, sizeof(T))) {
     if (g.r == 1) return launch_var_col_t<T, 1, TJ>(u, a, f, out, g, w, mode, partials, partials_max, s);
     return launch_var_col_t<T, 2, TJ>(u, a, f, out, g, w, mode, partials, partials_max, s);

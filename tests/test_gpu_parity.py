@@ -418,9 +418,11 @@ def test_jacobi_solve_not_converged_and_zero_iters(lib, cuda, solve_mode):
 VW = si.VARCOEF_W
 
 
-@pytest.fixture(params=[-1, 0])
+@pytest.fixture(params=[-1, 0, 1])
 def var_variant(request, lib):
-    """-1: the column kernel with shared face coefficients (default); 0: the plane kernel."""
+    """-1: automatic (the TMA-staged kernel for float radius-2 sweeps on rows of
+    a multiple of 16 bytes, else the column kernel with shared face
+    coefficients); 0: the plane kernel; 1: the column kernel."""
     lib.stencil_tune_set("var_variant", request.param)
     yield request.param
     lib.stencil_tune_set("var_variant", -1)

@@ -95,6 +95,13 @@ def test_varcoef_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r):
         assert ny > 65535 * 4, (nx, ny, nz)
         return
     check_common(q, nx, ny, nz, r)
+    if q["variant"] == 2:
+        # TMA-staged: float, radius 2, rows a multiple of 16 bytes
+        assert esize == 4 and r == 2 and ((nx + 2 * r) * 4) % 16 == 0
+        assert (q["tile_w"], q["tile_h"], q["block_threads"]) == (64, 16, 256)
+        assert q["smem_bytes"] == VT_SMEM_ALLOC and q["stage_elems"] == 0
+        assert q["grid_z"] <= ceil_div(nz, 16)
+        return
     assert q["smem_bytes"] == 0 and q["stage_elems"] == 0
     if q["variant"] == 1:
         tj = 4 if esize == 4 else 2
@@ -106,6 +113,111 @@ def test_varcoef_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r):
         assert q["grid_x"] * q["grid_y"] * q["grid_z"] <= max(32768, q["grid_x"] * q["grid_y"])
     else:
         assert q["variant"] == 0 and (q["tile_w"], q["tile_h"], q["block_threads"]) == (32, 8, 256)
+
+
+# the TMA-staged variable-coefficient float sweep (radius 2)
+VT_TW, VT_TH, VT_R, VT_S, VT_Q = 64, 16, 2, 6, 5
+VT_PW, VT_PH = VT_TW + 2 * VT_R, VT_TH + 2 * VT_R
+VT_FIELD = -(-(VT_PW * VT_PH) // 32) * 32
+VT_SMEM_ALLOC = VT_S * 2 * VT_FIELD * 4 + 128
+
+
+def tma_block_replay(nx, ny, nz, bx, by, bz, kchunk):
+    """Replays one block of the TMA-staged kernel: the tensor-map box origin of
+    every plane it stages (x a multiple of 16 bytes, z inside the grid), the
+    ring's issue and wait order (a plane is issued before it is waited for and
+    never into a stage whose plane is still in use), every shared-memory
+    element the threads read (inside the box and the stage), and every global
+    f load and out store (inside the interior, on 8-byte boundaries)."""
+    R = VT_R
+    NX, NY, NZ = nx + 2 * R, ny + 2 * R, nz + 2 * R
+    tx0, ty0 = bx * VT_TW, by * VT_TH
+    k0 = R + bz * kchunk
+    k1 = min(k0 + kchunk, nz + R)
+    assert k0 < k1
+    pfirst, plast = k0 - R, k1 - 1 + R
+    assert (tx0 * 4) % 16 == 0 and tx0 < NX and ty0 < NY
+    assert 0 <= pfirst and plast <= NZ - 1
+    assert VT_S * 2 * VT_FIELD * 4 + 128 <= SMEM_PER_BLOCK_MAX
+    issued, waited, in_use = [], set(), {}
+    nxt = pfirst
+
+    def issue_upto(limit):
+        nonlocal nxt
+        while nxt <= plast and nxt < limit:
+            s = (nxt - pfirst) % VT_S
+            prev = in_use.get(s)
+            assert prev is None or prev in waited, (nxt, prev)
+            in_use[s] = nxt
+            issued.append(nxt)
+            nxt += 1
+
+    def wait(p):
+        assert p in issued and p not in waited, p
+        waited.add(p)
+
+    issue_upto(pfirst + VT_S)
+    for p in range(pfirst, pfirst + 2 * R):
+        wait(p)
+    live = set(range(pfirst, pfirst + 2 * R))  # planes read so far and not yet released
+    for k in range(k0, k1):
+        wait(k + R)
+        # after the barrier: planes < k are no longer read by anyone
+        live = {p for p in live if p >= k}
+        issue_upto(k + VT_S)
+        for p in live | {k, k + R}:
+            assert in_use[(p - pfirst) % VT_S] == p, (k, p)  # its stage still holds it
+        live |= {k, k + R}
+    assert waited == set(issued) == set(range(pfirst, plast + 1))
+    # shared-memory reads and global accesses of every thread
+    for tid in range(256):
+        lx, ly = tid & 31, tid >> 5
+        c, rr = 2 * lx + R, 2 * ly + R
+        for col in (c - 2, c, c + 2):      # 8-byte loads: columns col, col + 1
+            assert col % 2 == 0 and 0 <= col and col + 1 < VT_PW
+        for row in range(rr - 2, rr + 4):
+            assert 0 <= row < VT_PH
+        gi, gj = tx0 + c, ty0 + rr
+        for t in (0, 1):
+            if gj + t < ny + R and gi < nx + R:
+                for k in range(k0, k1):
+                    off = (k * NY + gj + t) * NX + gi
+                    assert off % 2 == 0  # 8-byte f loads / out stores
+                    assert R <= gj + t < ny + R and R <= gi and gi + 1 <= nx + R < NX
+
+
+def test_tma_varcoef_is_automatic_on_large_grids_only(lib):
+    """The TMA-staged float sweep is the automatic choice where it has at least
+    four waves of blocks (the variable-coefficient workload's grid), the column
+    kernel below that and on rows that are not a multiple of 16 bytes."""
+    assert lib.stencil_plan_query("varcoef_sweep", 768, 768, 384, 4, 2)["variant"] == 2
+    assert lib.stencil_plan_query("varcoef_sweep", 512, 512, 256, 4, 2)["variant"] == 2
+    assert lib.stencil_plan_query("varcoef_sweep", 96, 96, 48, 4, 2)["variant"] == 1
+    assert lib.stencil_plan_query("varcoef_sweep", 767, 768, 384, 4, 2)["variant"] == 1
+    assert lib.stencil_plan_query("varcoef_sweep", 768, 768, 384, 4, 1)["variant"] == 1
+    assert lib.stencil_plan_query("varcoef_sweep", 768, 768, 384, 8, 2)["variant"] == 1
+
+
+@pytest.fixture
+def tma_forced(lib):
+    lib.stencil_tune_set("var_variant", 2)
+    yield
+    lib.stencil_tune_set("var_variant", -1)
+
+
+@pytest.mark.parametrize("shape", [(768, 768, 384), (64, 16, 8), (68, 17, 5), (4, 1, 1), (196, 50, 23),
+                                   (60, 15, 130), (8, 100, 2), (132, 7, 64), (256, 33, 17), (384, 96, 200),
+                                   (512, 512, 256), (28, 20, 12)])
+def test_tma_varcoef_addressing_stays_in_bounds(lib, tma_forced, shape):
+    nx, ny, nz = shape
+    q = lib.stencil_plan_query("varcoef_sweep", nx, ny, nz, 4, 2)
+    assert q["variant"] == 2
+    check_common(q, nx, ny, nz, 2)
+    gx, gy, gz, kc = q["grid_x"], q["grid_y"], q["grid_z"], q["kchunk"]
+    for bx in sorted({0, gx - 1}):
+        for by in sorted({0, gy - 1}):
+            for bz in sorted({0, min(1, gz - 1), gz - 1}):
+                tma_block_replay(nx, ny, nz, bx, by, bz, kc)
 
 
 def staged_copies_stay_in_bounds(nx, ny, nz, esize, r, q, base_misalign):
