@@ -459,13 +459,25 @@ int jacobi_solve_batched_refined(const stn_problem* probs, int64_t count, const 
 
 /*
  * Serving loop (continuous batching; not in the paper).  A server owns a
- * device-memory budget and a persistent scheduler kernel.  Requests (one
- * Poisson/Jacobi solve u = S u + rhs each, extents per request) are submitted
- * at any time from any thread; the server admits them in arrival order as
- * their grids fit in the budget, runs every admitted request concurrently on
- * the GPU (requests admitted while others run join the running kernel), and
- * hands back the solution.  A result depends only on its request: it is the
- * same alone and in any mix of concurrent requests.
+ * device-memory budget.  Requests (one Poisson/Jacobi solve u = S u + rhs
+ * each, extents per request) are submitted at any time from any thread; the
+ * server admits them in arrival order as their grids fit in the budget, runs
+ * the admitted requests concurrently on the GPU, and hands back the
+ * solution.  Two engines:
+ *   0  a persistent scheduler kernel: every admitted request's passes are
+ *      split into work units that any CTA claims; requests admitted while
+ *      others run join the running kernel.  Its results are those of
+ *      jacobi_solve_batched_refined / _f64 on the request alone.
+ *   1  max_inflight worker streams: each takes the oldest admitted request,
+ *      runs it with the full-grid kernels of jacobi_solve_refined_f64 (or
+ *      jacobi_solve_f64 when not refined) and takes the next; the kernels of
+ *      different requests overlap on the device.  Its results are those of
+ *      jacobi_solve_refined_f64 / jacobi_solve_f64 on the request alone.  The
+ *      budget counts each running request's grids and scratch (3 double and,
+ *      refined, 3 float grids); each worker also keeps 2 MiB of reduction
+ *      slots and a few scalars outside it.
+ * A result depends only on its request: it is the same alone and in any mix
+ * of concurrent requests.
  */
 typedef struct stn_server stn_server;
 
@@ -480,8 +492,12 @@ typedef struct stn_server_opts {
   double inner_tol;        /* refined: inner stop (0 = run inner_sweeps) */
   int64_t check_every;     /* sweeps per convergence check */
   int64_t max_outer;       /* refined: outer step limit */
-  int max_inflight;        /* requests on the GPU at once */
-  int queue_capacity;      /* admitted-but-unfinished requests the device queue holds */
+  int max_inflight;        /* requests on the GPU at once (engine 1: worker streams, <= 64) */
+  int queue_capacity;      /* engine 0: admitted-but-unfinished requests the device queue holds */
+  int engine;              /* 0: the persistent work-unit scheduler kernel;
+                              1: a pool of max_inflight worker streams, each running one
+                                 request at a time on the full-grid kernels (the steps of
+                                 jacobi_solve_refined_f64 / jacobi_solve_f64) */
 } stn_server_opts;
 
 typedef struct stn_request {

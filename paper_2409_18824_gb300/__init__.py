@@ -54,7 +54,8 @@ class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("radius", ctypes.c_int), ("coeffs", ctypes.c_double * 3),
                 ("tol", ctypes.c_double), ("refined", ctypes.c_int), ("max_iters", ctypes.c_int64),
                 ("inner_sweeps", ctypes.c_int64), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int64),
-                ("max_outer", ctypes.c_int64), ("max_inflight", ctypes.c_int), ("queue_capacity", ctypes.c_int)]
+                ("max_outer", ctypes.c_int64), ("max_inflight", ctypes.c_int), ("queue_capacity", ctypes.c_int),
+                ("engine", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -569,7 +570,7 @@ class Server:
 
     def __init__(self, hbm_budget, coeffs=(0.0, 1.0 / 6.0), radius=1, tol=1e-8, refined=True, max_iters=10 ** 7,
                  inner_sweeps=200000, inner_tol=1e-2, check_every=50, max_outer=40, max_inflight=64,
-                 queue_capacity=4096):
+                 queue_capacity=4096, engine=0):
         o = ServerOpts()
         o.hbm_budget = int(hbm_budget)
         o.radius = radius
@@ -577,7 +578,7 @@ class Server:
             o.coeffs[i] = float(coeffs[i]) if i < len(coeffs) else 0.0
         o.tol, o.refined, o.max_iters = tol, int(refined), max_iters
         o.inner_sweeps, o.inner_tol, o.check_every, o.max_outer = inner_sweeps, inner_tol, check_every, max_outer
-        o.max_inflight, o.queue_capacity = max_inflight, queue_capacity
+        o.max_inflight, o.queue_capacity, o.engine = max_inflight, queue_capacity, engine
         h = _lib.stn_server_create(ctypes.byref(o))
         if not h:
             raise StencilError(STN_EINVAL, last_error())

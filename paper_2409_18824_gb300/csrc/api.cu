@@ -625,28 +625,15 @@ static int graph_groups(T* a, T* bgrid, const T* db, const Grid& g, const double
   return STN_OK;
 }
 
-static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, const double* coeffs,
-                       int radius, double tol, i64 max_iters, i64 check_every, stn_solve_info* info,
-                       void* stream) {
-  clear_error();
-  if (!u) return einval("NULL grid");
-  if (!coeffs) return einval("NULL coeffs");
-  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
-  if (!(tol >= 0.0)) return einval("tol must be >= 0");
-  if (max_iters < 0) return einval("max_iters < 0");
-  if (check_every < 1) return einval("check_every < 1");
-  const Grid g{nx, ny, nz, radius};
+// The double Jacobi solve of one device problem (tmp: a scratch grid of the
+// problem's size); synchronises `s`.  Shared by jacobi_solve_f64 and the
+// stream-pool server.
+int solve_jacobi_core(const double* db, double* du, double* tmp, const Grid& g, const double* coeffs, double tol,
+                      i64 max_iters, i64 check_every, stn_solve_info* info, cudaStream_t s) {
   const size_t bytes = (size_t)g.count() * sizeof(double);
-  if (rhs && overlap(rhs, u, bytes)) return einval("rhs and u overlap");
-  cudaStream_t s = (cudaStream_t)stream;
-  Stager st(s);
-  double *du, *db;
-  if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
-  if (int rc = st.add(rhs, bytes, true, false, (void**)&db)) return rc;
   Workspace* ws;
-  if (int rc = get_workspace(s, plan_star(g, kStarScalar, 8).blocks() + plan_star(g, kStarColumn, 8).blocks() + plan_star(g, kStarPlane2, 8).blocks() + plan_star(g, kStarStaged, 8).blocks(), bytes, &ws))
+  if (int rc = get_workspace(s, plan_star(g, kStarScalar, 8).blocks() + plan_star(g, kStarColumn, 8).blocks() + plan_star(g, kStarPlane2, 8).blocks() + plan_star(g, kStarStaged, 8).blocks(), 0, &ws))
     return rc;
-  double* tmp = (double*)ws->grid;
   const i64 nb_sweep = star_blocks(g, sizeof(double), du, db, tmp);
   if (int rc = launch_copy_halo<double>(du, tmp, g, s)) return rc;
   double bn = 0.0;
@@ -690,7 +677,6 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
     status = ws->host_scalars[3] != 0.0 ? STN_OK : STN_NOT_CONVERGED;
   }
   if (cur != du) STN_CUDA_TRY(cudaMemcpyAsync(du, cur, bytes, cudaMemcpyDeviceToDevice, s));
-  if (int rc = st.finish()) return rc;
   STN_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) {
     info->iters = done;
@@ -700,6 +686,34 @@ static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, con
     info->rhs_norm = bn;
     info->status = status;
   }
+  return status;
+}
+
+static int jacobi_impl(const double* rhs, double* u, i64 nx, i64 ny, i64 nz, const double* coeffs,
+                       int radius, double tol, i64 max_iters, i64 check_every, stn_solve_info* info,
+                       void* stream) {
+  clear_error();
+  if (!u) return einval("NULL grid");
+  if (!coeffs) return einval("NULL coeffs");
+  if (int rc = check_grid(nx, ny, nz, radius)) return rc;
+  if (!(tol >= 0.0)) return einval("tol must be >= 0");
+  if (max_iters < 0) return einval("max_iters < 0");
+  if (check_every < 1) return einval("check_every < 1");
+  const Grid g{nx, ny, nz, radius};
+  const size_t bytes = (size_t)g.count() * sizeof(double);
+  if (rhs && overlap(rhs, u, bytes)) return einval("rhs and u overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Stager st(s);
+  double *du, *db;
+  if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
+  if (int rc = st.add(rhs, bytes, true, false, (void**)&db)) return rc;
+  Workspace* ws;
+  if (int rc = get_workspace(s, 0, bytes, &ws)) return rc;
+  stn_solve_info loc{};
+  const int status = solve_jacobi_core(db, du, (double*)ws->grid, g, coeffs, tol, max_iters, check_every, &loc, s);
+  if (status < 0) return status;
+  if (int rc = st.finish()) return rc;
+  if (info) *info = loc;
   return status;
 }
 
@@ -724,18 +738,16 @@ int tune_set_refined_engine(int v) {
 }
 int tune_get_refined_engine() { return g_refined_engine; }
 
-static int refined_direct(const double* db, double* du, const Grid& g, const double* coeffs, double tol,
-                          i64 inner_sweeps, double inner_tol, i64 check_every, i64 max_outer,
-                          stn_solve_info* info, cudaStream_t s) {
+int solve_refined_core(const double* db, double* du, double* t, float* f32, const Grid& g, const double* coeffs,
+                       double tol, i64 inner_sweeps, double inner_tol, i64 check_every, i64 max_outer,
+                       stn_solve_info* info, cudaStream_t s) {
   const i64 n = g.count();
-  const size_t b64 = (size_t)n * sizeof(double), b32 = (size_t)n * sizeof(float);
+  const size_t b32 = (size_t)n * sizeof(float);
   i64 cap = 2 * 152 * 16;  // interior reductions: one partial per block of at most 152 * 16
   for (int v = 0; v < 4; v++) cap += plan_star(g, v, 8).blocks() + plan_star(g, v, 4).blocks();
   Workspace* ws;
-  if (int rc = get_workspace(s, cap, b64, &ws)) return rc;
-  if (int rc = ensure_grid2(ws, 3 * b32)) return rc;
-  double* t = (double*)ws->grid;
-  float* r32 = (float*)ws->grid2;
+  if (int rc = get_workspace(s, cap, 0, &ws)) return rc;
+  float* r32 = f32;
   float* e = r32 + n;
   float* e2 = e + n;
   // the correction's halo is zero (homogeneous Dirichlet): zero both buffers once
@@ -846,8 +858,13 @@ static int refined_direct_impl(const double* rhs, double* u, i64 nx, i64 ny, i64
   double *du, *db;
   if (int rc = st.add(u, bytes, true, true, (void**)&du)) return rc;
   if (int rc = st.add(rhs, bytes, true, false, (void**)&db)) return rc;
+  const i64 n = g.count();
+  Workspace* ws;
+  if (int rc = get_workspace(s, 0, (size_t)n * sizeof(double), &ws)) return rc;
+  if (int rc = ensure_grid2(ws, 3 * (size_t)n * sizeof(float))) return rc;
   stn_solve_info loc{};
-  const int status = refined_direct(db, du, g, coeffs, tol, inner_sweeps, inner_tol, check_every, max_outer, &loc, s);
+  const int status = solve_refined_core(db, du, (double*)ws->grid, (float*)ws->grid2, g, coeffs, tol, inner_sweeps,
+                                        inner_tol, check_every, max_outer, &loc, s);
   if (status < 0) return status;
   if (int rc = st.finish()) return rc;
   if (info) *info = loc;

@@ -287,6 +287,19 @@ int launch_var_tma(const float* u, const float* a, const float* f, float* out, c
 // out (the sweep stopped early); `clear` resets it.  Synchronous.
 int var_tma_status(bool clear, int* status);
 
+// ---- one-problem solves on the full-grid kernels (api.cu) -------------------
+// Double Jacobi of one device problem (db may be NULL); tmp: a scratch grid
+// of the problem's size.  Synchronises `s`; returns STN_OK,
+// STN_NOT_CONVERGED or an error.
+int solve_jacobi_core(const double* db, double* du, double* tmp, const Grid& g, const double* coeffs, double tol,
+                      i64 max_iters, i64 check_every, stn_solve_info* info, cudaStream_t s);
+// The refinement of jacobi_solve_refined_f64 for one device problem; t: a
+// double scratch grid, f32: three float scratch grids (r32, e, e'), all of
+// the problem's size.  Synchronises `s`.
+int solve_refined_core(const double* db, double* du, double* t, float* f32, const Grid& g, const double* coeffs,
+                       double tol, i64 inner_sweeps, double inner_tol, i64 check_every, i64 max_outer,
+                       stn_solve_info* info, cudaStream_t s);
+
 // ---- refinement helpers (refine.cu) ----------------------------------------
 // r32 = float(rho / s), s = dst_scalar[0] (device); e = 0 on the interior.
 int launch_refine_scale(const double* rho, float* r32, const Grid& g, const double* smax,

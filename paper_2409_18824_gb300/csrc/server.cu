@@ -19,6 +19,7 @@
 #include <string.h>
 #include <time.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -93,8 +94,132 @@ struct ServerImpl {
   size_t need_bytes(const Req& r) const {
     const size_t n = (size_t)((r.nx + 2 * opts.radius) * (r.ny + 2 * opts.radius) * (r.nz + 2 * opts.radius));
     const size_t n8 = (n * 8 + 255) / 256 * 256, n4 = (n * 4 + 255) / 256 * 256;
+    // pool engine: u, rhs, one double scratch grid and, refined, three float ones
+    if (opts.engine == 1) return 3 * n8 + (opts.refined ? 3 * n4 : 0);
     const size_t units = (size_t)sched_units(r.nx, r.ny, r.nz);
     return 3 * n8 + (opts.refined ? 3 * n4 : 0) + (units * 8 + 255) / 256 * 256;
+  }
+
+  // --- stream-pool engine ----------------------------------------------------
+  // Worker w owns stream ws_[w].  It takes the oldest pending request when
+  // its grids fit the budget (arrival order: a request that does not fit
+  // holds back the ones behind it), runs it on the full-grid kernels, copies
+  // the solution out and frees the grids.  max_inflight workers run their
+  // requests at the same time, so requests arriving while others are on the
+  // GPU are admitted as workers and memory free up and their kernels overlap
+  // with the running ones.  A result depends only on its request.
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> wstreams;
+
+  void pool_worker(int w) {
+    cudaSetDevice(device);
+    cudaStream_t st = wstreams[(size_t)w];
+    {
+      // partial-sum slots for any request up to 256^3-class grids, sized once:
+      // growing them later would synchronise the device under the others
+      Workspace* ws;
+      if (get_workspace(st, (i64)1 << 17, 0, &ws) != STN_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        fail(STN_ENOMEM, "server worker workspace");
+        cv.notify_all();
+        return;
+      }
+    }
+    while (true) {
+      Req* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] {
+          if (fatal != STN_OK) return true;
+          if (pending.empty()) return stop;
+          return in_use + pending.front()->bytes <= opts.hbm_budget;
+        });
+        if (fatal != STN_OK) {  // the server cannot run: fail what is left
+          for (Req* q : pending) {
+            q->rc = fatal;
+            q->t_done = now_s();
+            q->state = 2;
+          }
+          pending.clear();
+          cv.notify_all();
+          return;
+        }
+        if (pending.empty()) return;
+        r = pending.front();
+        pending.pop_front();
+        in_use += r->bytes;
+        running.push_back(r);
+        r->state = 1;
+        r->t_admit = now_s();
+      }
+      const int rc = pool_run(r, st);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        if (rc == -1) {  // device pool busy (or an injected failure): back to the head, retry
+          in_use -= r->bytes;
+          running.erase(std::find(running.begin(), running.end(), r));
+          r->state = 0;
+          r->t_admit = 0;
+          pending.push_front(r);
+          cv.notify_all();
+        } else {
+          r->rc = rc;
+          in_use -= r->bytes;
+          running.erase(std::find(running.begin(), running.end(), r));
+          r->t_done = now_s();
+          r->state = 2;
+          completed++;
+          cv.notify_all();
+        }
+      }
+      if (rc == -1) std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+  }
+
+  // One request on stream st: -1 when the grids could not be allocated now,
+  // else the solve's status or an error.
+  int pool_run(Req* r, cudaStream_t st) {
+    const int R = opts.radius;
+    const Grid g{r->nx, r->ny, r->nz, R};
+    const size_t n = (size_t)g.count();
+    const size_t n8 = (n * 8 + 255) / 256 * 256;
+    {
+      SchedFaults& f = sched_faults();
+      std::lock_guard<std::mutex> lk(mu);
+      if (f.admit_fail > 0) {  // injected allocation failure: same path as a busy pool
+        f.admit_fail--;
+        f.admit_failed++;
+        return -1;
+      }
+    }
+    char* dev = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dev, r->bytes, st);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return -1;
+    }
+    double* du = (double*)dev;
+    double* db = (double*)(dev + n8);
+    double* dt = (double*)(dev + 2 * n8);
+    float* f32 = (float*)(dev + 3 * n8);
+    int rc = STN_OK;
+    if ((e = cudaMemcpyAsync(du, r->u.data(), n * 8, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(db, r->rhs.data(), n * 8, cudaMemcpyHostToDevice, st)))
+      rc = cuda_fail(e, "server admission copy");
+    stn_solve_info info{};
+    if (rc == STN_OK) {
+      rc = opts.refined ? solve_refined_core(db, du, dt, f32, g, opts.coeffs, opts.tol, opts.inner_sweeps,
+                                             opts.inner_tol, opts.check_every, opts.max_outer, &info, st)
+                        : solve_jacobi_core(db, du, dt, g, opts.coeffs, opts.tol, opts.max_iters, opts.check_every,
+                                            &info, st);
+    }
+    if (rc >= 0) {
+      if ((e = cudaMemcpyAsync(r->u.data(), du, n * 8, cudaMemcpyDeviceToHost, st))) rc = cuda_fail(e, "server copy-out");
+    }
+    cudaFreeAsync(dev, st);
+    if ((e = cudaStreamSynchronize(st)) && rc >= 0) rc = cuda_fail(e, "server request");
+    r->info = info;
+    return rc;
   }
 
   int fail(int rc, const std::string& m) {
@@ -310,7 +435,8 @@ stn_server* stn_server_create(const stn_server_opts* o) {
   }
   if ((o->radius != 1 && o->radius != 2) || !(o->tol >= 0.0) || o->check_every < 1 ||
       o->max_inflight < 1 || o->max_iters < 0 || o->inner_sweeps < 0 || o->max_outer < 0 ||
-      !(o->inner_tol >= 0.0) || o->hbm_budget == 0 || o->queue_capacity < 1) {
+      !(o->inner_tol >= 0.0) || o->hbm_budget == 0 || o->queue_capacity < 1 || o->engine < 0 || o->engine > 1 ||
+      (o->engine == 1 && o->max_inflight > 64)) {
     set_error("invalid argument: server options out of range");
     return nullptr;
   }
@@ -323,6 +449,19 @@ stn_server* stn_server_create(const stn_server_opts* o) {
     return (stn_server*)nullptr;
   };
   if ((e = cudaGetDevice(&s->device))) return bad(e, "cudaGetDevice");
+  if (o->engine == 1) {
+    for (int w = 0; w < o->max_inflight; w++) {
+      cudaStream_t st;
+      if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) {
+        for (cudaStream_t x : s->wstreams) cudaStreamDestroy(x);
+        s->wstreams.clear();
+        return bad(e, "stream");
+      }
+      s->wstreams.push_back(st);
+    }
+    for (int w = 0; w < o->max_inflight; w++) s->workers.emplace_back([s, w] { s->pool_worker(w); });
+    return (stn_server*)s;
+  }
   s->ctas = sched_ctas(o->radius, o->coeffs[0] != 0.0, o->refined != 0);
   if (s->ctas < 1) {
     set_error("scheduler kernel does not fit on an SM");
@@ -506,6 +645,14 @@ void stn_server_destroy(stn_server* sv) {
     s->cv.notify_all();
   }
   if (s->th.joinable()) s->th.join();
+  for (auto& t : s->workers)
+    if (t.joinable()) t.join();
+  if (s->opts.engine == 1) {
+    for (cudaStream_t x : s->wstreams) cudaStreamDestroy(x);
+    for (auto& kv : s->reqs) delete kv.second;
+    delete s;
+    return;
+  }
   cudaStreamSynchronize(s->sk);
   cudaStreamSynchronize(s->sc);
   for (auto& kv : s->reqs) {

@@ -306,6 +306,11 @@ def test_server_rejects_bad_options(lib):
     o.radius = 1
     o.hbm_budget = 0
     assert not lib.lib().stn_server_create(ctypes.byref(o))
+    o.hbm_budget = 1 << 20
+    for engine, inflight in ((2, 4), (-1, 4), (1, 65)):  # unknown engine; too many worker streams
+        o.engine, o.max_inflight = engine, inflight
+        assert not lib.lib().stn_server_create(ctypes.byref(o))
+        assert "out of range" in lib.last_error()
     assert not lib.lib().stn_server_create(None)
 
 

@@ -1,8 +1,10 @@
 """Serving loop (stn_server_*): requests arrive while others run, are admitted
-against a device-memory budget and run concurrently in the persistent
-scheduler.  Each result must be the same bits alone and in the mix (compared
-with the batched solver on that request alone) and meet its tolerance on the
-CPU oracle's independent double residual."""
+against a device-memory budget and run concurrently -- engine 0 in the
+persistent scheduler, engine 1 on a pool of worker streams running the
+full-grid kernels.  Each result must be the same bits alone and in the mix
+(compared with the same engine's solver on that request alone: the batched
+solver for engine 0, jacobi_solve_refined_f64 / jacobi_solve_f64 for engine 1)
+and meet its tolerance on the CPU oracle's independent double residual."""
 import threading
 import time
 
@@ -26,10 +28,17 @@ def requests(n, seed=31, lo=6, hi=24):
     return [si.normal_interior(int(x), int(y), int(z), 1, seed=seed * 1000 + i) for i, (x, y, z) in enumerate(sizes)]
 
 
-def alone(lib, rhs, refined, tol):
+def alone(lib, rhs, refined, tol, engine=0):
     import torch
     u = torch.zeros(rhs.shape, dtype=torch.float64, device="cuda")
     b = torch.from_numpy(rhs).cuda()
+    if engine == 1:
+        if refined:
+            rc, info = lib.jacobi_solve_refined_f64(b, u, L7, 1, tol, 200000, 1e-2, 50, 40)
+        else:
+            rc, info = lib.jacobi_solve_f64(b, u, L7, 1, tol, 10 ** 6, 50)
+        torch.cuda.synchronize()
+        return u.cpu().numpy(), info
     if refined:
         rc, infos = lib.jacobi_solve_batched_refined([u], [b], L7, 1, tol, 200000, 1e-2, 50, 40)
     else:
@@ -38,12 +47,18 @@ def alone(lib, rhs, refined, tol):
     return u.cpu().numpy(), infos[0]
 
 
+@pytest.fixture(params=[0, 1])
+def engine(request):
+    return request.param
+
+
 @pytest.mark.parametrize("refined", [True, False])
-def test_serving_results_same_alone_and_in_the_mix(lib, cuda, refined):
+def test_serving_results_same_alone_and_in_the_mix(lib, cuda, refined, engine):
     tol = 1e-8
     rhss = requests(16)
     got = {}
-    with lib.Server(hbm_budget=1 << 30, tol=tol, refined=refined, check_every=50, max_inflight=8) as srv:
+    with lib.Server(hbm_budget=1 << 30, tol=tol, refined=refined, check_every=50, max_inflight=8,
+                    engine=engine) as srv:
         tickets = []
         for i, b in enumerate(rhss):  # arrivals spread over the run
             tickets.append(srv.submit(b))
@@ -59,17 +74,17 @@ def test_serving_results_same_alone_and_in_the_mix(lib, cuda, refined):
         assert st["bytes_in_use"] == 0
     for i, b in enumerate(rhss):
         u, res = got[i]
-        ref, info = alone(lib, b, refined, tol)
+        ref, info = alone(lib, b, refined, tol, engine)
         assert bitwise(u, ref), i
         assert res["iters"] == info["iters"] and res["outer"] == info["outer"]
         assert oracle.residual_norm(u, L7, 1, b) / oracle.interior_norm(b, 1) <= tol
 
 
-def test_serving_admission_respects_budget(lib, cuda):
+def test_serving_admission_respects_budget(lib, cuda, engine):
     rhss = requests(10, seed=41, lo=20, hi=28)
     per = 3 * 8 * max(b.size for b in rhss) + 3 * 4 * max(b.size for b in rhss) + (1 << 16)
     budget = int(per * 1.5)  # room for the largest request plus a small one
-    with lib.Server(hbm_budget=budget, tol=1e-8, refined=True, max_inflight=8) as srv:
+    with lib.Server(hbm_budget=budget, tol=1e-8, refined=True, max_inflight=8, engine=engine) as srv:
         tickets = [srv.submit(b) for b in rhss]
         peak_pending, peak_bytes = 0, 0
         done = 0
@@ -90,16 +105,16 @@ def test_serving_admission_respects_budget(lib, cuda):
             assert oracle.residual_norm(u, L7, 1, b) / oracle.interior_norm(b, 1) <= 1e-8
 
 
-def test_serving_rejects_oversize_and_concurrent_submitters(lib, cuda):
+def test_serving_rejects_oversize_and_concurrent_submitters(lib, cuda, engine):
     big = np.zeros(si.padded_shape(64, 64, 64, 1))
-    with lib.Server(hbm_budget=1 << 20, tol=1e-6, refined=True) as srv:
+    with lib.Server(hbm_budget=1 << 20, tol=1e-6, refined=True, max_inflight=4, engine=engine) as srv:
         with pytest.raises(lib.StencilError) as ei:
             srv.submit(big)
         assert ei.value.code == lib.STN_EBUSY
     # several host threads submitting at once
     rhss = requests(12, seed=51, lo=6, hi=14)
     out = [None] * len(rhss)
-    with lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=False, max_inflight=4) as srv:
+    with lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=False, max_inflight=4, engine=engine) as srv:
         def worker(k):
             for i in range(k, len(rhss), 3):
                 t = srv.submit(rhss[i])
@@ -112,9 +127,9 @@ def test_serving_rejects_oversize_and_concurrent_submitters(lib, cuda):
     assert all(r is not None and r["status"] == 0 for r in out)
 
 
-def test_serving_shutdown_with_requests_in_flight(lib, cuda):
+def test_serving_shutdown_with_requests_in_flight(lib, cuda, engine):
     rhss = requests(6, seed=61, lo=10, hi=20)
-    srv = lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=True, max_inflight=2)
+    srv = lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=True, max_inflight=2, engine=engine)
     for b in rhss:
         srv.submit(b)
     t0 = time.time()
@@ -122,14 +137,14 @@ def test_serving_shutdown_with_requests_in_flight(lib, cuda):
     assert time.time() - t0 < 120
 
 
-def test_serving_survives_injected_admission_failures(lib, cuda):
+def test_serving_survives_injected_admission_failures(lib, cuda, engine):
     """Host-side fault injection: the first admission allocations fail; the
     server retries them later and every request still completes correctly."""
     rhss = requests(6, seed=71, lo=8, hi=16)
     lib.stencil_tune_set("fault_admit_fail", 5)
     before = lib.stencil_tune_get("fault_admit_failed")
     try:
-        with lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=True, max_inflight=4) as srv:
+        with lib.Server(hbm_budget=1 << 28, tol=1e-8, refined=True, max_inflight=4, engine=engine) as srv:
             tickets = [srv.submit(b) for b in rhss]
             for t, b in zip(tickets, rhss):
                 res = srv.wait(t, 60.0)
