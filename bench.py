@@ -393,6 +393,10 @@ def run_cuda(args, wl):
             if allc is not None:
                 out["cpu_all_cores"] = allc
             del ref_out
+        if ws == 1 and wl is WORKLOADS["sweep512"] and not args.no_extras:
+            del d_in, d_out
+            torch.cuda.empty_cache()
+            out.update(run_extras(args, dev))
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -1385,6 +1389,357 @@ def run_serving(args):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------ the metric's other configurations --
+# The default run adds, after the 512^3 headline, the other parts of the
+# benchmark metric under their own keys of the same JSON line: the 64^3
+# configuration ("c1"), the 2048-solve batch ("batched") and the serving loop
+# ("serving").  They run in this order within a wall-clock budget
+# (--extras-budget); a part that would not fit is recorded as skipped.
+
+SERVE_REQUESTS = 200
+SERVE_LOADS = (0.5, 0.8, 1.1)
+SERVE_WORKERS = 4
+
+
+def lindley(arrivals, service):
+    """Latencies of a single first-come-first-served server: request i starts
+    when it has arrived and request i-1 has finished, and runs for service[i]."""
+    lat, free = [], 0.0
+    for a, sv in zip(arrivals, service):
+        start = max(a, free)
+        free = start + sv
+        lat.append(free - a)
+    return lat
+
+
+def pct(x, q):
+    return float(np.percentile(np.asarray(x, dtype=np.float64), q))
+
+
+def extra_c1(stn, dev, with_cpu):
+    """64^3 FP64, U[0,1) seed 1, zero halo, c = {0, 1/6}: 100 sweeps, then the
+    residual L2 norm.  The grid (2.3 MB) stays in L2, so the bound is the
+    kernel latency and the FP64 pipe, not HBM."""
+    import torch
+    n, sweeps, steps = 64, 100, 20
+    u0 = si.uniform_interior(n, n, n, 1, seed=1)
+    d_in = torch.from_numpy(u0).to(dev)
+    d_out = torch.zeros_like(d_in)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        stn.stencil_sweep_f64(d_in, d_out, si.LAPLACE7, 1, sweeps)
+        return stn.residual_norm_f64(d_out, si.LAPLACE7, 1)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index or 0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            norm = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    lups = float(n) ** 3 * sweeps
+    out = {"workload": "7-point Jacobi, 64^3 FP64, zero halo, interior U[0,1) seed 1, 100 sweeps + residual L2 norm",
+           "value": lups / (ms * 1e-3) / 1e9, "unit": "GLUP/s", "ms_per_step": ms, "steps": steps, "warmup": 3,
+           "us_per_sweep": ms * 1e3 / (sweeps + 1), "residual_norm": norm, "clocks": clk.summary(),
+           "roofline": {"bound": "latency", "note": "the grid (2.3 MB per array) stays in L2: a sweep is bound by "
+                        "kernel latency and the FP64 pipe, not HBM"}}
+    out["roofline"].update(fp64_pipe(6.0 * lups, ms, load_peaks()[0], "6 double ops per update"))
+    h_in, h_out = u0.copy(), np.zeros_like(u0)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        stn.stencil_sweep_f64(h_in, h_out, si.LAPLACE7, 1, sweeps)
+        stn.residual_norm_f64(h_out, si.LAPLACE7, 1)
+    e2e_s = (time.perf_counter() - t0) / 3
+    out["e2e"] = {"value": lups / e2e_s / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": 2 * u0.nbytes,
+                  "d2h_bytes_per_step": 2 * u0.nbytes + 8}
+    if with_cpu:
+        import oracle
+        # the timed steps reuse `in` as the ping-pong buffer; one more step from
+        # the configuration's own grid gives the result the oracle checks
+        d_in.copy_(torch.from_numpy(u0))
+        norm = step()
+        t0 = time.perf_counter()
+        ref = oracle.stencil_sweep(u0, si.LAPLACE7, 1, sweeps)
+        rnorm = oracle.residual_norm(ref, si.LAPLACE7, 1)
+        t = time.perf_counter() - t0
+        got = d_out.cpu().numpy()
+        out["cpu_baseline"] = {"value": lups / t / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the whole configuration, plain C oracle, one thread ({t:.2f} s)",
+                               "bitwise_oracle": bool(np.array_equal(got.view(np.uint64), ref.view(np.uint64))),
+                               "norm_rel_diff_oracle": abs(norm - rnorm) / rnorm}
+    return out
+
+
+def extra_batched(stn, dev, refined, with_cpu):
+    """The 2048-solve batch (per-axis sizes log-U[16,128] seed 4, b ~ N(0,1),
+    tol 1e-8) in one persistent scheduler launch: device time of the solve
+    (CUDA events) and, in the same run, the end-to-end time including the
+    right-hand sides' copy in from pinned host memory and the solutions' copy
+    out."""
+    import torch
+    sizes, seeds = batch_problems(2048)
+    tol = 1e-8
+    counts = [(nx + 2) * (ny + 2) * (nz + 2) for nx, ny, nz in sizes]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    total = int(offs[-1])
+    h_rhs = torch.empty(total, dtype=torch.float64).pin_memory()
+    hr = h_rhs.numpy()
+    for i, (nx, ny, nz) in enumerate(sizes):
+        hr[offs[i]:offs[i + 1]] = si.normal_interior(nx, ny, nz, 1, seed=seeds[i]).ravel()
+    h_u = torch.empty(total, dtype=torch.float64).pin_memory()
+    d_rhs = torch.empty(total, dtype=torch.float64, device=dev)
+    d_u = torch.zeros(total, dtype=torch.float64, device=dev)
+    us = [d_u[offs[i]:offs[i + 1]].view(nz + 2, ny + 2, nx + 2) for i, (nx, ny, nz) in enumerate(sizes)]
+    bs = [d_rhs[offs[i]:offs[i + 1]].view(nz + 2, ny + 2, nx + 2) for i, (nx, ny, nz) in enumerate(sizes)]
+
+    def solve(u_list, b_list):
+        if refined:
+            return stn.jacobi_solve_batched_refined(u_list, b_list, si.LAPLACE7, 1, tol, 200000, 1e-2, 50, 40)
+        return stn.jacobi_solve_batched_f64(u_list, b_list, si.LAPLACE7, 1, tol, 10 ** 7, 100)
+
+    d_rhs.copy_(h_rhs)
+    solve(us[:64], bs[:64])  # warm-up: the first 64 problems
+    d_u.zero_()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index or 0) as clk:
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        t0 = time.perf_counter()
+        d_rhs.copy_(h_rhs, non_blocking=True)
+        e[0].record(stream)
+        rc, infos = solve(us, bs)
+        e[1].record(stream)
+        h_u.copy_(d_u, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    ms = e[0].elapsed_time(e[1])
+    pts = np.array([nx * ny * nz for nx, ny, nz in sizes], dtype=np.float64)
+    iters = np.array([i["iters"] for i in infos], dtype=np.float64)
+    out = {"workload": "2048 independent 7-point Poisson solves u = S u + b, per-axis sizes log-uniform in [16,128] "
+                       "(seed 4), b ~ N(0,1), tol 1e-8, one persistent work-unit scheduler launch, "
+                       + ("FP32 sweeps with FP64 refinement" if refined else "FP64"),
+           "value": 2048 / (ms * 1e-3), "unit": "solves/s", "seconds": ms * 1e-3,
+           "aggregate_glups": float((pts * iters).sum()) / (ms * 1e-3) / 1e9,
+           "converged": int(sum(1 for i in infos if i["status"] == 0)),
+           "sweeps_median": float(np.median(iters)), "sweeps_max": int(iters.max()),
+           "e2e": {"value": 2048 / wall, "unit": "solves/s", "h2d_bytes_per_step": total * 8,
+                   "d2h_bytes_per_step": total * 8},
+           "gpu_launches": 1, "scheduler_counters": stn.stencil_sched_stats(), "clocks": clk.summary(),
+           "roofline": {"bound": "latency", "note": "most grids stay in L2 (<= 17.6 MB per array); the scheduler's "
+                        "unit sweeps are bound by latency and, in double, the FP64 pipe"}}
+    if with_cpu:
+        import oracle
+        idx = list(range(0, 2048, 256)) + [int(np.argmax(pts))]
+        hu = h_u.numpy()
+        rels = []
+        for i in idx:
+            nx, ny, nz = sizes[i]
+            u = hu[offs[i]:offs[i + 1]].reshape(nz + 2, ny + 2, nx + 2)
+            b = hr[offs[i]:offs[i + 1]].reshape(nz + 2, ny + 2, nx + 2)
+            rels.append(oracle.residual_norm(u, si.LAPLACE7, 1, b) / oracle.interior_norm(b, 1))
+        out["cpu_baseline"] = cpu_sample_batched(sizes, seeds, pts, iters)
+        out["cpu_baseline"]["oracle_check"] = {
+            "problems": idx, "max_rel_res": max(rels), "tol": tol, "all_within_tol": bool(max(rels) <= tol),
+            "what": "the oracle's own FP64 residual ||S u + b - u|| / ||b|| of the returned u"}
+    return out
+
+
+def serve_pool(stn, rhss, arrivals, tol, keep=()):
+    """One trace through the refined pool server (engine 1): request i is
+    submitted at arrivals[i] s.  Returns (span_s, latencies, statuses, kept
+    solutions by index)."""
+    kept = {}
+    with stn.Server(hbm_budget=40 << 30, tol=tol, refined=True, inner_sweeps=200000, inner_tol=1e-2,
+                    check_every=50, max_outer=40, max_inflight=SERVE_WORKERS, engine=1) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for i, at in enumerate(arrivals):
+            d = at - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(rhss[i]))
+        lat, status = [], []
+        for i, t in enumerate(tickets):
+            r = srv.wait(t, 3600.0)
+            lat.append(r["latency_s"])
+            status.append(r["status"])
+            if i in keep:
+                kept[i] = srv.result(t, rhss[i].shape)
+            srv.release(t)
+        span = time.perf_counter() - t0
+    return span, lat, status, kept
+
+
+def plain_service_times(stn, rhss, tols, deadline):
+    """The plain comparison: one FP64 jacobi_solve_f64 per request, one at a
+    time on the whole GPU, in arrival order.  Each request is copied in,
+    solved to tols[0], copied out (its service time at tols[0]) and then, from
+    that iterate, solved on to tols[1] and copied out again (the continuation
+    is the same sequence of sweeps as a direct solve to tols[1]: groups of 50
+    from the start).  Returns per-tol service times and statuses, or None past
+    the deadline."""
+    import torch
+    svc = {t: [] for t in tols}
+    st = {t: [] for t in tols}
+    for i, b in enumerate(rhss):
+        if time.perf_counter() > deadline:
+            return None, None
+        t0 = time.perf_counter()
+        d_b = torch.from_numpy(b).cuda()
+        d_u = torch.zeros_like(d_b)
+        rc, info = stn.jacobi_solve_f64(d_b, d_u, si.LAPLACE7, 1, tols[0], 10 ** 7, 50)
+        ta = time.perf_counter()
+        d_u.cpu()
+        tb = time.perf_counter()
+        rc2, info2 = stn.jacobi_solve_f64(d_b, d_u, si.LAPLACE7, 1, tols[1], 10 ** 7, 50)
+        d_u.cpu()
+        t2 = time.perf_counter()
+        svc[tols[0]].append(tb - t0)                 # in, solve to tols[0], out
+        st[tols[0]].append(info["status"])
+        svc[tols[1]].append((ta - t0) + (t2 - tb))   # in, solve to tols[1], out
+        st[tols[1]].append(info2["status"])
+    return svc, st
+
+
+def extra_serving(stn, dev, deadline, with_cpu):
+    """Serving (sizes log-U[32,256] seed 6, b ~ N(0,1), Poisson arrivals seed 8,
+    40 GiB budget): the FP32-refined pool server at saturation and at three
+    offered loads of SERVE_REQUESTS requests each, against the plain FP64
+    per-request path on the same requests at the same offered rates, to 1e-10
+    and to 1e-8."""
+    sizes, seeds = serve_requests(SERVE_REQUESTS)
+    rhss = [si.normal_interior(nx, ny, nz, 1, seed=sd) for (nx, ny, nz), sd in zip(sizes, seeds)]
+    n = len(rhss)
+    pts = np.array([nx * ny * nz for nx, ny, nz in sizes], dtype=np.float64)
+    keep = set(range(0, n, 40)) | {int(np.argmax(pts))}
+    out = {"workload": f"{n} Poisson solve requests per trace, per-axis sizes log-uniform in [32,256] (seed 6), "
+                       "rhs N(0,1), Poisson arrivals (seed 8), 40 GiB admission budget",
+           "requests_per_load": n, "engine": f"pool of {SERVE_WORKERS} worker streams on the full-grid kernels",
+           "plain": "one jacobi_solve_f64 per request, in arrival order, on the whole GPU; latencies at each "
+                    "offered rate from its measured per-request service times through the single-server "
+                    "first-come-first-served recursion"}
+    solutions = {}
+
+    def refined_block(tol):
+        res = {}
+        with ClockSampler(dev.index or 0) as clk:
+            span, lat, status, kept = serve_pool(stn, rhss, [0.0] * n, tol, keep)
+        cap = n / span
+        solutions[tol] = kept
+        res["saturation"] = {"solves_per_s": cap, "p50_s": pct(lat, 50), "p99_s": pct(lat, 99),
+                             "converged": int(sum(1 for x in status if x == 0)), "clocks": clk.summary()}
+        res["loads"] = []
+        for frac in SERVE_LOADS:
+            rate = frac * cap
+            est = n / rate * 1.1 + 5
+            if time.perf_counter() + est > deadline:
+                res["loads"].append({"offered_frac": frac, "skipped": f"time budget (about {est:.0f} s)"})
+                continue
+            arr = si.poisson_arrival_times(n, rate, seed=8).tolist()
+            with ClockSampler(dev.index or 0) as clk:
+                span_l, lat_l, st_l, _ = serve_pool(stn, rhss, arr, tol)
+            res["loads"].append({"offered_frac": frac, "offered_per_s": rate, "solves_per_s": n / span_l,
+                                 "p50_s": pct(lat_l, 50), "p99_s": pct(lat_l, 99),
+                                 "converged": int(sum(1 for x in st_l if x == 0)), "clocks": clk.summary()})
+        out[f"tol_{tol:g}"] = {"refined": res}
+
+    # the north-star comparison first: refined to 1e-10, then the plain path
+    # (both tolerances in one pass), then refined to 1e-8
+    refined_block(1e-10)
+    svc = st = None
+    plain_clocks = None
+    if time.perf_counter() + 60 > deadline:
+        out["plain_skipped"] = "time budget"
+    else:
+        with ClockSampler(dev.index or 0) as clk:
+            svc, st = plain_service_times(stn, rhss, (1e-8, 1e-10), deadline)
+        plain_clocks = clk.summary()
+        if svc is None:
+            out["plain_skipped"] = "time budget (stopped part way)"
+    if time.perf_counter() + 30 < deadline:
+        refined_block(1e-8)
+    else:
+        out["tol_1e-08"] = {"skipped": "time budget"}
+    if svc is not None:
+        for tol in (1e-10, 1e-8):
+            key = f"tol_{tol:g}"
+            if "refined" not in out.get(key, {}):
+                continue
+            s_t = svc[tol]
+            sat_lat = lindley([0.0] * n, s_t)
+            plain = {"saturation": {"solves_per_s": n / sum(s_t), "p50_s": pct(sat_lat, 50), "p99_s": pct(sat_lat, 99),
+                                    "converged": int(sum(1 for x in st[tol] if x == 0))},
+                     "service_s": {"median": pct(s_t, 50), "max": max(s_t), "sum": sum(s_t)},
+                     "clocks": plain_clocks, "loads": []}
+            for ld in out[key]["refined"]["loads"]:
+                if "offered_per_s" not in ld:
+                    continue
+                arr = si.poisson_arrival_times(n, ld["offered_per_s"], seed=8).tolist()
+                lat_p = lindley(arr, s_t)
+                plain["loads"].append({"offered_per_s": ld["offered_per_s"], "p50_s": pct(lat_p, 50),
+                                       "p99_s": pct(lat_p, 99),
+                                       "solves_per_s": n / max(a + l for a, l in zip(arr, lat_p))})
+            out[key]["plain"] = plain
+            ref = out[key]["refined"]
+            cmp = {"solves_per_s_ratio": ref["saturation"]["solves_per_s"] / plain["saturation"]["solves_per_s"],
+                   "p99_ratio_at_saturation": plain["saturation"]["p99_s"] / ref["saturation"]["p99_s"]}
+            for lr, lp in zip([x for x in ref["loads"] if "offered_per_s" in x], plain["loads"]):
+                cmp[f"p99_ratio_at_{lr['offered_frac']:g}"] = lp["p99_s"] / lr["p99_s"]
+            cmp["refined_wins"] = bool(cmp["solves_per_s_ratio"] > 1 and all(
+                v > 1 for k, v in cmp.items() if k.startswith("p99_ratio")))
+            out[key]["refined_vs_plain"] = cmp
+    if with_cpu:
+        import oracle
+        checks = {}
+        t0 = time.perf_counter()
+        for tol, kept in solutions.items():
+            rels = [oracle.residual_norm(u, si.LAPLACE7, 1, rhss[i]) / oracle.interior_norm(rhss[i], 1)
+                    for i, u in kept.items()]
+            checks[f"tol_{tol:g}"] = {"requests": sorted(kept), "max_rel_res": max(rels),
+                                      "all_within_tol": bool(max(rels) <= tol)}
+        t_chk = time.perf_counter() - t0
+        # oracle timing sample: the plain C oracle's sweep rate on the median-size request
+        i_med = int(np.argsort(pts)[n // 2])
+        nx, ny, nz = sizes[i_med]
+        t0 = time.perf_counter()
+        oracle.stencil_sweep(rhss[i_med], si.LAPLACE7, 1, 200)
+        t = time.perf_counter() - t0
+        rate = float(nx) * ny * nz * 200 / t
+        out["cpu_baseline"] = {"value": rate / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+                               "sample": f"200 sweeps of request {i_med} ({nx}x{ny}x{nz}, the median size), plain C "
+                                         f"oracle, one thread ({t:.2f} s); the solves themselves would take hours",
+                               "oracle_check": checks, "oracle_check_s": t_chk,
+                               "what": "the oracle's own FP64 residual ||S u + b - u|| / ||b|| of served solutions "
+                                       "(every 40th request and the largest, from the saturation runs)"}
+    return out
+
+
+def run_extras(args, dev):
+    import paper_2409_18824_gb300 as stn
+    deadline = time.perf_counter() + args.extras_budget
+    with_cpu = not args.no_cpu_baseline
+    out = {}
+    for key, fn in (("c1", lambda: extra_c1(stn, dev, with_cpu)),
+                    ("batched_refined", lambda: extra_batched(stn, dev, True, with_cpu)),
+                    ("batched_f64", lambda: extra_batched(stn, dev, False, with_cpu)),
+                    ("serving", lambda: extra_serving(stn, dev, deadline, with_cpu))):
+        if time.perf_counter() > deadline:
+            out[key] = {"skipped": "time budget"}
+            continue
+        t0 = time.perf_counter()
+        try:
+            out[key] = fn()
+        except Exception as e:  # recorded, never costs the headline line
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+        out[key]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 # ------------------------------------------------------------ oracle (CPU) --
 def cpu_sample(wl, sweeps, keep=False):
     import oracle
@@ -1505,6 +1860,10 @@ def main():
                     help="sweeps fused per HBM pass (0 automatic, 1 off, 2..4)")
     ap.add_argument("--autotune", action="store_true",
                     help="sweep workloads: run the sweep autotuner on the workload's extents before timing")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the 64^3, batched and serving parts of the line")
+    ap.add_argument("--extras-budget", type=float, default=1020.0,
+                    help="wall-clock seconds for the 64^3, batched and serving parts of the default line")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="run only this many single-sweep launches (for profilers), print nothing")
     args = ap.parse_args()

@@ -122,3 +122,13 @@ def test_reference_arms_that_cannot_run_say_why(workload):
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
     assert d["impl"] == "reference" and "oracle" in d["unavailable"]
+
+
+def test_lindley_single_server_fifo():
+    """The plain per-request path serves one request at a time in arrival
+    order: start = max(arrival, previous finish)."""
+    import bench
+    assert bench.lindley([0.0, 0.0, 0.0], [1.0, 2.0, 3.0]) == [1.0, 3.0, 6.0]   # all at once: queue
+    assert bench.lindley([0.0, 10.0, 11.0], [1.0, 1.0, 1.0]) == [1.0, 1.0, 1.0]  # idle between arrivals
+    assert bench.lindley([0.0, 0.5, 4.0], [1.0, 1.0, 1.0]) == [1.0, 1.5, 1.0]
+    assert bench.lindley([], []) == []

@@ -154,3 +154,21 @@ def test_serving_survives_injected_admission_failures(lib, cuda, engine):
     finally:
         lib.stencil_tune_set("fault_admit_fail", 0)
     assert lib.stencil_tune_get("fault_admit_failed") - before == 5
+
+
+def test_plain_solve_continued_equals_direct(lib, cuda):
+    """The bench's plain per-request path solves to 1e-8, copies out, and
+    continues from that iterate to 1e-10: groups of check_every sweeps start
+    at the same sweeps as in a direct solve to 1e-10, so the continued solve
+    ends at the same iterate, bit for bit, after the same number of sweeps."""
+    import torch
+    for i, b in enumerate(requests(3, seed=81, lo=12, hi=30)):
+        d_b = torch.from_numpy(b).cuda()
+        u1 = torch.zeros_like(d_b)
+        rc1, i1 = lib.jacobi_solve_f64(d_b, u1, L7, 1, 1e-8, 10 ** 7, 50)
+        rc2, i2 = lib.jacobi_solve_f64(d_b, u1, L7, 1, 1e-10, 10 ** 7, 50)
+        u3 = torch.zeros_like(d_b)
+        rc3, i3 = lib.jacobi_solve_f64(d_b, u3, L7, 1, 1e-10, 10 ** 7, 50)
+        assert rc1 == rc2 == rc3 == 0
+        assert i1["iters"] + i2["iters"] == i3["iters"], (i1, i2, i3)
+        assert bitwise(u1.cpu().numpy(), u3.cpu().numpy()), i
