@@ -125,12 +125,16 @@ int stencil_release_workspace(void);
  *                   refined solver's inner sweeps) run as a CUDA graph whose
  *                   while node repeats 16 sweeps on the device; 0: one stream
  *                   launch per sweep.  Same kernels, same results.
+ *   "var_chunks":   k chunks per tile column of the TMA-staged variable-
+ *                   coefficient sweep (0 = planned: about six waves of
+ *                   blocks).  Changes the grid, never the results.
  *   "refined_engine": jacobi_solve_refined_f64: 1 (default) full-grid kernels
  *                   per step; 0 a batch of one in the persistent scheduler.
  *   "var_variant":  variable-coefficient kernels: -1 automatic (default: float
  *                   radius-2 sweeps on grids whose padded rows are a multiple
- *                   of 16 bytes, with u and a 16-byte and f and out 8-byte
- *                   aligned, take the TMA-staged kernel; everything else the
+ *                   of 16 bytes, with u, a and f 16-byte and out 8-byte
+ *                   aligned, and at least four waves of its blocks, take the
+ *                   TMA-staged kernel; everything else the
  *                   register/shuffle column kernel that computes each face
  *                   coefficient once), 0 the shared-memory plane kernel, 1
  *                   column, 2 TMA-staged where it applies (column elsewhere).
@@ -560,7 +564,7 @@ int varcoef_apply_f64(const double* u, const double* a, double* out, int64_t nx,
  * (in's interior clobbered when iters > 1).  _f32 takes float a, f, grids;
  * weights rounded to float.  Float sweeps of radius 2 whose padded rows are
  * a multiple of 16 bytes (nx + 4 divisible by 4), with 16-byte-aligned in,
- * out (both serve as u) and a and an 8-byte-aligned f, stage their tiles
+ * out (both serve as u), a and f, stage their tiles
  * through shared memory by tensor-map copies (TMA); the results are the same
  * bits as every other variant.  Their device-side waits are bounded: a wait
  * that gave up (never expected) stops that sweep early and is reported as

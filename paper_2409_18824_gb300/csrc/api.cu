@@ -1234,6 +1234,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_refined_engine((int)value) != STN_OK) return einval("refined_engine must be 0 or 1");
     return STN_OK;
   }
+  if (strcmp(knob, "var_chunks") == 0) {
+    if (tune_set_var_chunks((int)value) != STN_OK) return einval("var_chunks must be in [0, 65535]");
+    return STN_OK;
+  }
   SchedFaults& f = sched_faults();
   if (strcmp(knob, "fault_withhold_last") == 0) {
     if (value < 0 || value > 1) return einval("fault_withhold_last must be 0 or 1");
@@ -1306,6 +1310,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "refined_engine") == 0) {
     *value = tune_get_refined_engine();
+    return STN_OK;
+  }
+  if (strcmp(knob, "var_chunks") == 0) {
+    *value = tune_get_var_chunks();
     return STN_OK;
   }
   const SchedFaults& f = sched_faults();

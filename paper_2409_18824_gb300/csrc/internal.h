@@ -269,6 +269,9 @@ ZPlan plan_var(const Grid& g, size_t esize);
 // Variable-coefficient kernel choice: -1 automatic (column), 0 plane, 1 column.
 int tune_set_var_variant(int v);
 int tune_get_var_variant();
+// k chunks per tile column of the TMA-staged variable-coefficient sweep (0 = planned).
+int tune_set_var_chunks(int v);
+int tune_get_var_chunks();
 // kVarRefine writes rho = f - A u (double) into out's interior and per-block
 // partial sums of rho^2 / maxima of |rho| into partials / partials_max.
 template <typename T>
@@ -276,7 +279,7 @@ int launch_var(const T* u, const T* a, const T* f, T* out, const Grid& g, const 
                VarMode mode, double* partials, double* partials_max, cudaStream_t s);
 
 // TMA-staged float sweep of radius 2 (varcoef_tma.cu): applicable when the
-// rows are a multiple of 16 bytes and u, a are 16-byte and f, out 8-byte
+// rows are a multiple of 16 bytes and u, a, f are 16-byte and out 8-byte
 // aligned (NULL pointers: not checked, for planning).
 bool var_tma_applicable(const Grid& g, size_t esize, const void* u, const void* a, const void* f,
                         const void* out);

@@ -434,6 +434,14 @@ int tune_set_var_variant(int v) {
 }
 int tune_get_var_variant() { return g_var_variant; }
 
+static std::atomic<int> g_var_chunks{0};  // k chunks of the TMA-staged sweep (0 = planned)
+int tune_set_var_chunks(int v) {
+  if (v < 0 || v > 65535) return STN_EINVAL;
+  g_var_chunks = v;
+  return STN_OK;
+}
+int tune_get_var_chunks() { return g_var_chunks.load(); }
+
 static bool var_use_column(const Grid& g, size_t esize) {
   // 32-bit row offsets: TJ + 2R rows of NX elements
   const int tj = esize == 4 ? VarColTJ<float>::value : VarColTJ<double>::value;
@@ -488,7 +496,7 @@ LaunchPlan var_launch_plan(const Grid& g, size_t esize) {
     q.grid_y = p.tiles_y;
     q.grid_z = p.chunks;
     q.kchunk = p.kchunk;
-    q.block_threads = 256;
+    q.block_threads = 288;  // 8 consumer warps and the producer warp
     q.tile_w = 64;
     q.tile_h = p.rg;
     q.smem = p.smem;

@@ -11,9 +11,12 @@
 // Layout of the work:
 //   * a block owns a tile of VT_TW x VT_TH interior (i, j) columns and streams
 //     a chunk of k planes through a ring of VT_S shared-memory stages;
-//   * one thread issues, per plane, two tiled bulk tensor copies
-//     (cp.async.bulk.tensor.3d) of the tile plus its radius-2 halo, one of u
-//     and one of a, completing on the stage's mbarrier.  The tensor maps
+//   * a producer warp (one lane) issues, per plane, three tiled bulk tensor
+//     copies (cp.async.bulk.tensor.3d) of the tile plus its radius-2 halo, of
+//     u, a and f, completing on the stage's "full" mbarrier; consumer warps
+//     wait on it themselves and each releases the stage with one arrive on
+//     its "empty" mbarrier, which the producer waits on before refilling it,
+//     so no block-wide barrier separates the planes.  The tensor maps
 //     describe the padded Fortran grid directly (rows of NX elements), which
 //     needs NX * 4 bytes to be a multiple of 16; the box starts R columns
 //     left of the tile, i.e. at a multiple of 64 elements, so every copy
@@ -27,10 +30,12 @@
 //     loop is unrolled by the queue length, so the queue rotates by renaming;
 //   * x and y faces are computed once per face for the thread's points (a
 //     face between two of its points serves both); z faces per point.
-//   * f is read and the result stored with plain 8-byte global accesses.
-// Every wait on an mbarrier is bounded: after about two seconds the block
-// records kVarTmaTimeout in a status word the host reads, stops streaming,
-// waits (again bounded) for its copies in flight, and returns.
+//   * f is read from the stage; the result is stored with plain 8-byte global
+//     stores.
+// Every wait on an mbarrier is bounded: after about two seconds (or once
+// another thread of the block gave up) the thread records kVarTmaTimeout in a
+// status word the host reads and stops; the producer then waits (again
+// bounded) for its copies in flight and the block returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -46,18 +51,19 @@ namespace {
 
 constexpr int VT_R = 2;
 constexpr int VT_TW = 64;   // interior columns per block (32 lanes x 2)
-constexpr int VT_TH = 16;   // interior rows per block (8 warps x 2)
-constexpr int VT_THREADS = 256;
-constexpr int VT_S = 6;     // ring stages: planes k .. k+2 in use, three in flight
+constexpr int VT_TH = 16;   // interior rows per block (8 consumer warps x 2)
+constexpr int VT_CWARPS = 8;                       // consumer warps
+constexpr int VT_THREADS = 32 * (VT_CWARPS + 1);   // plus one producer warp
+constexpr int VT_S = 6;     // ring stages
 constexpr int VT_Q = 2 * VT_R + 1;          // register queue: planes k-2 .. k+2
 constexpr int VT_PW = VT_TW + 2 * VT_R;     // box width (68 floats = 272 bytes)
 constexpr int VT_PH = VT_TH + 2 * VT_R;     // box height
 constexpr int VT_BOX = VT_PW * VT_PH;       // floats one copy writes
 constexpr int VT_FIELD = (VT_BOX + 31) & ~31;  // a field's box, rounded to 128 bytes
-constexpr int VT_STAGE = 2 * VT_FIELD;      // u then a
+constexpr int VT_STAGE = 3 * VT_FIELD;      // u, a, f
 constexpr int VT_SMEM = VT_S * VT_STAGE * 4;
 constexpr int VT_SMEM_ALLOC = VT_SMEM + 128;  // slack to start the ring on a 128-byte boundary
-constexpr unsigned VT_TX_BYTES = 2u * VT_BOX * 4u;  // bytes each stage's barrier expects
+constexpr unsigned VT_TX_BYTES = 3u * VT_BOX * 4u;  // bytes each stage's full barrier expects
 constexpr unsigned long long VT_WAIT_NS = 2000000000ull;
 constexpr int kVarTmaTimeout = 1;
 
@@ -81,84 +87,120 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for one phase of the barrier; false when it ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// Bounded wait for one phase of the barrier; false when it ran out, or when
+// another thread of the block has given up (*abort set).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* abort) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (!mbar_try(bar, parity))
-    if (gtimer() - t0 > VT_WAIT_NS) return false;
+    if (*abort || gtimer() - t0 > VT_WAIT_NS) return false;
   return true;
 }
 
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
+// One tiled bulk tensor copy of a (VT_PW x VT_PH x 1) box at (x, y, z) into
+// shared memory at dst, completing on the mbarrier at bar.
+__device__ __forceinline__ void tma_load(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 struct VtW {
   float h1, h2;  // w_d / 2 (exact halving)
 };
 
+// Stage s holds plane p = pfirst + s + VT_S * use: boxes of u, a and f.
+// full[s] completes when the copies of a plane have landed (the producer
+// arrives once with the expected bytes); empty[s] completes when every
+// consumer warp has read the plane for the last time (one arrive per warp),
+// after which the producer refills the stage.  Phase parity of use n is n & 1.
 __global__ void __launch_bounds__(VT_THREADS, 2)
     var_tma_kernel(const __grid_constant__ CUtensorMap tmu, const __grid_constant__ CUtensorMap tma,
-                   const float* __restrict__ f, float* __restrict__ out, int nx, int ny, int nz, int NX,
-                   int NY, int kchunk, VtW hw) {
+                   const __grid_constant__ CUtensorMap tmf, float* __restrict__ out, int nx, int ny, int nz,
+                   int NX, int NY, int kchunk, VtW hw) {
   using A = Arith<float>;
   constexpr int R = VT_R;
   extern __shared__ __align__(16) unsigned char vt_dyn[];
-  __shared__ __align__(8) unsigned long long bars[VT_S];
+  __shared__ __align__(8) unsigned long long full[VT_S], empty[VT_S];
+  __shared__ int abort_flag;
   // the ring starts on a 128-byte boundary (the launch adds 128 bytes of slack)
   float* const vt_ring = reinterpret_cast<float*>(
       vt_dyn + ((128u - ((unsigned)__cvta_generic_to_shared(vt_dyn) & 127u)) & 127u));
-  const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+  const int tid = threadIdx.x, lx = tid & 31, wid = tid >> 5;
   const int tx0 = blockIdx.x * VT_TW, ty0 = blockIdx.y * VT_TH;  // tile origin (interior offsets)
   const int k0 = R + blockIdx.z * kchunk;
   const int k1 = min(k0 + kchunk, nz + R);
   const int pfirst = k0 - R, plast = k1 - 1 + R;
   const unsigned ring_s = (unsigned)__cvta_generic_to_shared(vt_ring);
-  const unsigned bar_s = (unsigned)__cvta_generic_to_shared(bars);
+  const unsigned full_s = (unsigned)__cvta_generic_to_shared(full);
+  const unsigned empty_s = (unsigned)__cvta_generic_to_shared(empty);
   if (tid == 0) {
-    for (int s = 0; s < VT_S; s++)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
+    for (int s = 0; s < VT_S; s++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_s + 8u * s) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty_s + 8u * s), "r"(VT_CWARPS) : "memory");
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-
-  // plane p sits in stage (p - pfirst) % VT_S, use (p - pfirst) / VT_S of it
-  int next_issue = pfirst;
-  auto issue = [&](int p) {  // thread 0 only
-    const int s = (p - pfirst) % VT_S;
-    const unsigned bar = bar_s + 8u * s;
-    const unsigned dst = ring_s + (unsigned)(s * VT_STAGE * 4);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(VT_TX_BYTES)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(&tmu)), "r"(tx0), "r"(ty0), "r"(p), "r"(bar)
-        : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst + VT_FIELD * 4u),
-        "l"(reinterpret_cast<unsigned long long>(&tma)), "r"(tx0), "r"(ty0), "r"(p), "r"(bar)
-        : "memory");
+  const volatile int* abortp = &abort_flag;
+  auto give_up = [&]() {
+    abort_flag = 1;
+    atomicExch(&g_var_tma_status, kVarTmaTimeout);
   };
-  // thread 0 waits for plane p, then the block barrier publishes it
-  auto wait_plane = [&](int p) -> bool {
-    const int s = (p - pfirst) % VT_S;
-    return mbar_wait(bar_s + 8u * s, (unsigned)(((p - pfirst) / VT_S) & 1));
-  };
-  if (tid == 0)
-    while (next_issue <= plast && next_issue < pfirst + VT_S) issue(next_issue++);
 
-  // this thread's points: padded columns gi, gi+1 and rows gj, gj+1
-  const int c = 2 * lx + R, rr = 2 * ly + R;  // box column / row of its first point
+  if (wid == VT_CWARPS) {
+    // ---- producer warp: one lane issues every plane's copies in order ------
+    if (lx == 0) {
+      int p = pfirst;
+      for (; p <= plast; p++) {
+        const int s = (p - pfirst) % VT_S, use = (p - pfirst) / VT_S;
+        if (use > 0 && !mbar_wait(empty_s + 8u * s, (unsigned)((use - 1) & 1), abortp)) {
+          give_up();
+          break;
+        }
+        const unsigned bar = full_s + 8u * s;
+        const unsigned dst = ring_s + (unsigned)(s * VT_STAGE * 4);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(VT_TX_BYTES)
+                     : "memory");
+        tma_load(dst, &tmu, tx0, ty0, p, bar);
+        tma_load(dst + VT_FIELD * 4u, &tma, tx0, ty0, p, bar);
+        tma_load(dst + 2u * VT_FIELD * 4u, &tmf, tx0, ty0, p, bar);
+      }
+      // leave no copy in flight: wait (bounded) for the last VT_S planes issued
+      for (int q = max(pfirst, p - VT_S); q < p; q++) {
+        const int s = (q - pfirst) % VT_S;
+        (void)mbar_wait(full_s + 8u * s, (unsigned)(((q - pfirst) / VT_S) & 1), abortp);
+      }
+    }
+    return;
+  }
+
+  // ---- consumer warps ---------------------------------------------------------
+  const int ly = wid;
+  const int c = 2 * lx + R, rr = 2 * ly + R;  // box column / row of the thread's first point
   const int gi = tx0 + c, gj = ty0 + rr;
   const bool col0 = gi < nx + R, col1 = gi + 1 < nx + R;
   const bool row0 = gj < ny + R, row1 = gj + 1 < ny + R;
   const i64 psz = (i64)NX * NY;
-  const float* fb = f + (i64)gj * NX + gi;
   float* ob = out + (i64)gj * NX + gi;
 
   auto stage_u = [&](int p) -> const float* { return vt_ring + ((p - pfirst) % VT_S) * VT_STAGE; };
+  // every lane waits; the answer is the warp's (all lanes go on or none)
+  auto wait_full = [&](int p) -> bool {
+    const int s = (p - pfirst) % VT_S;
+    const bool ok = mbar_wait(full_s + 8u * s, (unsigned)(((p - pfirst) / VT_S) & 1), abortp);
+    return __all_sync(0xffffffffu, ok);
+  };
+  auto release = [&](int p) {  // this warp has read plane p for the last time
+    __syncwarp();
+    if (lx == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty_s + 8u * ((p - pfirst) % VT_S)) : "memory");
+  };
 
   // queue: planes by slot (p - pfirst) % VT_Q, rows 0 / 1, columns in .x / .y
   float2 qu[VT_Q][2], qa[VT_Q][2];
@@ -172,58 +214,47 @@ __global__ void __launch_bounds__(VT_THREADS, 2)
     }
   };
 
-  // prologue: planes pfirst .. pfirst + 3 (k0 - 2 .. k0 + 1) into the queue
-  bool ok = true;
-  if (tid == 0)
-    for (int p = pfirst; p < pfirst + 2 * R && p <= plast; p++) ok = ok && wait_plane(p);
-  bool stop = __syncthreads_or(tid == 0 && !ok) != 0;  // one answer for the whole block
-  if (!stop) {
+  // prologue: planes k0 - 2 .. k0 + 1 into the queue (k0 - 2 and k0 - 1 are
+  // not read again)
+  bool stop = false;
 #pragma unroll
-    for (int m = 0; m < 2 * R; m++)
-      if (pfirst + m <= plast) fill(m, pfirst + m);
+  for (int m = 0; m < 2 * R; m++) {
+    if (!stop && !wait_full(pfirst + m)) {
+      give_up();
+      stop = true;
+    }
+    if (!stop) fill(m, pfirst + m);
   }
-  float2 fq[2];
-  fq[0] = make_float2(0.f, 0.f);
-  fq[1] = fq[0];
-  if (!stop && k0 < k1) {
-    if (row0 && col0) fq[0] = ld2(fb + (i64)k0 * psz);
-    if (row1 && col0) fq[1] = ld2(fb + (i64)k0 * psz + NX);
+  if (!stop) {
+    release(pfirst);
+    release(pfirst + 1);
   }
 
   for (int kb = k0; kb < k1 && !stop; kb += VT_Q) {
 #pragma unroll
     for (int J = 0; J < VT_Q; J++) {
       const int k = kb + J;
-      if (k >= k1 || stop) break;
-      // plane k + 2 into the queue; every stage of planes < k is free again
-      bool got = true;
-      if (tid == 0) got = wait_plane(k + R);
-      if (__syncthreads_or(tid == 0 && !got)) {
+      if (k >= k1) break;
+      if (!wait_full(k + R)) {
+        give_up();
         stop = true;
         break;
       }
-      if (tid == 0)
-        while (next_issue <= plast && next_issue < k + VT_S) issue(next_issue++);
       // slots of planes k + d: (k - pfirst + d) % VT_Q = (J + R + d) % VT_Q,
       // since k - pfirst = (kb - k0) + J + R and kb - k0 is a multiple of VT_Q
       fill((J + 2 * R) % VT_Q, k + R);
-      // f of the next plane, loaded ahead
-      float2 fn[2];
-      fn[0] = make_float2(0.f, 0.f);
-      fn[1] = fn[0];
-      if (k + 1 < k1) {
-        if (row0 && col0) fn[0] = ld2(fb + (i64)(k + 1) * psz);
-        if (row1 && col0) fn[1] = ld2(fb + (i64)(k + 1) * psz + NX);
-      }
       const float* su = stage_u(k);
       const float* sa = su + VT_FIELD;
+      const float* sf = sa + VT_FIELD;
       // in-plane values: X[t][0..5] = columns c-2 .. c+3 of own row t,
       // Y[q][0..5] = rows rr-2 .. rr+3 of own column q
       float XU[2][6], XA[2][6], YU[2][6], YA[2][6];
+      float2 fq[2];
 #pragma unroll
       for (int t = 0; t < 2; t++) {
         const float2 l = ld2(su + (rr + t) * VT_PW + c - 2), r = ld2(su + (rr + t) * VT_PW + c + 2);
         const float2 la = ld2(sa + (rr + t) * VT_PW + c - 2), ra = ld2(sa + (rr + t) * VT_PW + c + 2);
+        fq[t] = ld2(sf + (rr + t) * VT_PW + c);
         const float2 cu = qu[(J + R) % VT_Q][t], ca = qa[(J + R) % VT_Q][t];
         XU[t][0] = l.x; XU[t][1] = l.y; XU[t][2] = cu.x; XU[t][3] = cu.y; XU[t][4] = r.x; XU[t][5] = r.y;
         XA[t][0] = la.x; XA[t][1] = la.y; XA[t][2] = ca.x; XA[t][3] = ca.y; XA[t][4] = ra.x; XA[t][5] = ra.y;
@@ -243,6 +274,7 @@ __global__ void __launch_bounds__(VT_THREADS, 2)
           YA[q][2] = XA[0][2 + q]; YA[q][3] = XA[1][2 + q];
         }
       }
+      release(k);  // plane k's stage is no longer read by this warp
       // faces along a line of six values v[0..5] (own points at 2, 3):
       // F1[m] = face (m+1, m+2) for d = 1, m = 0..2; F2[m] = face (m, m+2) for d = 2, m = 0..3
       float FX1[2][3], FX2[2][4], FY1[2][3], FY2[2][4];
@@ -278,6 +310,8 @@ __global__ void __launch_bounds__(VT_THREADS, 2)
             const float typ = d == 1 ? FY1[q][t + 1] : FY2[q][t + 2];
             const float2 am = qa[(J + R - d) % VT_Q][t], apl = qa[(J + R + d) % VT_Q][t];
             const float2 um = qu[(J + R - d) % VT_Q][t], upl = qu[(J + R + d) % VT_Q][t];
+            // z faces per point (carrying plus faces to the next planes costs
+            // registers that halve the blocks per SM)
             const float tzm = A::mul(h, A::add(ap, q == 0 ? am.x : am.y));
             const float tzp = A::mul(h, A::add(ap, q == 0 ? apl.x : apl.y));
             D = A::add(D, txm);
@@ -306,16 +340,7 @@ __global__ void __launch_bounds__(VT_THREADS, 2)
         else if (rowok && col0)
           ob[po + t * NX] = res[t][0];
       }
-      fq[0] = fn[0];
-      fq[1] = fn[1];
     }
-  }
-  // On a clean exit every plane issued was waited for.  After a wait ran out,
-  // thread 0 waits (bounded) for the copies that may still be in flight, the
-  // last VT_S issued, before the block's shared memory goes away.
-  if (tid == 0 && stop) {
-    for (int p = max(pfirst, next_issue - VT_S); p < next_issue; p++) (void)wait_plane(p);
-    atomicExch(&g_var_tma_status, kVarTmaTimeout);
   }
 }
 
@@ -381,7 +406,7 @@ bool var_tma_applicable(const Grid& g, size_t esize, const void* u, const void* 
   if (g.NX() > ((i64)1 << 31) || g.NY() > ((i64)1 << 31) || g.NZ() > ((i64)1 << 31)) return false;
   if ((i64)g.NX() * g.NY() * 4 >= ((i64)1 << 40)) return false;  // plane stride limit of a tensor map
   auto al = [](const void* p, uintptr_t m) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & (m - 1)) == 0; };
-  return al(u, 16) && al(a, 16) && al(f, 8) && al(out, 8);
+  return al(u, 16) && al(a, 16) && al(f, 16) && al(out, 8);
 }
 
 ZPlan plan_var_tma(const Grid& g) {
@@ -391,8 +416,12 @@ ZPlan plan_var_tma(const Grid& g) {
   p.tiles_y = (int)((g.ny + VT_TH - 1) / VT_TH);
   const i64 tiles = (i64)p.tiles_x * p.tiles_y;
   const i64 slots = (i64)device_sms() * vt_resident();
-  // about six waves of blocks, chunks of at least 16 planes
-  i64 chunks = (6 * slots + tiles - 1) / tiles;
+  // about twelve waves of blocks, chunks of at least 16 planes (a knob may set
+  // the chunk count).  Measured at 768 x 768 x 384 (576 tiles, 304 slots),
+  // GLUP/s for 2 / 3 / 4 / 6 / 8 / 12 / 16 / 24 chunks: 290 / 291 / 292 / 301 /
+  // 301 / 300 / 296 / 286
+  i64 chunks = (12 * slots + tiles / 2) / tiles;
+  if (const int kc = tune_get_var_chunks(); kc > 0) chunks = kc;
   const i64 max_chunks = (g.nz + 15) / 16;
   if (chunks > max_chunks) chunks = max_chunks;
   if (chunks < 1) chunks = 1;
@@ -407,9 +436,10 @@ int launch_var_tma(const float* u, const float* a, const float* f, float* out, c
                    cudaStream_t s) {
   const ZPlan p = plan_var_tma(g);
   if (int rc = check_launch_grid(p.tiles_x, p.tiles_y, p.chunks)) return rc;
-  CUtensorMap mu, ma;
+  CUtensorMap mu, ma, mf;
   if (int rc = encode(&mu, u, g)) return rc;
   if (int rc = encode(&ma, a, g)) return rc;
+  if (int rc = encode(&mf, f, g)) return rc;
   static std::atomic<bool> attr_set[64];
   int dev = 0;
   STN_CUDA_TRY(cudaGetDevice(&dev));
@@ -419,7 +449,7 @@ int launch_var_tma(const float* u, const float* a, const float* f, float* out, c
   }
   VtW hw{(float)(0.5 * w[1]), (float)(0.5 * w[2])};
   dim3 grid(p.tiles_x, p.tiles_y, p.chunks);
-  var_tma_kernel<<<grid, VT_THREADS, VT_SMEM_ALLOC, s>>>(mu, ma, f, out, (int)g.nx, (int)g.ny, (int)g.nz,
+  var_tma_kernel<<<grid, VT_THREADS, VT_SMEM_ALLOC, s>>>(mu, ma, mf, out, (int)g.nx, (int)g.ny, (int)g.nz,
                                                          (int)g.NX(), (int)g.NY(), p.kchunk, hw);
   STN_CUDA_TRY(cudaGetLastError());
   return STN_OK;

@@ -98,7 +98,7 @@ def test_varcoef_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r):
     if q["variant"] == 2:
         # TMA-staged: float, radius 2, rows a multiple of 16 bytes
         assert esize == 4 and r == 2 and ((nx + 2 * r) * 4) % 16 == 0
-        assert (q["tile_w"], q["tile_h"], q["block_threads"]) == (64, 16, 256)
+        assert (q["tile_w"], q["tile_h"], q["block_threads"]) == (64, 16, 288)
         assert q["smem_bytes"] == VT_SMEM_ALLOC and q["stage_elems"] == 0
         assert q["grid_z"] <= ceil_div(nz, 16)
         return
@@ -116,19 +116,23 @@ def test_varcoef_plan_covers_the_grid_within_limits(lib, nx, ny, nz, esize, r):
 
 
 # the TMA-staged variable-coefficient float sweep (radius 2)
-VT_TW, VT_TH, VT_R, VT_S, VT_Q = 64, 16, 2, 6, 5
+VT_TW, VT_TH, VT_R, VT_S, VT_Q, VT_CWARPS = 64, 16, 2, 6, 5, 8
 VT_PW, VT_PH = VT_TW + 2 * VT_R, VT_TH + 2 * VT_R
 VT_FIELD = -(-(VT_PW * VT_PH) // 32) * 32
-VT_SMEM_ALLOC = VT_S * 2 * VT_FIELD * 4 + 128
+VT_SMEM_ALLOC = VT_S * 3 * VT_FIELD * 4 + 128
 
 
 def tma_block_replay(nx, ny, nz, bx, by, bz, kchunk):
     """Replays one block of the TMA-staged kernel: the tensor-map box origin of
-    every plane it stages (x a multiple of 16 bytes, z inside the grid), the
-    ring's issue and wait order (a plane is issued before it is waited for and
-    never into a stage whose plane is still in use), every shared-memory
-    element the threads read (inside the box and the stage), and every global
-    f load and out store (inside the interior, on 8-byte boundaries)."""
+    every plane it stages (x a multiple of 16 bytes, z inside the grid); the
+    producer/consumer protocol of its ring (the producer puts plane p into
+    stage (p - pfirst) % S once every consumer warp has released plane p - S;
+    consumers wait for a plane's copies before reading it and release it after
+    its last read), run as a simulation in which the producer issues as early
+    as the protocol lets it: every read must find its own plane in the stage
+    and the simulation must never stall; and every shared-memory element and
+    global store of the threads (inside the box, inside the interior, on
+    8-byte boundaries)."""
     R = VT_R
     NX, NY, NZ = nx + 2 * R, ny + 2 * R, nz + 2 * R
     tx0, ty0 = bx * VT_TW, by * VT_TH
@@ -138,39 +142,36 @@ def tma_block_replay(nx, ny, nz, bx, by, bz, kchunk):
     pfirst, plast = k0 - R, k1 - 1 + R
     assert (tx0 * 4) % 16 == 0 and tx0 < NX and ty0 < NY
     assert 0 <= pfirst and plast <= NZ - 1
-    assert VT_S * 2 * VT_FIELD * 4 + 128 <= SMEM_PER_BLOCK_MAX
-    issued, waited, in_use = [], set(), {}
-    nxt = pfirst
+    assert VT_SMEM_ALLOC <= SMEM_PER_BLOCK_MAX
+    stage = {}          # stage -> plane it holds (issued)
+    released = set()
+    issued = []
 
-    def issue_upto(limit):
-        nonlocal nxt
-        while nxt <= plast and nxt < limit:
-            s = (nxt - pfirst) % VT_S
-            prev = in_use.get(s)
-            assert prev is None or prev in waited, (nxt, prev)
-            in_use[s] = nxt
-            issued.append(nxt)
-            nxt += 1
+    def produce():
+        # the producer issues every plane the protocol allows now
+        while len(issued) < plast - pfirst + 1:
+            p = pfirst + len(issued)
+            if p - VT_S >= pfirst and (p - VT_S) not in released:
+                return
+            stage[(p - pfirst) % VT_S] = p
+            issued.append(p)
 
-    def wait(p):
-        assert p in issued and p not in waited, p
-        waited.add(p)
+    def read(p):
+        produce()
+        assert p in issued, ("would wait forever for plane", p)
+        assert stage[(p - pfirst) % VT_S] == p, ("stage overwritten before its last read", p)
 
-    issue_upto(pfirst + VT_S)
-    for p in range(pfirst, pfirst + 2 * R):
-        wait(p)
-    live = set(range(pfirst, pfirst + 2 * R))  # planes read so far and not yet released
+    for p in range(pfirst, pfirst + 2 * R):   # prologue: queue fill
+        read(p)
+    released |= {pfirst, pfirst + 1}
     for k in range(k0, k1):
-        wait(k + R)
-        # after the barrier: planes < k are no longer read by anyone
-        live = {p for p in live if p >= k}
-        issue_upto(k + VT_S)
-        for p in live | {k, k + R}:
-            assert in_use[(p - pfirst) % VT_S] == p, (k, p)  # its stage still holds it
-        live |= {k, k + R}
-    assert waited == set(issued) == set(range(pfirst, plast + 1))
-    # shared-memory reads and global accesses of every thread
-    for tid in range(256):
+        read(k + R)      # queue fill of plane k + 2
+        read(k)          # in-plane neighbours, f
+        released.add(k)  # the warps' last read of plane k
+    produce()
+    assert issued == list(range(pfirst, plast + 1))
+    # shared-memory reads and global accesses of every consumer thread
+    for tid in range(32 * VT_CWARPS):
         lx, ly = tid & 31, tid >> 5
         c, rr = 2 * lx + R, 2 * ly + R
         for col in (c - 2, c, c + 2):      # 8-byte loads: columns col, col + 1
@@ -182,7 +183,7 @@ def tma_block_replay(nx, ny, nz, bx, by, bz, kchunk):
             if gj + t < ny + R and gi < nx + R:
                 for k in range(k0, k1):
                     off = (k * NY + gj + t) * NX + gi
-                    assert off % 2 == 0  # 8-byte f loads / out stores
+                    assert off % 2 == 0  # 8-byte out stores
                     assert R <= gj + t < ny + R and R <= gi and gi + 1 <= nx + R < NX
 
 
