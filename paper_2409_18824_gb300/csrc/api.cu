@@ -265,6 +265,35 @@ int tune_set_repeat_graph(int v) {
 int tune_get_repeat_graph() { return g_repeat_graph; }
 
 // --------------------------------------------------------------- drivers --
+// Resident launches on a stream keep their barrier words in workspace scalar
+// 44 and their status word in scalar 6 (low 32 bits), so the synchronising
+// calls that read scalars 0..6 see a timeout of an earlier resident sweep on
+// the same stream and report it once.
+static unsigned* resident_bar(Workspace* ws) { return reinterpret_cast<unsigned*>(ws->scalars + 44); }
+static int* resident_status(Workspace* ws) { return reinterpret_cast<int*>(ws->scalars + 6); }
+static int take_resident_status(Workspace* ws, cudaStream_t s) {
+  int v = 0;
+  memcpy(&v, ws->host_scalars + 6, sizeof(int));
+  if (v == 0) return STN_OK;
+  STN_CUDA_TRY(cudaMemsetAsync(ws->scalars + 6, 0, sizeof(double), s));
+  STN_CUDA_TRY(cudaStreamSynchronize(s));
+  ws->host_scalars[6] = 0.0;
+  set_error("a resident sweep gave up waiting at a grid barrier");
+  return STN_ETIMEOUT;
+}
+
+// The resident path runs only where nothing asks for a particular per-sweep
+// kernel: no forced variant or chunk count (knob or autotuner trial) and no
+// tuning-cache entry for the grid.
+static bool resident_allowed(const Grid& g, size_t esize) {
+  if (!resident3d_applicable(g, esize)) return false;
+  if (star_force().variant >= 0 || star_force().chunks > 0 || tune_get_star_variant() >= 0 ||
+      tune_get_star_chunks() > 0)
+    return false;
+  StarChoice tc;
+  return !tune_cache_lookup(g, esize, &tc);
+}
+
 template <typename T>
 static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeffs, int radius,
                       i64 iters, void* stream) {
@@ -304,7 +333,17 @@ static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeff
       std::swap(cur, nxt);
     }
   }
-  if (depth <= 1 && use_repeat_graph(g, iters)) {
+  if (depth <= 1 && iters >= 2 && resident_allowed(g, sizeof(T))) {
+    // small grids: every sweep in one cooperative launch
+    Workspace* ws;
+    if (int rc = get_workspace(s, 0, 0, &ws)) return rc;
+    if (int rc = launch_star_resident<T>(cur, nxt, nullptr, g, coeffs, iters, false, nullptr, nullptr,
+                                         resident_bar(ws), resident_status(ws), s))
+      return rc;
+    if (iters % 2) std::swap(cur, nxt);
+    it = iters;
+  }
+  if (depth <= 1 && it < iters && use_repeat_graph(g, iters)) {
     Workspace* ws;
     if (int rc = get_workspace(s, 0, 0, &ws)) return rc;
     const i64 reps = iters / kRepeatBody;
@@ -352,6 +391,8 @@ static int read_scalars(Workspace* ws, int first, int n, cudaStream_t s) {
   return STN_OK;
 }
 
+
+
 template <typename T>
 static int residual_impl(const T* u, const T* b, i64 nx, i64 ny, i64 nz, const double* coeffs,
                          int radius, double* norm_out, void* stream) {
@@ -373,7 +414,8 @@ static int residual_impl(const T* u, const T* b, i64 nx, i64 ny, i64 nz, const d
   if (int rc = launch_star<T>(du, db, nullptr, g, coeffs, kResidualOnly, ws->partials, s, ws->partials_cap, &nl))
     return rc;
   if (int rc = launch_finalize(ws->partials, nl, ws->scalars, nullptr, 0.0, s)) return rc;
-  if (int rc = read_scalars(ws, 0, 2, s)) return rc;
+  if (int rc = read_scalars(ws, 0, 7, s)) return rc;
+  if (int rc = take_resident_status(ws, s)) return rc;
   *norm_out = ws->host_scalars[1];
   return st.finish();
 }
@@ -598,10 +640,17 @@ static int graph_groups(T* a, T* bgrid, const T* db, const Grid& g, const double
     T* cur = a;
     T* nxt = bgrid;
     i64 nl = 0;  // partials the group's last (residual) sweep writes
-    for (i64 k = 0; k < group && rc == STN_OK; k++) {
-      rc = launch_star<T>(cur, db, nxt, g, coeffs, k == group - 1 ? kSweepResidual : kSweep, ws->partials, cs,
-                          ws->partials_cap, &nl);
-      std::swap(cur, nxt);
+    if (resident_allowed(g, sizeof(T)) && resident3d_blocks(g) <= ws->partials_cap) {
+      // small grids: the group's sweeps in one cooperative launch
+      rc = launch_star_resident<T>(cur, nxt, db, g, coeffs, group, true, ws->partials, &nl, resident_bar(ws),
+                                   resident_status(ws), cs);
+      if (group % 2) std::swap(cur, nxt);
+    } else {
+      for (i64 k = 0; k < group && rc == STN_OK; k++) {
+        rc = launch_star<T>(cur, db, nxt, g, coeffs, k == group - 1 ? kSweepResidual : kSweep, ws->partials, cs,
+                            ws->partials_cap, &nl);
+        std::swap(cur, nxt);
+      }
     }
     if (rc == STN_OK) rc = launch_decide(ws->partials, nl, dst, tol, group, max_full, h, cs);
     if (rc == STN_OK && cur != a) e = cudaMemcpyAsync(a, cur, bytes, cudaMemcpyDeviceToDevice, cs);
@@ -614,6 +663,8 @@ static int graph_groups(T* a, T* bgrid, const T* db, const Grid& g, const double
     if ((e = cudaMemsetAsync(dst + 5, 0, sizeof(double), s))) break;
     if ((e = cudaGraphLaunch(exec, s))) break;
     if ((rc = read_scalars(ws, first, 6, s))) break;
+    if ((rc = read_scalars(ws, 6, 1, s))) break;
+    if ((rc = take_resident_status(ws, s))) break;
     *it_out = (i64)ws->host_scalars[first + 5];
     *conv_out = ws->host_scalars[first + 3] != 0.0;
   } while (false);
@@ -764,7 +815,8 @@ int solve_refined_core(const double* db, double* du, double* t, float* f32, cons
     if (int rc = launch_finalize(ws->partials, nl, ws->scalars, ws->scalars + 9, tol, s)) return rc;
     if (int rc = launch_diff_max(t, du, g, ws->partials, &nm, s)) return rc;
     if (int rc = launch_max_finalize(ws->partials, nm, ws->scalars + 4, s)) return rc;
-    if (int rc = read_scalars(ws, 0, 5, s)) return rc;
+    if (int rc = read_scalars(ws, 0, 7, s)) return rc;
+    if (int rc = take_resident_status(ws, s)) return rc;  // the previous step's resident sweeps ran whole
     res = ws->host_scalars[1];
     rel = ws->host_scalars[2];
     if (ws->host_scalars[3] != 0.0) {
@@ -806,7 +858,13 @@ int solve_refined_core(const double* db, double* du, double* t, float* f32, cons
         conv = ws->host_scalars[19] != 0.0;
       }
     } else {
-      if (use_repeat_graph(g, inner_sweeps)) {
+      if (inner_sweeps >= 2 && resident_allowed(g, sizeof(float))) {
+        if (int rc = launch_star_resident<float>(cur, nxt, r32, g, coeffs, inner_sweeps, false, nullptr, nullptr,
+                                                 resident_bar(ws), resident_status(ws), s))
+          return rc;
+        if (inner_sweeps % 2) std::swap(cur, nxt);
+        done = inner_sweeps;
+      } else if (use_repeat_graph(g, inner_sweeps)) {
         const i64 reps = inner_sweeps / kRepeatBody;
         int rc = graph_repeat(ws, reps, s, [&](cudaStream_t cs) -> int {
           for (i64 k = 0; k < kRepeatBody; k++)
@@ -1238,6 +1296,14 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_var_chunks((int)value) != STN_OK) return einval("var_chunks must be in [0, 65535]");
     return STN_OK;
   }
+  if (strcmp(knob, "resident3d") == 0) {
+    if (tune_set_resident3d((int)value) != STN_OK) return einval("resident3d must be 0 or 1");
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_withhold_3d") == 0) {
+    if (tune_set_withhold3d((int)value) != STN_OK) return einval("fault_withhold_3d must be 0 or 1");
+    return STN_OK;
+  }
   SchedFaults& f = sched_faults();
   if (strcmp(knob, "fault_withhold_last") == 0) {
     if (value < 0 || value > 1) return einval("fault_withhold_last must be 0 or 1");
@@ -1314,6 +1380,14 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "var_chunks") == 0) {
     *value = tune_get_var_chunks();
+    return STN_OK;
+  }
+  if (strcmp(knob, "resident3d") == 0) {
+    *value = tune_get_resident3d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "fault_withhold_3d") == 0) {
+    *value = tune_get_withhold3d();
     return STN_OK;
   }
   const SchedFaults& f = sched_faults();

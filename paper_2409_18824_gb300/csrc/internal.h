@@ -153,6 +153,27 @@ int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coe
 template <typename T>
 int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s);
 
+// ---- many sweeps of a small grid in one cooperative launch (resident3d.cu) --
+constexpr int kResidentTimeout = 1;
+// Whether the grid is small enough (every interior point one of at most 8
+// per thread of two 512-thread blocks per SM; the sweeps' data stay in L2).
+bool resident3d_applicable(const Grid& g, size_t esize);
+// Blocks (and residual partials) of the resident launch for this grid.
+i64 resident3d_blocks(const Grid& g);
+// `sweeps` sweeps ping-ponging a -> b2 -> a ... (b2's halo must equal a's;
+// the result is in b2 when sweeps is odd), rhs optional; with resid_last the
+// last sweep writes one partial sum of rho^2 per block (*nparts of them).
+// bar: two zero-initialised words the launch resets; status: set to
+// kResidentTimeout when a grid barrier's bounded wait ran out.
+template <typename T>
+int launch_star_resident(T* a, T* b2, const T* rhs, const Grid& g, const double* coeffs, i64 sweeps,
+                         bool resid_last, double* partials, i64* nparts, unsigned* bar, int* status,
+                         cudaStream_t s);
+int tune_set_resident3d(int v);
+int tune_get_resident3d();
+int tune_set_withhold3d(int v);
+int tune_get_withhold3d();
+
 // ---- two-dimensional star stencil (jacobi2d.cu) ------------------------------
 // Padded (ny+2r) x (nx+2r) grid, i fastest.
 struct Grid2 {

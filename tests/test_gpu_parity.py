@@ -283,7 +283,8 @@ def test_host_grids_through_the_abi(lib, cuda):
     """The calls that stage host grids (the path the bench's e2e figures time)
     give the device calls' bits: residual norm, Jacobi solve, and the
     variable-coefficient apply, sweep, residual, solve and refined solve; the
-    constant-coefficient refined solve takes device grids only."""
+    constant-coefficient refined solve's scheduler engine takes device grids
+    only."""
     nx, ny, nz, r = 29, 17, 13, 1
     b = si.normal_interior(nx, ny, nz, r, seed=71)
     u = si.uniform_interior(nx, ny, nz, r, seed=72, lo=-1, hi=1)
@@ -318,9 +319,22 @@ def test_host_grids_through_the_abi(lib, cuda):
         rc_d, info_d = solve(to_dev(a), to_dev(f), ud, W, R, *args)
         assert rc_h == rc_d == 0 and info_h["iters"] == info_d["iters"], (solve, info_h, info_d)
         assert_bitwise(uh, to_host(ud))
-    with pytest.raises(lib.StencilError) as ei:
-        lib.jacobi_solve_refined_f64(b, np.zeros_like(b), L7, r, 1e-8, 100, 0.0, 10, 5)
-    assert ei.value.code == lib.STN_EINVAL
+    # the constant-coefficient refined solve: host grids are staged like the
+    # others on the full-grid engine (the default); the scheduler engine takes
+    # device grids only
+    uh = np.zeros_like(b)
+    rc_h, info_h = lib.jacobi_solve_refined_f64(b, uh, L7, r, 1e-8, 100, 0.0, 10, 5)
+    ud = to_dev(np.zeros_like(b))
+    rc_d, info_d = lib.jacobi_solve_refined_f64(to_dev(b), ud, L7, r, 1e-8, 100, 0.0, 10, 5)
+    assert rc_h == rc_d and info_h["outer"] == info_d["outer"]
+    assert_bitwise(uh, to_host(ud))
+    lib.stencil_tune_set("refined_engine", 0)
+    try:
+        with pytest.raises(lib.StencilError) as ei:
+            lib.jacobi_solve_refined_f64(b, np.zeros_like(b), L7, r, 1e-8, 100, 0.0, 10, 5)
+        assert ei.value.code == lib.STN_EINVAL
+    finally:
+        lib.stencil_tune_set("refined_engine", 1)
 
 
 def test_eigenmode_decay_1000_sweeps_128(lib, cuda):

@@ -47,7 +47,7 @@ CASES = [
     ("vec_reduce_kernel_dot_2e27_full.md", 2 ** 27, bench.TRAFFIC_DOT_PER_PAIR),
     ("sum_kernel_f64_2e27_full.md", 2 ** 27, bench.TRAFFIC_SUM_PER_ELEMENT),
     ("advect_kernel_f64_512x512x256_full.md", 512 * 512 * 256, bench.TRAFFIC_ADVECT_PER_CELL),
-    ("var_col_kernel_f32_512x512x256_full.md", 512 * 512 * 256, bench.TRAFFIC_VARCOEF_F32_PER_LUP),
+    ("var_tma_kernel_f32_512x512x256_full.md", 512 * 512 * 256, bench.TRAFFIC_VARCOEF_F32_PER_LUP),
 ]
 
 
