@@ -161,8 +161,13 @@ int stencil_release_workspace(void);
  *                   host loop that reads the residual every check (0).
  *   "batch_engine": batched solvers: 0 dynamic work-unit scheduler (default:
  *                   any CTA may take any unit of any problem in flight),
- *                   1 one thread-block cluster per problem.
- * Every variant, depth and engine computes bitwise the same iterates.
+ *                   1 one thread-block cluster per problem, 2 a pool of
+ *                   eight worker streams taking the problems largest first,
+ *                   each solved as jacobi_solve_f64 / jacobi_solve_refined_f64
+ *                   solve it alone (full-grid or resident kernels).
+ * Every variant, depth and engine computes bitwise the same iterates (with a
+ * fixed number of inner sweeps, for refined solves; with inner_tol > 0 the
+ * engines' inner stopping sums may round differently).
  * Limits and host-side fault injection (for tests of failure handling; no
  * GPU fault is ever caused):
  *   "sched_idle_ms": batched scheduler idle limit (default 2000 ms); CTAs

@@ -333,7 +333,16 @@ static int sweep_impl(T* in, T* out, i64 nx, i64 ny, i64 nz, const double* coeff
       std::swap(cur, nxt);
     }
   }
-  if (depth <= 1 && iters >= 2 && resident_allowed(g, sizeof(T))) {
+  if constexpr (sizeof(T) == 8) {
+    if (tune_get_double_word() && dw_applicable(g, coeffs, nullptr)) {
+      // opt-in: every sweep in double-word float arithmetic (not bitwise)
+      for (; it < iters; it++) {
+        if (int rc = launch_star_dw(cur, nxt, g, coeffs, s)) return rc;
+        std::swap(cur, nxt);
+      }
+    }
+  }
+  if (depth <= 1 && it < iters && iters >= 2 && resident_allowed(g, sizeof(T))) {
     // small grids: every sweep in one cooperative launch
     Workspace* ws;
     if (int rc = get_workspace(s, 0, 0, &ws)) return rc;
@@ -1281,7 +1290,7 @@ int stencil_tune_set(const char* knob, int64_t value) {
     return STN_OK;
   }
   if (strcmp(knob, "batch_engine") == 0) {
-    if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0 or 1");
+    if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0, 1 or 2");
     return STN_OK;
   }
   if (strcmp(knob, "solve_graph") == 0) {
@@ -1298,6 +1307,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
   }
   if (strcmp(knob, "resident3d") == 0) {
     if (tune_set_resident3d((int)value) != STN_OK) return einval("resident3d must be 0 or 1");
+    return STN_OK;
+  }
+  if (strcmp(knob, "fp64_double_word") == 0) {
+    if (tune_set_double_word((int)value) != STN_OK) return einval("fp64_double_word must be 0 or 1");
     return STN_OK;
   }
   if (strcmp(knob, "fault_withhold_3d") == 0) {
@@ -1384,6 +1397,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "resident3d") == 0) {
     *value = tune_get_resident3d();
+    return STN_OK;
+  }
+  if (strcmp(knob, "fp64_double_word") == 0) {
+    *value = tune_get_double_word();
     return STN_OK;
   }
   if (strcmp(knob, "fault_withhold_3d") == 0) {

@@ -688,7 +688,7 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
 
 static int g_batch_engine = 0;
 int tune_set_batch_engine(int v) {
-  if (v < 0 || v > 1) return STN_EINVAL;
+  if (v < 0 || v > 2) return STN_EINVAL;
   g_batch_engine = v;
   return STN_OK;
 }
@@ -700,6 +700,9 @@ int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int
   if (g_batch_engine == 1)
     return batched_clusters(probs, count, coeffs, radius, tol, iters, check_every, inner_tol, max_outer,
                             refined, infos, s);
+  if (g_batch_engine == 2)
+    return batched_pool(probs, count, coeffs, radius, tol, iters, check_every, inner_tol, max_outer, refined,
+                        infos, s);
   return batched_sched(probs, count, coeffs, radius, tol, iters, check_every, inner_tol, max_outer,
                        refined, infos, s);
 }

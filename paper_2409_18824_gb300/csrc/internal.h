@@ -153,6 +153,12 @@ int launch_star(const T* u, const T* b, T* out, const Grid& g, const double* coe
 template <typename T>
 int launch_copy_halo(const T* src, T* dst, const Grid& g, cudaStream_t s);
 
+// ---- opt-in double sweep in double-word float arithmetic (sweep_dw.cu) ------
+bool dw_applicable(const Grid& g, const double* coeffs, const void* b);
+int launch_star_dw(const double* u, double* out, const Grid& g, const double* coeffs, cudaStream_t s);
+int tune_set_double_word(int v);
+int tune_get_double_word();
+
 // ---- many sweeps of a small grid in one cooperative launch (resident3d.cu) --
 constexpr int kResidentTimeout = 1;
 // Whether the grid is small enough (every interior point one of at most 8
@@ -259,7 +265,13 @@ int batched_solve(const stn_problem* probs, i64 count, const double* coeffs, int
                   i64 iters, i64 check_every, double inner_tol, i64 max_outer, bool refined,
                   stn_solve_info* infos, cudaStream_t s);
 
-// Tuning: batched engine (0 = dynamic unit scheduler, 1 = one cluster per problem).
+// Batch engine 2: the problems, largest first, on a pool of worker streams,
+// each solved by solve_refined_core / solve_jacobi_core (batched_pool.cu).
+int batched_pool(const stn_problem* probs, i64 count, const double* coeffs, int radius, double tol, i64 iters,
+                 i64 check_every, double inner_tol, i64 max_outer, bool refined, stn_solve_info* infos,
+                 cudaStream_t s);
+// Tuning: batched engine (0 = dynamic unit scheduler, 1 = one cluster per
+// problem, 2 = worker streams running the one-problem solves).
 int tune_set_batch_engine(int v);
 int tune_get_batch_engine();
 

@@ -167,7 +167,7 @@ def test_tuning_knobs(lib):
     lib.stencil_tune_set("star_variant", 1)
     assert lib.stencil_tune_get("star_variant") == 1
     lib.stencil_tune_set("star_variant", -1)
-    for knob, good, bad in (("temporal_depth", 3, 5), ("batch_engine", 1, 2), ("solve_graph", 0, 2),
+    for knob, good, bad in (("temporal_depth", 3, 5), ("batch_engine", 2, 3), ("solve_graph", 0, 2),
                             ("star_chunks", 7, -1), ("var_variant", 2, 3), ("repeat_graph", 0, 2),
                             ("sweep2d_resident", 0, 2), ("sweep2d_chunk", 100, 0),
                             ("fault_withhold_2d", 0, 2), ("sweep2d_tma", 0, 2),

@@ -15,10 +15,11 @@ import stencil_inputs as si
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[0, 1], ids=["scheduler", "clusters"])
+@pytest.fixture(params=[0, 1, 2], ids=["scheduler", "clusters", "pool"])
 def engine(request, lib):
-    """Both batched engines: the dynamic work-unit scheduler and one cluster
-    per problem; they must give the same bits."""
+    """The batched engines: the dynamic work-unit scheduler, one cluster per
+    problem, and worker streams running the one-problem solves; they must give
+    the same bits."""
     lib.stencil_tune_set("batch_engine", request.param)
     yield request.param
     lib.stencil_tune_set("batch_engine", 0)
