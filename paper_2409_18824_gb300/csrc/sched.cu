@@ -81,12 +81,17 @@ __host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
   g.tiles_x = (nx + tw - 1) / tw;
   g.tiles_y = (ny + th - 1) / th;
   // k chunks sized from the extents alone (the unit split fixes the order of
-  // every reduction): aim at ~1024 units per pass so a large problem can
-  // occupy the whole GPU, with chunks of 16..64 planes.
+  // every reduction): aim at ~512 units per pass so a large problem can
+  // occupy the whole GPU, with chunks of 64..128 planes.  Measured on the
+  // 2048-solve mix (refined / FP64 solves/s): 16..64 planes, 2048 units:
+  // 90.6 / -; 32..64, 1024: 114.3 / 43.8; 64..128, 512: 125.4 / 45.1;
+  // 96..128: 125.7 / -; 128..256, 256: 127.5 / -.  Longer units cost less
+  // claiming (16 % -> 10 % of CTA cycles) and fewer pipeline start-ups; the
+  // shortest keep more units per pass for the large grids of a serving mix.
   const long long tiles = (long long)g.tiles_x * g.tiles_y;
-  long long klen = ((long long)nz * tiles + 1023) / 1024;
-  if (klen < 32) klen = 32;
-  if (klen > 64) klen = 64;
+  long long klen = ((long long)nz * tiles + 511) / 512;
+  if (klen < 64) klen = 64;
+  if (klen > 128) klen = 128;
   if (klen > nz) klen = nz;
   g.klen = (int)klen;
   g.kc = (nz + g.klen - 1) / g.klen;

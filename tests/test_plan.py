@@ -411,7 +411,7 @@ def test_batched_unit_split_covers_each_problem_once(lib):
     (sizes log-uniform in [16, 128]), the serving mix ([32, 256]) and edge
     extents: the tiles and chunks cover the interior exactly once with no
     empty unit, the shape is the one with the fewest tiles (ties to the wider
-    rows), chunks are 32-64 planes (fewer only when nz is), and every shape's
+    rows), chunks are 64-128 planes (fewer only when nz is), and every shape's
     shared plane (tile plus a halo of 2 on each side) fits the kernel's one
     plane buffer.  The shape counts over the 2048 mix are those the
     scheduler's measurements were taken with: 1050, 420 and 578."""
@@ -429,7 +429,7 @@ def test_batched_unit_split_covers_each_problem_once(lib):
         tiles = {s: ceil_div(nx, w) * ceil_div(ny, 256 // w) for s, w in widths.items()}
         assert tiles[q["variant"]] == min(tiles.values())
         assert all(tiles[s] > tiles[q["variant"]] for s in range(q["variant"]))  # ties to the wider shape
-        assert q["kchunk"] <= 64 and (q["kchunk"] >= 32 or q["kchunk"] == nz)
+        assert q["kchunk"] <= 128 and (q["kchunk"] >= 64 or q["kchunk"] == nz)
         for w in widths.values():
             assert (256 // w + 4) * (w + 4) <= q["stage_elems"]
         if k < len(mix):
