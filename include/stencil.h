@@ -165,6 +165,10 @@ int stencil_release_workspace(void);
  *                   eight worker streams taking the problems largest first,
  *                   each solved as jacobi_solve_f64 / jacobi_solve_refined_f64
  *                   solve it alone (full-grid or resident kernels).
+ *   "batch_graph":  the batch scheduler's persistent launch as a CUDA graph
+ *                   captured and launched on the call's stream (1, default;
+ *                   a failure to capture falls back to a plain launch), or a
+ *                   plain launch (0).  Same kernel, same results.
  * Every variant, depth and engine computes bitwise the same iterates (with a
  * fixed number of inner sweeps, for refined solves; with inner_tol > 0 the
  * engines' inner stopping sums may round differently).

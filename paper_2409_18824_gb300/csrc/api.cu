@@ -1293,6 +1293,10 @@ int stencil_tune_set(const char* knob, int64_t value) {
     if (tune_set_batch_engine((int)value) != STN_OK) return einval("batch_engine must be 0, 1 or 2");
     return STN_OK;
   }
+  if (strcmp(knob, "batch_graph") == 0) {
+    if (tune_set_batch_graph((int)value) != STN_OK) return einval("batch_graph must be 0 or 1");
+    return STN_OK;
+  }
   if (strcmp(knob, "solve_graph") == 0) {
     if (tune_set_solve_graph((int)value) != STN_OK) return einval("solve_graph must be 0 or 1");
     return STN_OK;
@@ -1381,6 +1385,10 @@ int stencil_tune_get(const char* knob, int64_t* value) {
   }
   if (strcmp(knob, "batch_engine") == 0) {
     *value = tune_get_batch_engine();
+    return STN_OK;
+  }
+  if (strcmp(knob, "batch_graph") == 0) {
+    *value = tune_get_batch_graph();
     return STN_OK;
   }
   if (strcmp(knob, "solve_graph") == 0) {

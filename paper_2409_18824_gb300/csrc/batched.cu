@@ -534,6 +534,47 @@ static int batched_clusters(const stn_problem* probs, i64 count, const double* c
 
 // Scheduler engine: one persistent launch of the dynamic unit scheduler
 // (sched.cu) over all problems, queued largest estimated work first.
+// The persistent launch of a batch as a one-node CUDA graph: captured on a
+// private stream, instantiated and launched on the caller's stream (which
+// may be the legacy default stream, which cannot be captured).  Any failure
+// to capture or instantiate falls back to a plain launch (knob batch_graph:
+// 1 default, 0 plain).
+static int g_batch_graph = 1;
+int tune_set_batch_graph(int v) {
+  if (v < 0 || v > 1) return STN_EINVAL;
+  g_batch_graph = v;
+  return STN_OK;
+}
+int tune_get_batch_graph() { return g_batch_graph; }
+
+static int launch_sched_graph(const SchedArgs& a, int radius, bool hc0, int ctas, cudaStream_t s) {
+  if (!g_batch_graph) return sched_launch(a, radius, hc0, ctas, s);
+  if (int rc = sched_prepare()) return rc;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool launched = false;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    const int rc = sched_launch(a, radius, hc0, ctas, cs);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (rc == STN_OK && ec == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess &&
+        cudaGraphLaunch(exec, s) == cudaSuccess)
+      launched = true;
+  }
+  // an executable graph that is still running is freed when it completes
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (launched) {
+    sched_set_stats_stream(s);
+    return STN_OK;
+  }
+  (void)cudaGetLastError();
+  clear_error();
+  return sched_launch(a, radius, hc0, ctas, s);
+}
+
 static int batched_sched(const stn_problem* probs, i64 count, const double* coeffs, int radius,
                          double tol, i64 iters, i64 check_every, double inner_tol, i64 max_outer,
                          bool refined, stn_solve_info* infos, cudaStream_t s) {
@@ -657,7 +698,7 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
     a.refined = refined ? 1 : 0;
     // idle limit without any claimable unit (2 s by default), in SM clock cycles
     a.idle_cycles = sched_faults().idle_ms * 2070000ll;
-    if ((rc = sched_launch(a, radius, hc0, ctas, s)) != STN_OK) break;
+    if ((rc = launch_sched_graph(a, radius, hc0, ctas, s)) != STN_OK) break;
     if ((e = cudaMemcpyAsync(hres.data(), base + o_res, sizeof(SchedResult) * count, cudaMemcpyDeviceToHost, s))) break;
     if ((e = cudaMemcpyAsync(&herr, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
     if ((e = cudaStreamSynchronize(s))) break;

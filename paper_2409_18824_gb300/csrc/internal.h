@@ -274,6 +274,9 @@ int batched_pool(const stn_problem* probs, i64 count, const double* coeffs, int 
 // problem, 2 = worker streams running the one-problem solves).
 int tune_set_batch_engine(int v);
 int tune_get_batch_engine();
+// Tuning: the batch's persistent scheduler launch as a CUDA graph (1, default) or plain (0).
+int tune_set_batch_graph(int v);
+int tune_get_batch_graph();
 
 // ---- reductions (reduce.cu) -------------------------------------------------
 // Sums partials[0..n) in a fixed order into dst[0] = sum, dst[1] = sqrt(sum),

@@ -645,9 +645,16 @@ void sched_last_stats(unsigned long long* out) {
     memset(out, 0, sizeof(g_stats_host));
 }
 
+int sched_prepare() {
+  if (!g_stats_dev) STN_CUDA_TRY(cudaMalloc(&g_stats_dev, sizeof(unsigned long long) * SCHED_NSTATS));
+  return STN_OK;
+}
+
+void sched_set_stats_stream(cudaStream_t s) { g_stats_stream = s; }
+
 int sched_launch(const SchedArgs& a0, int radius, bool has_c0, int ctas, cudaStream_t s) {
   SchedArgs a = a0;
-  if (!g_stats_dev) STN_CUDA_TRY(cudaMalloc(&g_stats_dev, sizeof(unsigned long long) * SCHED_NSTATS));
+  if (int rc = sched_prepare()) return rc;
   STN_CUDA_TRY(cudaMemsetAsync(g_stats_dev, 0, sizeof(unsigned long long) * SCHED_NSTATS, s));
   g_stats_stream = s;
   a.stats = g_stats_dev;

@@ -94,6 +94,10 @@ enum {
 void sched_last_stats(unsigned long long* out);
 
 int sched_launch(const SchedArgs& a, int radius, bool has_c0, int ctas, cudaStream_t s);
+// Allocates the launch counters once (before a launch is captured into a
+// graph), and names the stream the counters are read back on.
+int sched_prepare();
+void sched_set_stats_stream(cudaStream_t s);
 
 // Fault injection and limits for tests (process-wide; all default to off).
 struct SchedFaults {

@@ -209,3 +209,22 @@ def test_full_2048_mix_sampled_parity(lib, cuda):
         assert st == 0 and infos[i]["iters"] == it_ref, (i, sizes[i])
         assert bitwise(to_host(us[i]), u_ref), (i, sizes[i])
         assert abs(infos[i]["rel_res"] - rel_ref) <= NORM_RTOL * rel_ref
+
+
+def test_graph_and_plain_launch_give_the_same_bits(lib, cuda):
+    """The scheduler's persistent launch captured in a CUDA graph (knob
+    batch_graph = 1, the default) and launched plainly (0): same results."""
+    rhs = make_batch(SIZES, seed0=61)
+    outs = []
+    try:
+        for v in (1, 0):
+            lib.stencil_tune_set("batch_graph", v)
+            d_u = [to_dev(np.zeros_like(b)) for b in rhs]
+            rc, infos = lib.jacobi_solve_batched_refined(d_u, [to_dev(b) for b in rhs], L7, 1, 1e-8, 200000, 1e-2, 50,
+                                                         40)
+            assert rc == 0
+            outs.append(([to_host(u) for u in d_u], [(i["iters"], i["outer"]) for i in infos]))
+    finally:
+        lib.stencil_tune_set("batch_graph", 1)
+    assert outs[0][1] == outs[1][1]
+    assert all(bitwise(a, b) for a, b in zip(outs[0][0], outs[1][0]))
