@@ -18,7 +18,8 @@
 //               state machine, resets the counters and publishes the next
 //               pass with an atomic exchange of the claim word (release).
 // Sweeps are computed by star_tile, the code of the single-problem kernels,
-// so every sweep is bitwise the single-problem sweep.  There is no device
+// or at radius 1 by star_tile_async, its arithmetic with the planes staged
+// asynchronously, so every sweep is bitwise the single-problem sweep.  There is no device
 // wait on another CTA's progress except the bounded idle back-off of a CTA
 // that found no work; it gives up after `idle_ns` and records STN_ETIMEOUT
 // (batch) or simply returns (serving, where the host relaunches on demand).
@@ -162,6 +163,116 @@ __device__ __forceinline__ void for_unit_points(const SchedProblem& P, const Geo
   for (int k = k0; k < k1; k++) f((i64)i + NX * ((i64)j + NY * k));
 }
 
+// one shared plane of any tile shape (radius <= 2): 12 x 36 = 36 x 12 = 432
+// elements for 32 x 8 and 8 x 32, 20 x 20 for 16 x 16
+constexpr int kPlaneElems = (TY + 4) * (TX + 4);
+static_assert((BT / 16 + 4) * (16 + 4) <= kPlaneElems && (BT / 8 + 4) * (8 + 4) <= kPlaneElems,
+              "every tile shape's plane fits");
+constexpr int kPlaneBytes = kPlaneElems * 8;
+
+// ---------------------------------------------------------------------------
+// Radius-1 unit sweeps stream their planes through a shared-memory ring
+// filled by element-wise asynchronous copies (cp.async.ca: the grids were
+// written by other CTAs in earlier passes, and the unit's acquire fence
+// precedes the copies as it preceded the loads), kAsyncPF planes ahead of the
+// 2R+1 in use, with one block barrier per plane.  The per-plane tile sweep
+// with a one-plane register prefetch (star_tile) spent most of its time at
+// its two barriers per plane and on long-scoreboard stalls: in ncu, 64 warps
+// per SM were resident and issued only 36 % of the cycles.  A stage holds the
+// tile's plane with its halo and, after it, the source term of the tile's
+// points; z neighbours come from the neighbouring stages.  Every value and
+// operation is star_tile's, in its order, so the results are its bits.
+constexpr int kAsyncPF = 2;
+constexpr int kAsyncStages = 2 * 1 + 1 + kAsyncPF;  // radius 1
+constexpr int kStageElems = kPlaneElems + BT;       // plane with halo, then b
+constexpr int kRingBytes = kAsyncStages * kStageElems * 8;
+// the unit's shared buffer: the ring at radius 1, one plane at radius 2
+template <int R>
+__host__ __device__ constexpr int unit_smem_bytes() { return R == 1 ? kRingBytes : kPlaneBytes; }
+
+__device__ __forceinline__ void cp_el(void* dst_smem, const void* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T, bool HAS_B, bool HAS_C0, int MODE>
+__device__ __forceinline__ void star_tile_async(const T* u, const T* b, T* out, int nx, int ny, int NX, int NY,
+                                                int tile_x, int tile_y, int k0, int k1, const StarCoeffs<T, 1>& cf,
+                                                int tw, int th, T* ring, double* rsum_io) {
+  using A = Arith<T>;
+  constexpr int R = 1, S = kAsyncStages;
+  const int flat = (int)(threadIdx.x + blockDim.x * threadIdx.y);
+  const int tx = flat % tw, ty = flat / tw;
+  const int pitch = tw + 2 * R;
+  const int gi = tile_x * tw + tx + R, gj = tile_y * th + ty + R;
+  const i64 sy = NX, sz = (i64)NX * NY;
+  const bool inx = gi < NX, iny = gj < NY;
+  const bool active = (gi < nx + R) && (gj < ny + R);
+  const bool hx = (tx < R) || (tx >= tw - R);
+  const int hx_i = (tx < R) ? gi - R : gi + R;
+  const int hx_lx = (tx < R) ? tx : tx + 2 * R;
+  const bool hx_ok = hx && hx_i < NX && iny;
+  const bool hy = (ty < R) || (ty >= th - R);
+  const int hy_j = (ty < R) ? gj - R : gj + R;
+  const int hy_ly = (ty < R) ? ty : ty + 2 * R;
+  const bool hy_ok = hy && hy_j < NY && inx;
+  const bool ld_c = inx && iny;
+  const int me = (ty + R) * pitch + tx + R;
+  const T* pc = u + gi + gj * sy;
+  const T* px = u + hx_i + gj * sy;
+  const T* py = u + gi + (i64)hy_j * sy;
+  const T* pb = HAS_B ? b + gi + gj * sy : nullptr;
+  const int pfirst = k0 - R, plast = k1 - 1 + R;
+  auto stage = [&](int p) -> T* { return ring + ((p - pfirst) % S) * kStageElems; };
+  auto issue = [&](int p) {  // every thread: its cells of plane p (one commit group, maybe empty)
+    if (p <= plast) {
+      T* st = stage(p);
+      const i64 po = (i64)p * sz;
+      if (ld_c) cp_el(st + me, pc + po, (int)sizeof(T));
+      if (hx_ok) cp_el(st + (ty + R) * pitch + hx_lx, px + po, (int)sizeof(T));
+      if (hy_ok) cp_el(st + hy_ly * pitch + tx + R, py + po, (int)sizeof(T));
+      if (HAS_B && active && p >= k0 && p < k1) cp_el(st + kPlaneElems + flat, pb + po, (int)sizeof(T));
+    }
+    cp_commit();
+  };
+  // planes k0 - R .. k0 + R + kAsyncPF - 1 before the first plane
+  for (int i = 0; i < S - 1; i++) issue(pfirst + i);
+  double rsum = *rsum_io;
+  for (int k = k0; k < k1; k++) {
+    cp_wait<kAsyncPF - 1>();  // this thread's copies of planes <= k + R have landed
+    __syncthreads();          // everyone's, and plane k - 1 - R is no longer read
+    issue(k + R + kAsyncPF);  // into the stage of plane k - 1 - R
+    if (active) {
+      const T* c0p = stage(k);
+      const T* cm = stage(k - 1);
+      const T* cp = stage(k + 1);
+      const T sx = A::add(c0p[me - 1], c0p[me + 1]);
+      const T sy_ = A::add(c0p[me - pitch], c0p[me + pitch]);
+      const T szz = A::add(cm[me], cp[me]);
+      T acc = A::mul(cf.c[1], A::add(A::add(sx, sy_), szz));
+      const T c = c0p[me];
+      if (HAS_C0) acc = A::add(acc, A::mul(cf.c[0], c));
+      if (HAS_B) acc = A::add(acc, c0p[kPlaneElems + flat]);
+      if (MODE != kResidualOnly) out[gi + gj * sy + (i64)k * sz] = acc;
+      if (MODE != kSweep) {
+        const double rho = (double)acc - (double)c;
+        rsum = __fma_rn(rho, rho, rsum);
+      }
+    }
+  }
+  cp_wait<0>();
+  __syncthreads();  // the ring is free again when this returns
+  *rsum_io = rsum;
+}
+
 template <typename T, int R, bool HAS_C0, int MODE>
 __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, const SchedProblem& P,
                                              const Geo& g, int q, const StarCoeffs<T, R>& cf, T* plane) {
@@ -172,6 +283,16 @@ __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, c
   const int NX = P.nx + 2 * R, NY = P.ny + 2 * R;
   const int tw = tile_width(g.shape);
   double rs = 0.0;
+  if constexpr (R == 1) {
+    // `plane` is the kernel's ring buffer at radius 1
+    if (b)
+      star_tile_async<T, true, HAS_C0, MODE>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw,
+                                             plane, &rs);
+    else
+      star_tile_async<T, false, HAS_C0, MODE>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw,
+                                              BT / tw, plane, &rs);
+    return rs;
+  }
   if (b)
     star_tile<T, R, true, HAS_C0, MODE>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw, plane,
                                         &rs);
@@ -181,21 +302,11 @@ __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, c
   return rs;
 }
 
-// one shared plane of any tile shape (radius <= 2): 12 x 36 = 36 x 12 = 432
-// elements for 32 x 8 and 8 x 32, 20 x 20 for 16 x 16
-constexpr int kPlaneElems = (TY + 4) * (TX + 4);
-static_assert((BT / 16 + 4) * (16 + 4) <= kPlaneElems && (BT / 8 + 4) * (8 + 4) <= kPlaneElems,
-              "every tile shape's plane fits");
-struct SmemPlanes {
-  double d[kPlaneElems];
-  float f[kPlaneElems];
-};
-
 // Processes unit q of the slot's current pass; returns the partial (valid in
 // thread 0) to store at partials[q].
 template <int R, bool HAS_C0>
 __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedProblem& P, int q,
-                           SmemPlanes& sp, double* red) {
+                           unsigned char* smem, double* red) {
   const Geo g = make_geo(P.nx, P.ny, P.nz);
   StarCoeffs<double, R> c64;
   StarCoeffs<float, R> c32;
@@ -204,8 +315,8 @@ __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedPr
     c64.c[d] = a.coeffs[d];
     c32.c[d] = (float)a.coeffs[d];
   }
-  double* t64 = sp.d;
-  float* t32 = sp.f;
+  double* t64 = (double*)smem;
+  float* t32 = (float*)smem;
   double v = 0.0;
   switch (S.phase) {
     case PH_INIT: {
@@ -507,7 +618,7 @@ __device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, cons
 // allocation unconstrained gave 96 registers and 2 blocks per SM).
 template <int R, bool HAS_C0, int MINB>
 __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
-  __shared__ SmemPlanes sp;
+  __shared__ __align__(16) unsigned char smem[unit_smem_bytes<R>()];
   __shared__ double red[BT / 32];
   __shared__ SchedSlot s_state;
   __shared__ SchedProblem s_prob;
@@ -600,7 +711,7 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
     __threadfence();  // acquire for every thread: the previous pass's grids
     const SchedSlot S = s_state;
     const SchedProblem P = s_prob;
-    const double part = run_unit<R, HAS_C0>(a, S, P, s_unit, sp, red);
+    const double part = run_unit<R, HAS_C0>(a, S, P, s_unit, smem, red);
     __syncthreads();  // every thread's writes of this unit precede the release
     const long long t2 = clock64();
     st[SCHED_CYC_UNIT] += t2 - t1;
