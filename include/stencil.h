@@ -193,8 +193,9 @@ int stencil_release_workspace(void);
 int stencil_tune_set(const char* knob, int64_t value);
 /* Counters of the last batched/served scheduler launch in this process
  * (summed over CTAs): cycles claiming, computing units, completing units, in
- * pass epilogues, idle; units; epilogues; empty claim scans.  Returns the
- * number of counters written (at most n). */
+ * pass epilogues, idle; units; epilogues; empty claim scans; units claimed
+ * on the slot and pass of the CTA's previous unit; claim atomics issued by
+ * slot scans.  Returns the number of counters written (at most n). */
 int stencil_sched_stats(uint64_t* out, int n);
 int stencil_tune_get(const char* knob, int64_t* value);
 

@@ -634,7 +634,8 @@ class Server:
         self.close()
 
 
-SCHED_STATS = ("cyc_claim", "cyc_unit", "cyc_done", "cyc_epilogue", "cyc_idle", "units", "epilogues", "misses")
+SCHED_STATS = ("cyc_claim", "cyc_unit", "cyc_done", "cyc_epilogue", "cyc_idle", "units", "epilogues", "misses",
+               "fast_claims", "claim_tries")
 
 
 def stencil_sched_stats() -> dict:

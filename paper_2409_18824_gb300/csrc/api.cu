@@ -1214,7 +1214,7 @@ static int batch_impl(const stn_problem* probs, i64 count, const double* coeffs,
       return einval("batched problem extent too large");
     if (!p.u) return einval("NULL problem grid");
     const i64 units = sched_units(p.nx, p.ny, p.nz);
-    if (units > INT32_MAX) return einval("batched problem needs more than 2^31 - 1 work units");
+    if (units > kMaxPassUnits) return einval("batched problem needs more than 2^22 work units per pass");
     const size_t bytes = (size_t)Grid{p.nx, p.ny, p.nz, radius}.count() * sizeof(double);
     if (p.rhs && overlap(p.rhs, p.u, bytes)) return einval("problem rhs overlaps its u");
     scratch += (double)Grid{p.nx, p.ny, p.nz, radius}.count() * (refined ? 20.0 : 8.0) + 8.0 * (double)units;

@@ -7,8 +7,9 @@
 // problem soaks up every CTA the small ones leave idle, and a problem's
 // critical path shrinks to its own work divided by the whole GPU.
 //
-//   claim     : 64-bit word per slot = (pass id << 32) | next unit; one
-//               atomicAdd claims a unit AND names the pass it belongs to.
+//   claim     : 64-bit word per slot = pass id, the pass's unit count and
+//               the next unit; one atomicAdd claims a unit AND names the pass
+//               it belongs to, and tells whether the claim is valid.
 //   complete  : per-unit partial results are written to the problem's
 //               partials array, then a release fence and an atomicAdd on the
 //               slot's done counter; the CTA that completes the last unit
@@ -174,7 +175,7 @@ constexpr int kPlaneBytes = kPlaneElems * 8;
 // Radius-1 unit sweeps stream their planes through a shared-memory ring
 // filled by element-wise asynchronous copies (cp.async.ca: the grids were
 // written by other CTAs in earlier passes, and the unit's acquire fence
-// precedes the copies as it preceded the loads), kAsyncPF planes ahead of the
+// precedes the copies as it preceded the loads), PF planes ahead of the
 // 2R+1 in use, with one block barrier per plane.  The per-plane tile sweep
 // with a one-plane register prefetch (star_tile) spent most of its time at
 // its two barriers per plane and on long-scoreboard stalls: in ncu, 64 warps
@@ -182,13 +183,23 @@ constexpr int kPlaneBytes = kPlaneElems * 8;
 // tile's plane with its halo and, after it, the source term of the tile's
 // points; z neighbours come from the neighbouring stages.  Every value and
 // operation is star_tile's, in its order, so the results are its bits.
-constexpr int kAsyncPF = 2;
-constexpr int kAsyncStages = 2 * 1 + 1 + kAsyncPF;  // radius 1
-constexpr int kStageElems = kPlaneElems + BT;       // plane with halo, then b
-constexpr int kRingBytes = kAsyncStages * kStageElems * 8;
+// The ring takes what the launch's blocks per SM leave of shared memory:
+// 8 double stages (44 KB) at 4 blocks per SM, 5 (27.5 KB) at 7.  Float
+// planes take half the bytes, so they run up to 8 planes ahead.  Enough
+// bytes in flight is what the units need: with loads two planes ahead they
+// were bound by memory latency.
+constexpr int kStageElems = kPlaneElems + BT;  // plane with halo, then b
+template <int MINB>
+__host__ __device__ constexpr int ring_bytes() { return (MINB <= 4 ? 8 : 5) * kStageElems * 8; }
+template <typename T, int MINB>
+__host__ __device__ constexpr int ring_pf() {
+  return ring_bytes<MINB>() / (kStageElems * (int)sizeof(T)) - 3 > 8
+             ? 8
+             : ring_bytes<MINB>() / (kStageElems * (int)sizeof(T)) - 3;
+}
 // the unit's shared buffer: the ring at radius 1, one plane at radius 2
-template <int R>
-__host__ __device__ constexpr int unit_smem_bytes() { return R == 1 ? kRingBytes : kPlaneBytes; }
+template <int R, int MINB>
+__host__ __device__ constexpr int unit_smem_bytes() { return R == 1 ? ring_bytes<MINB>() : kPlaneBytes; }
 
 __device__ __forceinline__ void cp_el(void* dst_smem, const void* src, int bytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
@@ -203,12 +214,13 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <typename T, bool HAS_B, bool HAS_C0, int MODE>
+template <typename T, bool HAS_B, bool HAS_C0, int MODE, int PF>
 __device__ __forceinline__ void star_tile_async(const T* u, const T* b, T* out, int nx, int ny, int NX, int NY,
                                                 int tile_x, int tile_y, int k0, int k1, const StarCoeffs<T, 1>& cf,
                                                 int tw, int th, T* ring, double* rsum_io) {
   using A = Arith<T>;
-  constexpr int R = 1, S = kAsyncStages;
+  constexpr int R = 1, S = 2 * R + 1 + PF;
+  static_assert(PF >= 1, "at least one plane ahead");
   const int flat = (int)(threadIdx.x + blockDim.x * threadIdx.y);
   const int tx = flat % tw, ty = flat / tw;
   const int pitch = tw + 2 * R;
@@ -243,13 +255,13 @@ __device__ __forceinline__ void star_tile_async(const T* u, const T* b, T* out, 
     }
     cp_commit();
   };
-  // planes k0 - R .. k0 + R + kAsyncPF - 1 before the first plane
+  // planes k0 - R .. k0 + R + PF - 1 before the first plane
   for (int i = 0; i < S - 1; i++) issue(pfirst + i);
   double rsum = *rsum_io;
   for (int k = k0; k < k1; k++) {
-    cp_wait<kAsyncPF - 1>();  // this thread's copies of planes <= k + R have landed
+    cp_wait<PF - 1>();  // this thread's copies of planes <= k + R have landed
     __syncthreads();          // everyone's, and plane k - 1 - R is no longer read
-    issue(k + R + kAsyncPF);  // into the stage of plane k - 1 - R
+    issue(k + R + PF);  // into the stage of plane k - 1 - R
     if (active) {
       const T* c0p = stage(k);
       const T* cm = stage(k - 1);
@@ -273,7 +285,7 @@ __device__ __forceinline__ void star_tile_async(const T* u, const T* b, T* out, 
   *rsum_io = rsum;
 }
 
-template <typename T, int R, bool HAS_C0, int MODE>
+template <typename T, int R, bool HAS_C0, int MODE, int MINB>
 __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, const SchedProblem& P,
                                              const Geo& g, int q, const StarCoeffs<T, R>& cf, T* plane) {
   const int tiles = g.tiles_x * g.tiles_y;
@@ -286,10 +298,10 @@ __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, c
   if constexpr (R == 1) {
     // `plane` is the kernel's ring buffer at radius 1
     if (b)
-      star_tile_async<T, true, HAS_C0, MODE>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw,
+      star_tile_async<T, true, HAS_C0, MODE, ring_pf<T, MINB>()>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw,
                                              plane, &rs);
     else
-      star_tile_async<T, false, HAS_C0, MODE>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw,
+      star_tile_async<T, false, HAS_C0, MODE, ring_pf<T, MINB>()>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw,
                                               BT / tw, plane, &rs);
     return rs;
   }
@@ -304,7 +316,7 @@ __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, c
 
 // Processes unit q of the slot's current pass; returns the partial (valid in
 // thread 0) to store at partials[q].
-template <int R, bool HAS_C0>
+template <int R, bool HAS_C0, int MINB>
 __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedProblem& P, int q,
                            unsigned char* smem, double* red) {
   const Geo g = make_geo(P.nx, P.ny, P.nz);
@@ -330,9 +342,9 @@ __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedPr
       double* cur = S.parity ? P.t : P.u;
       double* nxt = S.parity ? P.u : P.t;
       if (S.resid)
-        v = unit_sweep<double, R, HAS_C0, kSweepResidual>(cur, P.b, nxt, P, g, q, c64, t64);
+        v = unit_sweep<double, R, HAS_C0, kSweepResidual, MINB>(cur, P.b, nxt, P, g, q, c64, t64);
       else
-        unit_sweep<double, R, HAS_C0, kSweep>(cur, P.b, nxt, P, g, q, c64, t64);
+        unit_sweep<double, R, HAS_C0, kSweep, MINB>(cur, P.b, nxt, P, g, q, c64, t64);
       return block_sum_fixed<BT>(v, red);
     }
     case PH_COPY: {
@@ -340,7 +352,7 @@ __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedPr
       return 0.0;
     }
     case PH_RES: {
-      v = unit_sweep<double, R, HAS_C0, kSweepResidual>(P.u, P.b, P.t, P, g, q, c64, t64);
+      v = unit_sweep<double, R, HAS_C0, kSweepResidual, MINB>(P.u, P.b, P.t, P, g, q, c64, t64);
       return block_sum_fixed<BT>(v, red);
     }
     case PH_MAX: {
@@ -361,9 +373,9 @@ __device__ double run_unit(const SchedArgs& a, const SchedSlot& S, const SchedPr
       float* cur = S.parity ? P.e2 : P.e;
       float* nxt = S.parity ? P.e : P.e2;
       if (S.resid)
-        v = unit_sweep<float, R, HAS_C0, kSweepResidual>(cur, P.r32, nxt, P, g, q, c32, t32);
+        v = unit_sweep<float, R, HAS_C0, kSweepResidual, MINB>(cur, P.r32, nxt, P, g, q, c32, t32);
       else
-        unit_sweep<float, R, HAS_C0, kSweep>(cur, P.r32, nxt, P, g, q, c32, t32);
+        unit_sweep<float, R, HAS_C0, kSweep, MINB>(cur, P.r32, nxt, P, g, q, c32, t32);
       return block_sum_fixed<BT>(v, red);
     }
     case PH_UPDATE: {
@@ -509,10 +521,11 @@ __device__ __forceinline__ int ld_acquire_sys_s32(const int* p) {
 __device__ __forceinline__ void publish(const SchedArgs& a, int si) {
   SchedSlot& S = a.slots[si];
   const unsigned pass = *(volatile unsigned*)&S.pass + 1;
+  const int nunits = *(volatile int*)&S.nunits;
   S.pass = pass;
   S.done = 0;
   __threadfence();
-  atomicExch(&a.words[si], (unsigned long long)pass << 32);
+  atomicExch(&a.words[si], claim_word(pass, nunits));
 }
 
 // Loads problem `pi` into slot `si` (one thread) and publishes its first pass.
@@ -618,15 +631,17 @@ __device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, cons
 // allocation unconstrained gave 96 registers and 2 blocks per SM).
 template <int R, bool HAS_C0, int MINB>
 __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
-  __shared__ __align__(16) unsigned char smem[unit_smem_bytes<R>()];
+  __shared__ __align__(16) unsigned char smem[unit_smem_bytes<R, MINB>()];
   __shared__ double red[BT / 32];
   __shared__ SchedSlot s_state;
   __shared__ SchedProblem s_prob;
-  __shared__ int s_slot, s_unit, s_last, s_flag;
+  __shared__ int s_slot, s_unit, s_last, s_flag, s_fast;
   const int nslots = a.nslots;
   int cursor = (int)(blockIdx.x % (unsigned)(nslots > 0 ? nslots : 1));
+  // slot of this CTA's last unit while its pass may have units left, else -1
+  int sticky = -1;
   long long idle_since = -1;
-  unsigned long long st[SCHED_NSTATS] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long st[SCHED_NSTATS] = {};
   long long t0 = clock64();
   for (;;) {
     if (tid_flat() < 32) {
@@ -634,34 +649,54 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
       // tries the ones with units left in slot order, one lane at a time: the
       // claim and its validation are those of a single thread's scan
       const int lane = tid_flat();
+      // first the next unit of the last unit's pass: one atomic, and the
+      // slot state, the problem and the acquired grids stay those of that
+      // pass (pass ids of a slot only grow, so an equal id is the same pass)
+      int fast = 0;
+      if (sticky >= 0) {
+        if (lane == 0) {
+          const unsigned long long w = atomicAdd(&a.words[sticky], 1ull);
+          const int q = claim_next(w);
+          if (claim_pass(w) == (s_state.pass & 0xffffu) && q < claim_units(w)) {
+            s_unit = q;
+            fast = 1;
+          }
+        }
+        fast = __shfl_sync(0xffffffffu, fast, 0);
+        if (!fast) sticky = -1;
+      }
       // -1 none yet, -3 stop; lane 0 reads the error word so that every lane
       // takes the same path through the ballots below
-      int found = lane == 0 && *(volatile int*)a.error != 0 ? -3 : -1;
+      int found = fast ? sticky : (lane == 0 && *(volatile int*)a.error != 0 ? -3 : -1);
       found = __shfl_sync(0xffffffffu, found, 0);
       for (int base = 0; found == -1 && base < nslots; base += 32) {
         const int si = (cursor + base + lane) % nslots;
         bool cand = false;
         if (base + lane < nslots) {
           const unsigned long long w0 = *(volatile unsigned long long*)&a.words[si];
-          const int nu = *(volatile int*)&a.slots[si].nunits;
-          cand = (int)(w0 & 0xffffffffu) < nu;
+          cand = claim_next(w0) < claim_units(w0);
         }
         unsigned mask = __ballot_sync(0xffffffffu, cand);
         while (mask && found == -1) {
           const int l = __ffs(mask) - 1;
           mask &= mask - 1;
           int ok = 0;
+          st[SCHED_N_TRIES]++;
           if (lane == l) {
             const unsigned long long w = atomicAdd(&a.words[si], 1ull);
-            __threadfence();
-            const unsigned pass = (unsigned)(w >> 32);
-            const int q = (int)(w & 0xffffffffu);
-            const SchedSlot S = vload(&a.slots[si]);
-            if (S.pass == pass && q < S.nunits && S.nunits > 0) {
-              s_state = S;
-              s_prob = vload(&a.probs[S.problem]);
-              s_unit = q;
-              ok = 1;
+            const int q = claim_next(w);
+            if (q < claim_units(w)) {
+              // a unit of the published pass: its state was written before
+              // the word (release), and the pass cannot end while this unit
+              // is held, so the state read after the fence is that pass's
+              __threadfence();
+              const SchedSlot S = vload(&a.slots[si]);
+              if ((S.pass & 0xffffu) == claim_pass(w) && q < S.nunits) {
+                s_state = S;
+                s_prob = vload(&a.probs[S.problem]);
+                s_unit = q;
+                ok = 1;
+              }
             }
           }
           if (__shfl_sync(0xffffffffu, ok, l)) found = __shfl_sync(0xffffffffu, si, l);
@@ -669,6 +704,7 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
       }
       if (lane == 0) {
         s_slot = found;
+        s_fast = fast;
         if (found >= 0) {
           cursor = found;
         } else if (found == -1) {
@@ -707,11 +743,12 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
       continue;
     }
     st[SCHED_CYC_CLAIM] += t1 - t0;
+    st[SCHED_N_FAST] += s_fast;
     idle_since = -1;
-    __threadfence();  // acquire for every thread: the previous pass's grids
+    if (!s_fast) __threadfence();  // acquire for every thread: the previous pass's grids
     const SchedSlot S = s_state;
     const SchedProblem P = s_prob;
-    const double part = run_unit<R, HAS_C0>(a, S, P, s_unit, smem, red);
+    const double part = run_unit<R, HAS_C0, MINB>(a, S, P, s_unit, smem, red);
     __syncthreads();  // every thread's writes of this unit precede the release
     const long long t2 = clock64();
     st[SCHED_CYC_UNIT] += t2 - t1;
@@ -726,6 +763,7 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
     __syncthreads();
     const long long t3 = clock64();
     st[SCHED_CYC_DONE] += t3 - t2;
+    sticky = s_last ? -1 : si;  // the last unit's CTA moves the slot to its next pass
     if (s_last) {
       __threadfence();  // acquire for every thread: the other units' partials
       epilogue<R, HAS_C0>(a, si, P, S, red);
@@ -824,7 +862,7 @@ LaunchPlan batch_unit_plan(i64 nx, i64 ny, i64 nz) {
 }
 
 // The exact count (each factor fits an int for extents <= 2^20; their product
-// need not, and the batched entry points reject problems above 2^31 - 1).
+// need not, and the batched entry points reject problems above 2^22).
 i64 sched_units(i64 nx, i64 ny, i64 nz) {
   const Geo g = make_geo((int)nx, (int)ny, (int)nz);
   return (i64)g.tiles_x * g.tiles_y * g.kc;

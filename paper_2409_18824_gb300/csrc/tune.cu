@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "work_sched.h"
 
 namespace stn {
 
@@ -618,8 +619,8 @@ int stencil_plan_query(const char* op, int64_t nx, int64_t ny, int64_t nz, int e
   } else if (strcmp(op, "batch_unit") == 0) {
     if (nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20)) return tune_einval("batched problem extent too large");
     q = batch_unit_plan(nx, ny, nz);
-    if ((i64)q.grid_x * q.grid_y * q.grid_z > INT32_MAX)
-      return tune_einval("batched problem needs more than 2^31 - 1 work units");
+    if ((i64)q.grid_x * q.grid_y * q.grid_z > kMaxPassUnits)
+      return tune_einval("batched problem needs more than 2^22 work units per pass");
   } else if (strcmp(op, "sweep2d") == 0) {
     if (nz != 1) return tune_einval("sweep2d plans take nz = 1");
     q = sweep2d_launch_plan(Grid2{nx, ny, radius}, (size_t)esize);

@@ -50,7 +50,7 @@ struct SchedResult {
 struct SchedArgs {
   SchedProblem* probs;
   SchedSlot* slots;
-  unsigned long long* words;  // per slot: (pass << 32) | next unit
+  unsigned long long* words;  // per slot: claim word (pass id, units of the pass, next unit)
   int nslots;
   int count;                  // problems in total (batch) / queue capacity bound (serving)
   int qlen;                   // batch: queue entries available (count, or fewer under fault injection)
@@ -88,7 +88,9 @@ enum {
   SCHED_N_UNITS = 5,
   SCHED_N_EPI = 6,
   SCHED_N_MISS = 7,
-  SCHED_NSTATS = 8
+  SCHED_N_FAST = 8,   // units claimed on the same slot and pass as the CTA's previous unit
+  SCHED_N_TRIES = 9,  // claim atomics issued by slot scans (successful or not)
+  SCHED_NSTATS = 10
 };
 // Counters of the last scheduler launch made by this process.
 void sched_last_stats(unsigned long long* out);
@@ -112,5 +114,20 @@ SchedFaults& sched_faults();
 int sched_ctas(int radius, bool has_c0, bool refined);
 // Work units of a problem's pass.
 i64 sched_units(i64 nx, i64 ny, i64 nz);
+
+// A slot's claim word: the published pass's id (low 16 bits of it; compared
+// for equality only), its unit count (24 bits) and the next unit to hand out
+// (24 bits).  A claim is one atomicAdd, valid when the returned next unit is
+// below the returned count, so a failed claim costs no further reads.
+// Problems are limited to kMaxPassUnits units per pass, which leaves the
+// next-unit field 3 x 2^22 increments of headroom for claims that lose races
+// after a pass runs out (at most a few per CTA and pass).
+constexpr i64 kMaxPassUnits = (i64)1 << 22;
+__host__ __device__ inline unsigned long long claim_word(unsigned pass, int nunits) {
+  return ((unsigned long long)(pass & 0xffffu) << 48) | ((unsigned long long)(unsigned)nunits << 24);
+}
+__host__ __device__ inline unsigned claim_pass(unsigned long long w) { return (unsigned)(w >> 48); }
+__host__ __device__ inline int claim_units(unsigned long long w) { return (int)((w >> 24) & 0xffffffu); }
+__host__ __device__ inline int claim_next(unsigned long long w) { return (int)(w & 0xffffffu); }
 
 }  // namespace stn

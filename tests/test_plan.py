@@ -439,9 +439,9 @@ def test_batched_unit_split_covers_each_problem_once(lib):
 
 def test_batched_entry_rejects_problems_beyond_its_counters(lib):
     """Checked on the host before any allocation or launch: a problem whose
-    units overflow a 32-bit count, and a batch whose scratch exceeds any
-    device's memory, are refused (no CUDA call is made, so this runs on the
-    CPU); the plan query refuses the former too."""
+    units per pass exceed what a slot's claim word counts (2^22), and a batch
+    whose scratch exceeds any device's memory, are refused (no CUDA call is
+    made, so this runs on the CPU); the plan query refuses the former too."""
     import ctypes
     from paper_2409_18824_gb300 import Problem, StencilError
     so = lib._lib
@@ -452,9 +452,14 @@ def test_batched_entry_rejects_problems_beyond_its_counters(lib):
     assert "work units" in lib.last_error()
     with pytest.raises(StencilError):
         lib.stencil_plan_query("batch_unit", 1 << 20, 1 << 20, 8, 8, 1)
-    # 400 problems of 2^20 x 2^16 x 8: each within its limits, 2.2e15 bytes in all
-    many = (Problem * 400)(*[Problem(1 << 20, 1 << 16, 8, None, fake + i * 4096) for i in range(400)])
-    assert so.jacobi_solve_batched_f64(many, 400, coeffs, 1, 1e-8, 10, 1, None, None) == -2
+    # 2^17 x 2^10 x 2^10: 4096 x 128 tiles x 8 chunks of 128 planes = 2^22 units, the most
+    # allowed; one more column of tiles is refused
+    assert lib.stencil_plan_query("batch_unit", 1 << 17, 1 << 10, 1 << 10, 8, 1)
+    with pytest.raises(StencilError):
+        lib.stencil_plan_query("batch_unit", (1 << 17) + 1, 1 << 10, 1 << 10, 8, 1)
+    # 1000 problems of that size: each within its limits, 1.1e15 bytes in all
+    many = (Problem * 1000)(*[Problem(1 << 17, 1 << 10, 1 << 10, None, fake + i * 4096) for i in range(1000)])
+    assert so.jacobi_solve_batched_f64(many, 1000, coeffs, 1, 1e-8, 10, 1, None, None) == -2
     assert "scratch" in lib.last_error()
 
 
