@@ -191,11 +191,19 @@ constexpr int kPlaneBytes = kPlaneElems * 8;
 constexpr int kStageElems = kPlaneElems + BT;  // plane with halo, then b
 template <int MINB>
 __host__ __device__ constexpr int ring_bytes() { return (MINB <= 4 ? 8 : 5) * kStageElems * 8; }
+// stages of T the ring holds (at most 12)
+template <typename T, int MINB>
+__host__ __device__ constexpr int ring_stages() {
+  return ring_bytes<MINB>() / (kStageElems * (int)sizeof(T)) > 12 ? 12
+                                                                  : ring_bytes<MINB>() / (kStageElems * (int)sizeof(T));
+}
+// planes in flight beyond those in use: two planes are computed per block
+// barrier when the ring leaves at least one plane in flight that way
+template <typename T, int MINB>
+__host__ __device__ constexpr bool ring_pairs() { return ring_stages<T, MINB>() >= 6; }
 template <typename T, int MINB>
 __host__ __device__ constexpr int ring_pf() {
-  return ring_bytes<MINB>() / (kStageElems * (int)sizeof(T)) - 3 > 8
-             ? 8
-             : ring_bytes<MINB>() / (kStageElems * (int)sizeof(T)) - 3;
+  return ring_pairs<T, MINB>() ? ring_stages<T, MINB>() - 5 : ring_stages<T, MINB>() - 3;
 }
 // the unit's shared buffer: the ring at radius 1, one plane at radius 2
 template <int R, int MINB>
@@ -285,6 +293,113 @@ __device__ __forceinline__ void star_tile_async(const T* u, const T* b, T* out, 
   *rsum_io = rsum;
 }
 
+// The same tile sweep with two planes per block barrier: the ring holds the
+// 2R+2 planes a pair reads and PF more in flight; each thread updates its
+// column at planes k and k+1 (k's residual term first, as in the one-plane
+// loop), which halves the waits and barriers per point and gives each thread
+// two independent updates to overlap.  Plane p sits in stage (p - first
+// staged plane) mod S; stage indices advance instead of being recomputed.
+template <typename T, bool HAS_B, bool HAS_C0, int MODE, int PF>
+__device__ __forceinline__ void star_tile_async2(const T* u, const T* b, T* out, int nx, int ny, int NX, int NY,
+                                                 int tile_x, int tile_y, int k0, int k1,
+                                                 const StarCoeffs<T, 1>& cf, int tw, int th, T* ring,
+                                                 double* rsum_io) {
+  using A = Arith<T>;
+  constexpr int R = 1, S = 2 * R + 3 + PF;
+  static_assert(PF >= 1, "at least one plane ahead");
+  const int flat = (int)(threadIdx.x + blockDim.x * threadIdx.y);
+  const int tx = flat % tw, ty = flat / tw;
+  const int pitch = tw + 2 * R;
+  const int gi = tile_x * tw + tx + R, gj = tile_y * th + ty + R;
+  const i64 sz = (i64)NX * NY;
+  const bool inx = gi < NX, iny = gj < NY;
+  const bool active = (gi < nx + R) && (gj < ny + R);
+  const bool hx = (tx < R) || (tx >= tw - R);
+  const int hx_i = (tx < R) ? gi - R : gi + R;
+  const int hx_lx = (tx < R) ? tx : tx + 2 * R;
+  const bool hx_ok = hx && hx_i < NX && iny;
+  const bool hy = (ty < R) || (ty >= th - R);
+  const int hy_j = (ty < R) ? gj - R : gj + R;
+  const int hy_ly = (ty < R) ? ty : ty + 2 * R;
+  const bool hy_ok = hy && hy_j < NY && inx;
+  const bool ld_c = inx && iny;
+  const int me = (ty + R) * pitch + tx + R;
+  const int hx_at = (ty + R) * pitch + hx_lx, hy_at = hy_ly * pitch + tx + R;
+  const i64 col = gi + (i64)gj * NX;
+  const T* pc = u + col;
+  const T* px = u + (hx_i + (i64)gj * NX);
+  const T* py = u + (gi + (i64)hy_j * NX);
+  const T* pb = HAS_B ? b + col : nullptr;
+  const int pfirst = k0 - R, plast = k1 - 1 + R;
+  int p_iss = pfirst, s_iss = 0;  // next plane to issue and its stage
+  auto issue_next = [&]() {  // every thread: its cells of the next plane (one commit group, maybe empty)
+    if (p_iss <= plast) {
+      T* st = ring + s_iss * kStageElems;
+      const i64 po = (i64)p_iss * sz;
+      if (ld_c) cp_el(st + me, pc + po, (int)sizeof(T));
+      if (hx_ok) cp_el(st + hx_at, px + po, (int)sizeof(T));
+      if (hy_ok) cp_el(st + hy_at, py + po, (int)sizeof(T));
+      if (HAS_B && active && p_iss >= k0 && p_iss < k1) cp_el(st + kPlaneElems + flat, pb + po, (int)sizeof(T));
+    }
+    cp_commit();
+    p_iss++;
+    s_iss = s_iss + 1 == S ? 0 : s_iss + 1;
+  };
+  // planes k0 - R .. k0 + R + PF before the first pair
+  for (int i = 0; i < 2 * R + 1 + PF; i++) issue_next();
+  double rsum = *rsum_io;
+  int sk = R;  // stage of plane k
+  T* outk = out + col + (i64)k0 * sz;
+  for (int k = k0; k < k1; k += 2) {
+    cp_wait<PF - 1>();  // this thread's copies of planes <= k + 1 + R have landed
+    __syncthreads();    // everyone's, and planes <= k - 1 - R are no longer read
+    issue_next();       // planes k + R + PF + 1 and + 2, into the stages of k - 2 - R and k - 1 - R
+    issue_next();
+    if (active) {
+      const int sm = sk == 0 ? S - 1 : sk - 1;
+      const int sp = sk + 1 == S ? 0 : sk + 1;
+      const int spp = sp + 1 == S ? 0 : sp + 1;
+      const T* c0p = ring + sk * kStageElems;
+      const T* cm = ring + sm * kStageElems;
+      const T* cp = ring + sp * kStageElems;
+      const T c = c0p[me];
+      const T c1 = cp[me];
+      {
+        const T sx = A::add(c0p[me - 1], c0p[me + 1]);
+        const T sy_ = A::add(c0p[me - pitch], c0p[me + pitch]);
+        const T szz = A::add(cm[me], c1);
+        T acc = A::mul(cf.c[1], A::add(A::add(sx, sy_), szz));
+        if (HAS_C0) acc = A::add(acc, A::mul(cf.c[0], c));
+        if (HAS_B) acc = A::add(acc, c0p[kPlaneElems + flat]);
+        if (MODE != kResidualOnly) outk[0] = acc;
+        if (MODE != kSweep) {
+          const double rho = (double)acc - (double)c;
+          rsum = __fma_rn(rho, rho, rsum);
+        }
+      }
+      if (k + 1 < k1) {
+        const T* cpp = ring + spp * kStageElems;
+        const T sx = A::add(cp[me - 1], cp[me + 1]);
+        const T sy_ = A::add(cp[me - pitch], cp[me + pitch]);
+        const T szz = A::add(c, cpp[me]);
+        T acc = A::mul(cf.c[1], A::add(A::add(sx, sy_), szz));
+        if (HAS_C0) acc = A::add(acc, A::mul(cf.c[0], c1));
+        if (HAS_B) acc = A::add(acc, cp[kPlaneElems + flat]);
+        if (MODE != kResidualOnly) outk[sz] = acc;
+        if (MODE != kSweep) {
+          const double rho = (double)acc - (double)c1;
+          rsum = __fma_rn(rho, rho, rsum);
+        }
+      }
+    }
+    sk = sk + 2 >= S ? sk + 2 - S : sk + 2;
+    outk += 2 * sz;
+  }
+  cp_wait<0>();
+  __syncthreads();  // the ring is free again when this returns
+  *rsum_io = rsum;
+}
+
 template <typename T, int R, bool HAS_C0, int MODE, int MINB>
 __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, const SchedProblem& P,
                                              const Geo& g, int q, const StarCoeffs<T, R>& cf, T* plane) {
@@ -297,6 +412,15 @@ __device__ __forceinline__ double unit_sweep(const T* cur, const T* b, T* nxt, c
   double rs = 0.0;
   if constexpr (R == 1) {
     // `plane` is the kernel's ring buffer at radius 1
+    if constexpr (ring_pairs<T, MINB>()) {
+      if (b)
+        star_tile_async2<T, true, HAS_C0, MODE, ring_pf<T, MINB>()>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0,
+                                                                    k1, cf, tw, BT / tw, plane, &rs);
+      else
+        star_tile_async2<T, false, HAS_C0, MODE, ring_pf<T, MINB>()>(cur, nullptr, nxt, P.nx, P.ny, NX, NY, txi,
+                                                                     tyi, k0, k1, cf, tw, BT / tw, plane, &rs);
+      return rs;
+    }
     if (b)
       star_tile_async<T, true, HAS_C0, MODE, ring_pf<T, MINB>()>(cur, b, nxt, P.nx, P.ny, NX, NY, txi, tyi, k0, k1, cf, tw, BT / tw,
                                              plane, &rs);
@@ -516,6 +640,24 @@ __device__ __forceinline__ int ld_acquire_sys_s32(const int* p) {
   return v;
 }
 
+// Takes unit q of the pass named by claim word w of slot si (one thread; q
+// is below the word's unit count).  The pass's state was written before the
+// word (release), and the pass cannot end while this unit is held, so the
+// state read after the fence is that pass's.  The check below cannot fail
+// under that protocol; if it did, the unit would be left unrun and the
+// batch would end by its idle limit (STN_ETIMEOUT) rather than run a unit
+// of the wrong pass.
+__device__ __forceinline__ int take_claim(const SchedArgs& a, int si, unsigned long long w, int q,
+                                          SchedSlot& s_state, SchedProblem& s_prob, int& s_unit) {
+  __threadfence();
+  const SchedSlot S = vload(&a.slots[si]);
+  if ((S.pass & 0xffffu) != claim_pass(w) || q >= S.nunits) return 0;
+  s_state = S;
+  s_prob = vload(&a.probs[S.problem]);
+  s_unit = q;
+  return 1;
+}
+
 // Publishes the next pass of slot si (one thread; the slot state for that
 // pass has been written).  Release: state writes before the word exchange.
 __device__ __forceinline__ void publish(const SchedArgs& a, int si) {
@@ -647,27 +789,36 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
     if (tid_flat() < 32) {
       // warp 0 looks at 32 slots per round trip (from the cursor on), then
       // tries the ones with units left in slot order, one lane at a time: the
-      // claim and its validation are those of a single thread's scan
+      // claim and its validation are those of a single thread's scan.
+      // (Starting each CTA's tries at a lane of its own spread the CTAs over
+      // the slots, but the refined 2048-solve mix ran 3 % slower.)
       const int lane = tid_flat();
-      // first the next unit of the last unit's pass: one atomic, and the
-      // slot state, the problem and the acquired grids stay those of that
-      // pass (pass ids of a slot only grow, so an equal id is the same pass)
-      int fast = 0;
+      // first the slot of the last unit: one atomic.  A unit of the same
+      // pass keeps the slot state, the problem and the acquired grids (pass
+      // ids of a slot only grow, so an equal id is the same pass); a unit of
+      // a later pass (the pass ended meanwhile) is taken like a scan's claim.
+      // Either must be run: a valid claim is never dropped.
+      int got = 0, fast = 0;
       if (sticky >= 0) {
         if (lane == 0) {
           const unsigned long long w = atomicAdd(&a.words[sticky], 1ull);
           const int q = claim_next(w);
-          if (claim_pass(w) == (s_state.pass & 0xffffu) && q < claim_units(w)) {
-            s_unit = q;
-            fast = 1;
+          if (q < claim_units(w)) {
+            if (claim_pass(w) == (s_state.pass & 0xffffu)) {
+              s_unit = q;
+              got = fast = 1;
+            } else {
+              got = take_claim(a, sticky, w, q, s_state, s_prob, s_unit);
+            }
           }
         }
+        got = __shfl_sync(0xffffffffu, got, 0);
         fast = __shfl_sync(0xffffffffu, fast, 0);
-        if (!fast) sticky = -1;
+        if (!got) sticky = -1;
       }
       // -1 none yet, -3 stop; lane 0 reads the error word so that every lane
       // takes the same path through the ballots below
-      int found = fast ? sticky : (lane == 0 && *(volatile int*)a.error != 0 ? -3 : -1);
+      int found = got ? sticky : (lane == 0 && *(volatile int*)a.error != 0 ? -3 : -1);
       found = __shfl_sync(0xffffffffu, found, 0);
       for (int base = 0; found == -1 && base < nslots; base += 32) {
         const int si = (cursor + base + lane) % nslots;
@@ -685,19 +836,7 @@ __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
           if (lane == l) {
             const unsigned long long w = atomicAdd(&a.words[si], 1ull);
             const int q = claim_next(w);
-            if (q < claim_units(w)) {
-              // a unit of the published pass: its state was written before
-              // the word (release), and the pass cannot end while this unit
-              // is held, so the state read after the fence is that pass's
-              __threadfence();
-              const SchedSlot S = vload(&a.slots[si]);
-              if ((S.pass & 0xffffu) == claim_pass(w) && q < S.nunits) {
-                s_state = S;
-                s_prob = vload(&a.probs[S.problem]);
-                s_unit = q;
-                ok = 1;
-              }
-            }
+            if (q < claim_units(w)) ok = take_claim(a, si, w, q, s_state, s_prob, s_unit);
           }
           if (__shfl_sync(0xffffffffu, ok, l)) found = __shfl_sync(0xffffffffu, si, l);
         }

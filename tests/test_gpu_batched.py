@@ -228,3 +228,37 @@ def test_graph_and_plain_launch_give_the_same_bits(lib, cuda):
         lib.stencil_tune_set("batch_graph", 1)
     assert outs[0][1] == outs[1][1]
     assert all(bitwise(a, b) for a, b in zip(outs[0][0], outs[1][0]))
+
+
+def test_small_half_of_the_mix_refined_completes(lib, cuda):
+    """The 1150 problems of the 2048-solve mix with at most 48^3 points, refined
+    (tol 1e-8, inner 1e-2 every 50 sweeps), in one scheduler launch.  Their
+    passes have one to a few units, so a CTA that goes back to the slot of its
+    last unit often finds the next pass already published; the unit it then
+    holds belongs to that pass and must be run (dropping it stalled the batch
+    until the idle limit).  Every solve must converge; for a sample, the
+    oracle's own residual of the result must be within tol and agree with the
+    reported one, and the same problems solved on their own must give the
+    same bits."""
+    import torch
+    sizes = [tuple(int(v) for v in s) for s in si.log_uniform_sizes(2048, 16, 128, 4)]
+    pick = [i for i, (nx, ny, nz) in enumerate(sizes) if nx * ny * nz <= 48 ** 3]
+    assert len(pick) == 1150
+    bs = [torch.from_numpy(si.normal_interior(*sizes[i], 1, seed=5 * 1000003 + i)).cuda() for i in pick]
+    us = [torch.zeros_like(b) for b in bs]
+    tol, inner_tol, K, outer = 1e-8, 1e-2, 50, 40
+    rc, infos = lib.jacobi_solve_batched_refined(us, bs, L7, 1, tol, 200000, inner_tol, K, outer)
+    assert rc == 0
+    assert all(i["status"] == 0 and i["rel_res"] <= tol for i in infos)
+    sample = (0, 1, len(pick) // 2, len(pick) - 1)
+    for j in sample:
+        b, got = to_host(bs[j]), to_host(us[j])
+        rel = oracle.residual_norm(got, L7, 1, b) / oracle.interior_norm(b, 1)
+        assert rel <= tol and abs(rel - infos[j]["rel_res"]) <= 1e-6 * tol, (j, sizes[pick[j]])
+    alone = [torch.zeros_like(bs[j]) for j in sample]
+    rc2, infos2 = lib.jacobi_solve_batched_refined(alone, [bs[j] for j in sample], L7, 1, tol, 200000, inner_tol, K,
+                                                   outer)
+    assert rc2 == 0
+    for n, j in enumerate(sample):
+        assert bitwise(to_host(alone[n]), to_host(us[j])), (j, sizes[pick[j]])
+        assert (infos2[n]["iters"], infos2[n]["outer"]) == (infos[j]["iters"], infos[j]["outer"])

@@ -505,3 +505,70 @@ def test_rejection_starts_one_row_past_65535_tiles(lib, op, esize, r):
         assert q["grid_y"] == 65535
     after = plan_or_rejected(lib, op, 1, 65535 * h + 1, 1, esize, r)
     assert after is None or (after["grid_y"] <= 65535 and after["tile_h"] > h)
+
+
+# The scheduler's radius-1 unit ring (sched.cu): stages of a 12 x 36 plane
+# with halo plus the tile's 256 source-term values; 8 double stages at 4
+# blocks per SM, 5 at 7; float stages are half the size, at most 12.
+SCHED_STAGE_ELEMS = 12 * 36 + 256
+
+
+def sched_ring(esize, minb):
+    nbytes = (8 if minb <= 4 else 5) * SCHED_STAGE_ELEMS * 8
+    stages = min(12, nbytes // (SCHED_STAGE_ELEMS * esize))
+    pairs = stages >= 6
+    return stages, pairs, stages - 5 if pairs else stages - 3
+
+
+def sched_ring_replay(k0, k1, S, pairs, PF):
+    """Replays a unit's ring: one cp.async commit group per issued plane slot
+    (empty past the last plane), cp.async.wait_group PF - 1 then a block
+    barrier per step, the step's issues into the stages its planes free, then
+    its reads.  Every read plane must have landed (its group is not among the
+    PF - 1 most recent) and still sit in its stage; an issue may only
+    overwrite a plane no step from this one on reads."""
+    R = 1
+    pfirst, plast = k0 - R, k1 - 1 + R
+    groups, stage = [], {}
+
+    def issue(p):
+        if p <= plast:
+            old = stage.get((p - pfirst) % S)
+            assert old is None or old == p - S
+            stage[(p - pfirst) % S] = p
+        groups.append(p)
+        return stage.get((p - pfirst) % S) if p <= plast else None
+
+    step = 2 if pairs else 1
+    for p in range(pfirst, pfirst + (2 * R + 1 + PF if pairs else S - 1)):
+        issue(p)
+    for k in range(k0, k1, step):
+        landed = set(g for g in groups[:len(groups) - (PF - 1)] if g <= plast)
+        reads = [k - 1, k, k + 1] + ([k + 2] if pairs and k + 1 < k1 else [])
+        first_read_now = k - 1
+        news = [k + R + PF + 1, k + R + PF + 2] if pairs else [k + R + PF]
+        for p in news:
+            if p <= plast:
+                assert p - S < first_read_now, ("overwrites a plane still read", p - S, k)
+            issue(p)
+        for p in reads:
+            assert pfirst <= p <= plast
+            assert p in landed, ("read before its copy landed", p, k)
+            assert stage[(p - pfirst) % S] == p, ("stage overwritten before its read", p, k)
+    assert sorted(set(g for g in groups if g <= plast)) == list(range(pfirst, plast + 1))
+
+
+@pytest.mark.parametrize("esize,minb", [(4, 7), (8, 7), (4, 4), (8, 4)])
+def test_sched_unit_ring_protocol(esize, minb):
+    S, pairs, PF = sched_ring(esize, minb)
+    assert PF >= 1 and S * SCHED_STAGE_ELEMS * esize <= (8 if minb <= 4 else 5) * SCHED_STAGE_ELEMS * 8
+    expect = {(4, 7): (10, True, 5), (8, 7): (5, False, 2), (4, 4): (12, True, 7), (8, 4): (8, True, 3)}
+    assert (S, pairs, PF) == expect[(esize, minb)]
+    for k0 in (1, 65, 129):
+        for n in range(1, 140):
+            sched_ring_replay(k0, k0 + n, S, pairs, PF)
+    # the replay catches a ring one stage too small, and a wait one group too lax
+    with pytest.raises(AssertionError):
+        sched_ring_replay(1, 40, S - 1, pairs, PF)
+    with pytest.raises(AssertionError):
+        sched_ring_replay(1, 40, S, pairs, PF + 1)
