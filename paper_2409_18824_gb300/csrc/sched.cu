@@ -38,7 +38,7 @@ namespace stn {
 namespace {
 
 constexpr int BT = TX * TY;
-constexpr int kSchedMinBlocksRefined = 7;
+constexpr int kSchedMinBlocksRefined = 5;
 constexpr int kSchedMinBlocksPlain = 4;
 
 enum Phase : int {
@@ -183,14 +183,17 @@ constexpr int kPlaneBytes = kPlaneElems * 8;
 // tile's plane with its halo and, after it, the source term of the tile's
 // points; z neighbours come from the neighbouring stages.  Every value and
 // operation is star_tile's, in its order, so the results are its bits.
-// The ring takes what the launch's blocks per SM leave of shared memory:
-// 8 double stages (44 KB) at 4 blocks per SM, 5 (27.5 KB) at 7.  Float
-// planes take half the bytes, so they run up to 8 planes ahead.  Enough
-// bytes in flight is what the units need: with loads two planes ahead they
-// were bound by memory latency.
+// The ring is 27.5 KB: 5 double stages or 10 float stages.  Larger rings
+// were slower on the refined 2048-solve mix at 5 blocks per SM (8 double
+// stages: 128.0 solves/s against 147.0; 4 stages: 147.8), most likely
+// because shared memory taken from the unified L1 leaves less cache for the
+// units' element-wise copies and the spills.
 constexpr int kStageElems = kPlaneElems + BT;  // plane with halo, then b
 template <int MINB>
-__host__ __device__ constexpr int ring_bytes() { return (MINB <= 4 ? 8 : 5) * kStageElems * 8; }
+__host__ __device__ constexpr int ring_bytes() {
+  static_assert(MINB * (5 * kStageElems * 8 + 1024 + 512) <= 233472, "the rings of MINB blocks fit an SM");
+  return 5 * kStageElems * 8;
+}
 // stages of T the ring holds (at most 12)
 template <typename T, int MINB>
 __host__ __device__ constexpr int ring_stages() {
@@ -765,12 +768,15 @@ __device__ void epilogue(const SchedArgs& a, int si, const SchedProblem& P, cons
   __syncthreads();
 }
 
-// MINB: blocks per SM the register allocation must allow.  Refined work
-// (float inner sweeps, latency-bound) runs faster with more resident warps:
-// with 7 blocks per SM a batch of 256 refined solves went from 68.7 to 101.9
-// solves/s, while double batches lost 3.6 % (measured); so refined launches
-// use MINB = 7 and double ones MINB = 4 (62 registers, no spills; leaving the
-// allocation unconstrained gave 96 registers and 2 blocks per SM).
+// MINB: blocks per SM the register allocation must allow.  With the plane
+// kernel's units, refined work (float inner sweeps) was latency-bound and ran
+// faster with more resident warps (a batch of 256 refined solves: 68.7 solves/s
+// at 4 blocks per SM, 101.9 at 7).  With the ring units, the refined
+// 2048-solve mix runs 132.7 solves/s at 7 blocks (32 registers, spills),
+// 128.9 at 6 (40), 147.0 at 5 (48 registers, few spills) and 143.0 at 4, so
+// refined launches use MINB = 5.  Double launches use MINB = 4 (64 registers,
+// no spills; bound by the FP64 pipe; leaving the allocation unconstrained gave
+// 96 registers and 2 blocks per SM).
 template <int R, bool HAS_C0, int MINB>
 __global__ void __launch_bounds__(BT, MINB) sched_kernel(SchedArgs a) {
   __shared__ __align__(16) unsigned char smem[unit_smem_bytes<R, MINB>()];

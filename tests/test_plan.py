@@ -508,13 +508,14 @@ def test_rejection_starts_one_row_past_65535_tiles(lib, op, esize, r):
 
 
 # The scheduler's radius-1 unit ring (sched.cu): stages of a 12 x 36 plane
-# with halo plus the tile's 256 source-term values; 8 double stages at 4
-# blocks per SM, 5 at 7; float stages are half the size, at most 12.
+# with halo plus the tile's 256 source-term values; 27.5 KB, 5 double stages
+# or 10 float stages, at both 4 and 5 blocks per SM.
 SCHED_STAGE_ELEMS = 12 * 36 + 256
 
 
 def sched_ring(esize, minb):
-    nbytes = (8 if minb <= 4 else 5) * SCHED_STAGE_ELEMS * 8
+    nbytes = 5 * SCHED_STAGE_ELEMS * 8
+    assert minb * (nbytes + 1024 + 512) <= 233472
     stages = min(12, nbytes // (SCHED_STAGE_ELEMS * esize))
     pairs = stages >= 6
     return stages, pairs, stages - 5 if pairs else stages - 3
@@ -558,11 +559,11 @@ def sched_ring_replay(k0, k1, S, pairs, PF):
     assert sorted(set(g for g in groups if g <= plast)) == list(range(pfirst, plast + 1))
 
 
-@pytest.mark.parametrize("esize,minb", [(4, 7), (8, 7), (4, 4), (8, 4)])
+@pytest.mark.parametrize("esize,minb", [(4, 5), (8, 5), (4, 4), (8, 4)])
 def test_sched_unit_ring_protocol(esize, minb):
     S, pairs, PF = sched_ring(esize, minb)
-    assert PF >= 1 and S * SCHED_STAGE_ELEMS * esize <= (8 if minb <= 4 else 5) * SCHED_STAGE_ELEMS * 8
-    expect = {(4, 7): (10, True, 5), (8, 7): (5, False, 2), (4, 4): (12, True, 7), (8, 4): (8, True, 3)}
+    assert PF >= 1 and S * SCHED_STAGE_ELEMS * esize <= 5 * SCHED_STAGE_ELEMS * 8
+    expect = {(4, 5): (10, True, 5), (8, 5): (5, False, 2), (4, 4): (10, True, 5), (8, 4): (5, False, 2)}
     assert (S, pairs, PF) == expect[(esize, minb)]
     for k0 in (1, 65, 129):
         for n in range(1, 140):
