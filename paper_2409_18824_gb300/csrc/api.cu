@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -58,6 +59,21 @@ static int grow(void** p, size_t* cap, size_t want) {
   STN_CUDA_TRY(e);
   *cap = want;
   return STN_OK;
+}
+
+void keep_pool_memory() {
+  static std::atomic<bool> done[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return;
+  }
+  if (done[dev].exchange(true)) return;
+  cudaMemPool_t pool;
+  unsigned long long keep = kPoolKeepBytes;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+    (void)cudaGetLastError();  // an optimisation only: allocations work without it
 }
 
 int get_workspace(cudaStream_t stream, i64 partials, size_t grid_bytes, Workspace** out) {
@@ -169,6 +185,7 @@ class Stager {
       a.dev = a.user;
     } else {
       any_host_ = true;
+      keep_pool_memory();
       cudaError_t e = cudaMallocAsync(&a.dev, bytes, s_);
       if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();

@@ -404,6 +404,7 @@ static int batched_clusters(const stn_problem* probs, i64 count, const double* c
   const size_t off_32 = off_64 + pool64 * sizeof(double);
   const size_t total = off_32 + pool32 * sizeof(float) + 256;
   char* base = nullptr;
+  keep_pool_memory();
   cudaError_t e = cudaMallocAsync((void**)&base, total, s);
   if (e == cudaErrorMemoryAllocation) {
     (void)cudaGetLastError();
@@ -613,6 +614,7 @@ static int batched_sched(const stn_problem* probs, i64 count, const double* coef
   for (i64 i = 0; i < count && refined; i++) o_e[i] = take(3 * sizeof(float) * ((npts[i] + 63) / 64 * 64));
   const size_t total = off + 256;
   char* base = nullptr;
+  keep_pool_memory();
   cudaError_t e = cudaMallocAsync((void**)&base, total, s);
   if (e == cudaErrorMemoryAllocation) {
     (void)cudaGetLastError();

@@ -52,6 +52,7 @@ int prepare(Worker& w, size_t need) {
     if (w.scratch) STN_CUDA_TRY(cudaFreeAsync(w.scratch, w.stream));
     w.scratch = nullptr;
     w.bytes = 0;
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(&w.scratch, need, w.stream);
     if (e == cudaErrorMemoryAllocation) {
       (void)cudaGetLastError();

@@ -74,6 +74,15 @@ struct Workspace {
   double* host_scalars = nullptr;  // pinned host mirror of scalars
 };
 
+// Lets the current device's default stream-ordered memory pool keep up to
+// kPoolKeepBytes of freed memory instead of returning it to the driver at
+// every synchronisation (its default), so the library's per-call
+// allocations (host-grid staging, batch scratch, served requests) reuse
+// mapped memory.  Once per device and process; the setting belongs to this
+// process's CUDA context and ends with it.
+constexpr unsigned long long kPoolKeepBytes = 16ull << 30;
+void keep_pool_memory();
+
 // Returns the workspace of the current device and `stream`, with at least
 // `partials` partial slots and (if grid_bytes > 0) a grid buffer of that size.
 int get_workspace(cudaStream_t stream, i64 partials, size_t grid_bytes, Workspace** ws);

@@ -449,6 +449,7 @@ stn_server* stn_server_create(const stn_server_opts* o) {
     return (stn_server*)nullptr;
   };
   if ((e = cudaGetDevice(&s->device))) return bad(e, "cudaGetDevice");
+  keep_pool_memory();
   if (o->engine == 1) {
     for (int w = 0; w < o->max_inflight; w++) {
       cudaStream_t st;
