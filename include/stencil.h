@@ -165,6 +165,20 @@ int stencil_release_workspace(void);
  *                   eight worker streams taking the problems largest first,
  *                   each solved as jacobi_solve_f64 / jacobi_solve_refined_f64
  *                   solve it alone (full-grid or resident kernels).
+ *   "resident3d":   1 (default): sweep loops of at least two sweeps over 3-D
+ *                   grids of at most 2^18 interior points (stencil_sweep_*,
+ *                   a solve's group of sweeps, the refined solver's inner
+ *                   loop, when no kernel variant, chunk count or tuning-cache
+ *                   entry is forced) run in one cooperative launch, sweeps
+ *                   separated by a bounded grid barrier; 0: per-sweep kernels.
+ *                   Same results.
+ *   "fp64_double_word": 0 (default): double sweeps take the canonical
+ *                   update.  1: radius-1 double sweeps without source term or
+ *                   centre coefficient evaluate the update in double-word
+ *                   float arithmetic on the FP32 pipe (error per sweep at most
+ *                   40 * 2^-48 of the largest |u| next to the point; NOT
+ *                   bitwise; points next to values outside the float split's
+ *                   range take the canonical update).
  *   "batch_graph":  the batch scheduler's persistent launch as a CUDA graph
  *                   captured and launched on the call's stream (1, default;
  *                   a failure to capture falls back to a plain launch), or a
@@ -182,6 +196,10 @@ int stencil_release_workspace(void);
  *   "fault_withhold_2d": 1 = the last band of a resident 2-D sweep never
  *                   publishes its rows, so its neighbour's wait runs out and
  *                   the call returns STN_ETIMEOUT.
+ *   "fault_withhold_3d": 1 = the last block of the next resident 3-D sweep
+ *                   launches never arrives at the grid barrier, so the other
+ *                   blocks' bounded waits run out and the next synchronising
+ *                   call on the stream returns STN_ETIMEOUT.
  *   "fault_admit_fail": the server's next N admission allocations fail
  *                   (retried later, like a busy pool); "fault_admit_failed"
  *                   (read only) counts the injected failures.
