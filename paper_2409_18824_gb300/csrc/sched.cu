@@ -83,17 +83,17 @@ __host__ __device__ inline Geo make_geo(int nx, int ny, int nz) {
   g.tiles_x = (nx + tw - 1) / tw;
   g.tiles_y = (ny + th - 1) / th;
   // k chunks sized from the extents alone (the unit split fixes the order of
-  // every reduction): aim at ~512 units per pass so a large problem can
-  // occupy the whole GPU, with chunks of 64..128 planes.  Measured on the
-  // 2048-solve mix (refined / FP64 solves/s): 16..64 planes, 2048 units:
-  // 90.6 / -; 32..64, 1024: 114.3 / 43.8; 64..128, 512: 125.4 / 45.1;
-  // 96..128: 125.7 / -; 128..256, 256: 127.5 / -.  Longer units cost less
-  // claiming (16 % -> 10 % of CTA cycles) and fewer pipeline start-ups; the
-  // shortest keep more units per pass for the large grids of a serving mix.
+  // every reduction): aim at ~256 units per pass, with chunks of 128..256
+  // planes.  Measured on the 2048-solve mix (refined / FP64 solves/s), with
+  // the plane kernel's units: 16..64 planes, 2048 units per pass: 90.6 / -;
+  // 32..64, 1024: 114.3 / 43.8; 64..128, 512: 125.4 / 45.1; 96..128: 125.7;
+  // 128..256, 256: 127.5.  With the ring units: 64..128, 512: 146.3-147.4 /
+  // 45.5; 128..256, 256: 151.4 / 45.9.  Longer units cost less claiming per
+  // point (22 % -> 16 % of CTA cycles, refined) and fewer ring start-ups.
   const long long tiles = (long long)g.tiles_x * g.tiles_y;
-  long long klen = ((long long)nz * tiles + 511) / 512;
-  if (klen < 64) klen = 64;
-  if (klen > 128) klen = 128;
+  long long klen = ((long long)nz * tiles + 255) / 256;
+  if (klen < 128) klen = 128;
+  if (klen > 256) klen = 256;
   if (klen > nz) klen = nz;
   g.klen = (int)klen;
   g.kc = (nz + g.klen - 1) / g.klen;

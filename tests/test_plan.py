@@ -411,7 +411,7 @@ def test_batched_unit_split_covers_each_problem_once(lib):
     (sizes log-uniform in [16, 128]), the serving mix ([32, 256]) and edge
     extents: the tiles and chunks cover the interior exactly once with no
     empty unit, the shape is the one with the fewest tiles (ties to the wider
-    rows), chunks are 64-128 planes (fewer only when nz is), and every shape's
+    rows), chunks are 128-256 planes (fewer only when nz is), and every shape's
     shared plane (tile plus a halo of 2 on each side) fits the kernel's one
     plane buffer.  The shape counts over the 2048 mix are those the
     scheduler's measurements were taken with: 1050, 420 and 578."""
@@ -429,7 +429,7 @@ def test_batched_unit_split_covers_each_problem_once(lib):
         tiles = {s: ceil_div(nx, w) * ceil_div(ny, 256 // w) for s, w in widths.items()}
         assert tiles[q["variant"]] == min(tiles.values())
         assert all(tiles[s] > tiles[q["variant"]] for s in range(q["variant"]))  # ties to the wider shape
-        assert q["kchunk"] <= 128 and (q["kchunk"] >= 64 or q["kchunk"] == nz)
+        assert q["kchunk"] <= 256 and (q["kchunk"] >= 128 or q["kchunk"] == nz)
         for w in widths.values():
             assert (256 // w + 4) * (w + 4) <= q["stage_elems"]
         if k < len(mix):
@@ -452,13 +452,13 @@ def test_batched_entry_rejects_problems_beyond_its_counters(lib):
     assert "work units" in lib.last_error()
     with pytest.raises(StencilError):
         lib.stencil_plan_query("batch_unit", 1 << 20, 1 << 20, 8, 8, 1)
-    # 2^17 x 2^10 x 2^10: 4096 x 128 tiles x 8 chunks of 128 planes = 2^22 units, the most
+    # 2^17 x 2^10 x 2^11: 4096 x 128 tiles x 8 chunks of 256 planes = 2^22 units, the most
     # allowed; one more column of tiles is refused
-    assert lib.stencil_plan_query("batch_unit", 1 << 17, 1 << 10, 1 << 10, 8, 1)
+    assert lib.stencil_plan_query("batch_unit", 1 << 17, 1 << 10, 1 << 11, 8, 1)
     with pytest.raises(StencilError):
-        lib.stencil_plan_query("batch_unit", (1 << 17) + 1, 1 << 10, 1 << 10, 8, 1)
-    # 1000 problems of that size: each within its limits, 1.1e15 bytes in all
-    many = (Problem * 1000)(*[Problem(1 << 17, 1 << 10, 1 << 10, None, fake + i * 4096) for i in range(1000)])
+        lib.stencil_plan_query("batch_unit", (1 << 17) + 1, 1 << 10, 1 << 11, 8, 1)
+    # 1000 problems of that size: each within its limits, 2.2e15 bytes in all
+    many = (Problem * 1000)(*[Problem(1 << 17, 1 << 10, 1 << 11, None, fake + i * 4096) for i in range(1000)])
     assert so.jacobi_solve_batched_f64(many, 1000, coeffs, 1, 1e-8, 10, 1, None, None) == -2
     assert "scratch" in lib.last_error()
 
