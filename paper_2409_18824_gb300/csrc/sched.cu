@@ -176,7 +176,8 @@ constexpr int kPlaneBytes = kPlaneElems * 8;
 // filled by element-wise asynchronous copies (cp.async.ca: the grids were
 // written by other CTAs in earlier passes, and the unit's acquire fence
 // precedes the copies as it preceded the loads), PF planes ahead of the
-// 2R+1 in use, with one block barrier per plane.  The per-plane tile sweep
+// 2R+1 in use, with one block barrier per plane (per two planes where the
+// ring has room: star_tile_async2, below).  The per-plane tile sweep
 // with a one-plane register prefetch (star_tile) spent most of its time at
 // its two barriers per plane and on long-scoreboard stalls: in ncu, 64 warps
 // per SM were resident and issued only 36 % of the cycles.  A stage holds the
