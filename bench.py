@@ -1660,6 +1660,10 @@ def extra_batched(stn, dev, refined, with_cpu):
            "gpu_launches": 1, "scheduler_counters": stn.stencil_sched_stats(), "clocks": clk.summary(),
            "roofline": {"bound": "latency", "note": "most grids stay in L2 (<= 17.6 MB per array); the scheduler's "
                         "unit sweeps are bound by latency and, in double, the FP64 pipe"}}
+    if not refined:
+        # every update of the FP64 batch is a canonical double sweep update
+        out["roofline"].update(fp64_pipe(6.0 * float((pts * iters).sum()), ms, load_peaks()[0],
+                                         "6 double ops per update over all sweeps of the batch"))
     if with_cpu:
         import oracle
         idx = list(range(0, 2048, 256)) + [int(np.argmax(pts))]
