@@ -573,3 +573,72 @@ def test_sched_unit_ring_protocol(esize, minb):
         sched_ring_replay(1, 40, S - 1, pairs, PF)
     with pytest.raises(AssertionError):
         sched_ring_replay(1, 40, S, pairs, PF + 1)
+
+
+def sched_unit_bounds_replay(nx, ny, nz, shape, q):
+    """The addresses of one scheduler unit's radius-1 ring sweep (sched.cu,
+    star_tile_async / star_tile_async2), replayed for every thread of the
+    block: each copy reads inside the padded grid and writes inside its
+    stage (plane with halo, then the tile's source-term values), every cell an
+    updating thread reads was written by some thread's copy, and every store
+    goes to an interior point of the unit's tile and planes."""
+    R, BT = 1, 256
+    tw = {0: 32, 1: 16, 2: 8}[shape]
+    th = BT // tw
+    NX, NY, NZ = nx + 2, ny + 2, nz + 2
+    tiles_x, tiles_y = ceil_div(nx, tw), ceil_div(ny, th)
+    tiles = tiles_x * tiles_y
+    klen = min(max(ceil_div(nz * tiles, 256), 128), 256, nz)
+    kci, tq = divmod(q, tiles)
+    tyi, txi = divmod(tq, tiles_x)
+    k0 = R + kci * klen
+    k1 = min(k0 + klen, nz + R)
+    pitch = tw + 2
+    plane_elems = (8 + 4) * (32 + 4)
+    written, reads, stores = set(), [], []
+    for flat in range(BT):
+        tx, ty = flat % tw, flat // tw
+        gi, gj = txi * tw + tx + R, tyi * th + ty + R
+        inx, iny = gi < NX, gj < NY
+        active = gi < nx + R and gj < ny + R
+        hx = tx < R or tx >= tw - R
+        hx_i = gi - R if tx < R else gi + R
+        hx_lx = tx if tx < R else tx + 2 * R
+        hx_ok = hx and hx_i < NX and iny
+        hy = ty < R or ty >= th - R
+        hy_j = gj - R if ty < R else gj + R
+        hy_ly = ty if ty < R else ty + 2 * R
+        hy_ok = hy and hy_j < NY and inx
+        me = (ty + R) * pitch + tx + R
+        copies = []
+        if inx and iny:
+            copies.append((me, gi, gj))
+        if hx_ok:
+            copies.append(((ty + R) * pitch + hx_lx, hx_i, gj))
+        if hy_ok:
+            copies.append((hy_ly * pitch + tx + R, gi, hy_j))
+        for cell, i, j in copies:
+            assert 0 <= cell < plane_elems and 0 <= i < NX and 0 <= j < NY
+            written.add(cell)
+        if active:
+            assert plane_elems + flat < plane_elems + BT
+            reads += [me, me - 1, me + 1, me - pitch, me + pitch]
+            stores.append((gi, gj))
+    for cell in reads:
+        assert cell in written, ("read of a cell no copy fills", cell)
+    for gi, gj in stores:
+        assert 1 <= gi <= nx and 1 <= gj <= ny
+    # planes copied: k0 - 1 .. k1 (the Dirichlet planes at the ends included)
+    assert 0 <= k0 - R and k1 - 1 + R <= NZ - 1 and k0 < k1
+
+
+@pytest.mark.parametrize("ext", [(16, 16, 16), (37, 19, 11), (130, 7, 40), (1, 1, 1), (33, 40, 3), (8, 30, 12),
+                                 (64, 20, 9), (123, 123, 122), (9, 300, 200), (300, 9, 130), (17, 256, 5)])
+def test_sched_unit_addresses_in_bounds(lib, ext):
+    nx, ny, nz = ext
+    p = lib.stencil_plan_query("batch_unit", nx, ny, nz, 8, 1)
+    shape = p["variant"]
+    n = p["grid_x"] * p["grid_y"] * p["grid_z"]
+    assert p["kchunk"] == min(max(ceil_div(nz * p["grid_x"] * p["grid_y"], 256), 128), 256, nz)
+    for q in sorted({0, 1, n // 2, n - 1} & set(range(n))):
+        sched_unit_bounds_replay(nx, ny, nz, shape, q)
