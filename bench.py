@@ -1128,41 +1128,29 @@ def cpu_sample_batched(sizes, seeds, pts, iters, n_sample=8, sweeps=1000):
                       f"{len(sizes)} solves ({total_s:.0f} s of oracle work)"}
 
 
-def run_varcoef(args):
-    """768x768x384 radius-2 variable-coefficient Poisson problem: per-sweep rates at
-    full size (float Jacobi sweep, double residual), and complete solves to a
-    1e-10 relative residual on a 96x96x48 grid of the same construction (FP32
-    sweeps with FP64 refinement vs plain FP64 Jacobi)."""
+def varcoef_problem(stn, dev, nx, ny, nz):
+    """The variable-coefficient workload's problem: a ~ U[0.5,1.5] (seed 3),
+    the (1,1,1) sine mode as the solution u*, f = A u* (device grids)."""
     import torch
-    import paper_2409_18824_gb300 as stn
+    W, R = si.VARCOEF_W, 2
+    a = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3)).to(dev)
+    ustar = torch.from_numpy(si.sine_mode(nx, ny, nz, R)).to(dev)
+    f = torch.zeros_like(ustar)
+    stn.varcoef_apply_f64(ustar, a, f, W, R)  # manufactured right-hand side f = A u*
+    return a, f, ustar
 
-    dev = torch.device("cuda", 0)
-    W = si.VARCOEF_W
-    R = 2
 
-    if args.kernel_only:
-        # the float variable-coefficient sweep alone at 512 x 512 x 256 (for profilers)
-        nx, ny, nz = 512, 512, 256
-        a32 = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3, dtype=np.float32)).to(dev)
-        f32 = torch.from_numpy(si.normal_interior(nx, ny, nz, R, seed=4, dtype=np.float32)).to(dev)
-        e0 = torch.zeros_like(f32)
-        e1 = torch.zeros_like(f32)
-        stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, args.kernel_only)
-        torch.cuda.synchronize()
-        return
+def varcoef_rates(stn, dev):
+    """Full-size (768 x 768 x 384) sweep rates, float and double, and the
+    complete refined and plain FP64 solves to 1e-10 on 96 x 96 x 48.  Returns
+    (measurements, the two solves, clocks, the 96 x 96 x 48 grids)."""
+    import torch
+    W, R = si.VARCOEF_W, 2
 
     def problem(nx, ny, nz):
-        a = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3)).to(dev)
-        ustar = torch.from_numpy(si.sine_mode(nx, ny, nz, R)).to(dev)
-        f = torch.zeros_like(ustar)
-        stn.varcoef_apply_f64(ustar, a, f, W, R)  # manufactured right-hand side f = A u*
-        return a, f, ustar
+        return varcoef_problem(stn, dev, nx, ny, nz)
 
     out = {"workload": "varcoef"}
-    full_solve = None
-    if not args.varcoef_reduced:
-        full_solve = varcoef_full_solve(stn, dev, problem, with_cpu=not args.no_cpu_baseline)
-        torch.cuda.empty_cache()
     with ClockSampler(0) as clk:
         # full size: rates
         nx, ny, nz = 768, 768, 384
@@ -1219,6 +1207,54 @@ def run_varcoef(args):
                          "outer": info["outer"], "err_vs_manufactured": err}
         out["reduced_96x96x48"] = res
         clocks = clk.summary()
+    return out, res, clocks, (a, f, ustar)
+
+
+def varcoef_roofline(fs):
+    """HBM roofline of the full-size float sweep (16 compulsory bytes per update)."""
+    peaks, peak_kind = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    # ncu on a 512 x 512 x 256 float sweep of the TMA-staged kernel: 837.3 MB
+    # read + 250.5 MB written for 67.1 M updates = 16.2 B per update, scaled to
+    # the full grid
+    return {"bound": "hbm", "achieved": fs["f32_sweep_hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": fs["f32_sweep_hbm_gbs"] / hbm_peak, "traffic": TRAFFIC_VARCOEF_F32_PER_LUP * 768 * 768 * 384,
+            "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
+            "kernel": "var_tma_kernel (TMA-staged float sweep, radius 2, one sweep at 768 x 768 x 384)",
+            "kernel_ms": fs["f32_sweep_ms"]}
+
+
+def run_varcoef(args):
+    """768x768x384 radius-2 variable-coefficient Poisson problem: per-sweep rates at
+    full size (float Jacobi sweep, double residual), and complete solves to a
+    1e-10 relative residual on a 96x96x48 grid of the same construction (FP32
+    sweeps with FP64 refinement vs plain FP64 Jacobi)."""
+    import torch
+    import paper_2409_18824_gb300 as stn
+
+    dev = torch.device("cuda", 0)
+    W = si.VARCOEF_W
+    R = 2
+
+    if args.kernel_only:
+        # the float variable-coefficient sweep alone at 512 x 512 x 256 (for profilers)
+        nx, ny, nz = 512, 512, 256
+        a32 = torch.from_numpy(si.uniform_full(nx, ny, nz, R, seed=3, dtype=np.float32)).to(dev)
+        f32 = torch.from_numpy(si.normal_interior(nx, ny, nz, R, seed=4, dtype=np.float32)).to(dev)
+        e0 = torch.zeros_like(f32)
+        e1 = torch.zeros_like(f32)
+        stn.varcoef_sweep_f32(e0, e1, a32, f32, W, R, args.kernel_only)
+        torch.cuda.synchronize()
+        return
+
+    def problem(nx, ny, nz):
+        return varcoef_problem(stn, dev, nx, ny, nz)
+
+    full_solve = None
+    if not args.varcoef_reduced:
+        full_solve = varcoef_full_solve(stn, dev, problem, with_cpu=not args.no_cpu_baseline)
+        torch.cuda.empty_cache()
+    out, res, clocks, (a, f, ustar) = varcoef_rates(stn, dev)
     ratio = res["plain_f64"]["seconds"] / res["refined"]["seconds"]
     # e2e: the refined solve through the C ABI with host (numpy) grids, copies included
     a_h, f_h, us_h = (t.cpu().numpy() for t in (a, f, ustar))
@@ -1226,17 +1262,7 @@ def run_varcoef(args):
     t0 = time.perf_counter()
     stn.jacobi_solve_varcoef_refined(a_h, f_h, u_h, W, R, 1e-10, 4000, 40)
     e2e_s = time.perf_counter() - t0
-    fs = out["full_size"]
-    peaks, peak_kind = load_peaks()
-    hbm_peak = float(peaks["hbm_gbs"])
-    # ncu on a 512 x 512 x 256 float sweep of the TMA-staged kernel: 837.3 MB
-    # read + 250.5 MB written for 67.1 M updates = 16.2 B per update, scaled to
-    # the full grid
-    roofline = {"bound": "hbm", "achieved": fs["f32_sweep_hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": fs["f32_sweep_hbm_gbs"] / hbm_peak, "traffic": TRAFFIC_VARCOEF_F32_PER_LUP * 768 * 768 * 384,
-                "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
-                "kernel": "var_tma_kernel (TMA-staged float sweep, radius 2, one sweep at 768 x 768 x 384)",
-                "kernel_ms": fs["f32_sweep_ms"]}
+    roofline = varcoef_roofline(out["full_size"])
     if full_solve is not None:
         fs_solve = full_solve
         line_metric = ("time to a 1e-10 relative residual, 768x768x384 variable-coefficient r=2 Poisson, "
@@ -1520,8 +1546,9 @@ def double_word_variant(stn, dev, u0, d_in, d_out, peaks):
 # ------------------------------------------ the metric's other configurations --
 # The default run adds, after the 512^3 headline, the other parts of the
 # benchmark metric under their own keys of the same JSON line: the 64^3
-# configuration ("c1"), the 2048-solve batch ("batched") and the serving loop
-# ("serving").  They run in this order within a wall-clock budget
+# configuration ("c1"), the variable-coefficient configuration's sweep rates
+# and reduced solves ("c3"), the 2048-solve batch ("batched") and the serving
+# loop ("serving").  They run in this order within a wall-clock budget
 # (--extras-budget); a part that would not fit is recorded as skipped.
 
 SERVE_REQUESTS = 200
@@ -1679,6 +1706,27 @@ def extra_batched(stn, dev, refined, with_cpu):
             "problems": idx, "max_rel_res": max(rels), "tol": tol, "all_within_tol": bool(max(rels) <= tol),
             "what": "the oracle's own FP64 residual ||S u + b - u|| / ||b|| of the returned u"}
     return out
+
+
+def extra_c3(stn, dev, with_cpu):
+    """The variable-coefficient configuration (768 x 768 x 384, radius 2,
+    a ~ U[0.5,1.5], manufactured sine solution): the full-size float sweep's
+    rate and HBM roofline, the double sweep and residual rates, and complete
+    refined and plain FP64 solves to 1e-10 on 96 x 96 x 48.  The full-size
+    solve to 1e-10 (about ten minutes) runs under --workload varcoef."""
+    import torch
+    out, res, clocks, _ = varcoef_rates(stn, dev)
+    torch.cuda.empty_cache()
+    fs = out["full_size"]
+    d = {"workload": "768x768x384 variable-coefficient 13-point Poisson, a ~ U[0.5,1.5] (seed 3), manufactured "
+                     "(1,1,1) sine solution: full-size float sweep rate; complete solves to 1e-10 on 96x96x48",
+         "value": fs["f32_sweep_glups"], "unit": "GLUP/s (float sweep, 768x768x384)",
+         "full_size": fs, "reduced_96x96x48": res,
+         "speedup_refined_vs_f64_96x96x48": res["plain_f64"]["seconds"] / res["refined"]["seconds"],
+         "roofline": varcoef_roofline(fs), "clocks": clocks}
+    if with_cpu:
+        d["cpu_baseline"] = cpu_sample_varcoef()
+    return d
 
 
 def serve_pool(stn, rhss, arrivals, tol, keep=()):
@@ -1857,6 +1905,7 @@ def run_extras(args, dev):
     with_cpu = not args.no_cpu_baseline
     out = {}
     for key, fn in (("c1", lambda: extra_c1(stn, dev, with_cpu)),
+                    ("c3", lambda: extra_c3(stn, dev, with_cpu)),
                     ("batched_refined", lambda: extra_batched(stn, dev, True, with_cpu)),
                     ("batched_f64", lambda: extra_batched(stn, dev, False, with_cpu)),
                     ("serving", lambda: extra_serving(stn, dev, deadline, with_cpu))):
