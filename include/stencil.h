@@ -459,18 +459,31 @@ int jacobi_solve_refined_f64(const double* rhs, double* u, int64_t nx, int64_t n
 
 /*
  * Batched solves: many independent problems of different extents (a C4-style
- * batch) in ONE persistent kernel launch of thread-block clusters.  Each
- * cluster takes the next problem (largest estimated work first) from a
- * device-side queue and iterates it to convergence; sweeps are separated by
- * the cluster's hardware barrier and convergence checks are reduced in a
- * fixed order, so every result is bitwise independent of the rest of the
- * batch and its sweeps are those of the single-problem path.
+ * batch) in ONE persistent kernel launch (captured in a CUDA graph and
+ * launched on `stream`; knob "batch_graph").  By default (knob
+ * "batch_engine" = 0) a dynamic work-unit scheduler runs one wave of CTAs:
+ * up to 96 problems are in flight at a time, largest estimated work first;
+ * each problem advances pass by pass (a sweep, a residual sweep or a
+ * refinement step), a pass is split into units (a tile of columns times a
+ * chunk of 128-256 planes, from the extents alone) that any CTA claims, and
+ * the CTA that completes a pass's last unit reduces its partials in unit
+ * order and publishes the next pass.  Every sweep is the single-problem
+ * path's canonical update and every reduction has a fixed order, so each
+ * result is bitwise independent of the rest of the batch.  Engine 1 gives
+ * each problem one thread-block cluster (sweeps separated by the cluster's
+ * barrier), engine 2 a pool of worker streams running the one-problem
+ * solves; both give the same iterates.
  *   probs   HOST array of `count` problems; their grids are DEVICE memory, each
  *           its own (problems must not share or overlap grids).
  *   infos   HOST array of `count` results (may be NULL).
- * The library allocates the scratch grids of the batch (stream-ordered) and
- * frees them before returning.  Synchronises `stream`.  Returns STN_OK when
- * every problem converged, STN_NOT_CONVERGED when one did not, or an error.
+ * Extents are at most 2^20 per axis and a problem at most 2^22 units per pass
+ * (STN_EINVAL otherwise); a batch whose scratch exceeds any device's memory
+ * returns STN_ENOMEM before any allocation.  The library allocates the
+ * scratch grids of the batch (stream-ordered) and frees them before
+ * returning.  Synchronises `stream`.  Returns STN_OK when every problem
+ * converged, STN_NOT_CONVERGED when one did not, STN_ETIMEOUT when the
+ * scheduler's CTAs found no work for the idle limit (a lost unit; never
+ * expected), or an error.
  */
 typedef struct stn_problem {
   int64_t nx, ny, nz;  /* interior extents */
