@@ -132,3 +132,21 @@ def test_lindley_single_server_fifo():
     assert bench.lindley([0.0, 10.0, 11.0], [1.0, 1.0, 1.0]) == [1.0, 1.0, 1.0]  # idle between arrivals
     assert bench.lindley([0.0, 0.5, 4.0], [1.0, 1.0, 1.0]) == [1.0, 1.5, 1.0]
     assert bench.lindley([], []) == []
+
+
+def test_roofline_helpers():
+    """The variable-coefficient line's HBM roofline (16 compulsory bytes per
+    update; traffic scaled from the 512 x 512 x 256 ncu capture) and the
+    FP64-pipe fraction used by the FP64 lines: achieved / peak, with the
+    peak derived from 2 double ops per clock per SM on 152 SMs."""
+    import bench
+    fs = {"f32_sweep_hbm_gbs": 4800.0, "f32_sweep_ms": 0.75}
+    r = bench.varcoef_roofline(fs)
+    peaks, _ = bench.load_peaks()
+    assert r["bound"] == "hbm" and r["achieved"] == 4800.0 and r["peak"] == float(peaks["hbm_gbs"])
+    assert abs(r["frac"] - 4800.0 / float(peaks["hbm_gbs"])) < 1e-12
+    assert abs(r["traffic"] / (768 * 768 * 384) - (837.3e6 + 250.5e6) / (512 * 512 * 256)) < 1e-9
+    p = bench.fp64_pipe(6.0 * 1e9, 10.0, {"sm_max_mhz": 2070.0}, "x")
+    assert abs(p["fp64_pipe_peak_tops"] - 2 * 152 * 2070e6 / 1e12) < 1e-12
+    assert abs(p["fp64_pipe_achieved_tops"] - 6e9 / 10e-3 / 1e12) < 1e-12
+    assert abs(p["fp64_pipe_frac"] - p["fp64_pipe_achieved_tops"] / p["fp64_pipe_peak_tops"]) < 1e-15
