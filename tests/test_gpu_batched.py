@@ -262,3 +262,40 @@ def test_small_half_of_the_mix_refined_completes(lib, cuda):
     for n, j in enumerate(sample):
         assert bitwise(to_host(alone[n]), to_host(us[j])), (j, sizes[pick[j]])
         assert (infos2[n]["iters"], infos2[n]["outer"]) == (infos[j]["iters"], infos[j]["outer"])
+
+
+def test_full_2048_mix_refined_sampled(lib, cuda):
+    """The refined batched workload at full size, in the configuration the
+    benchmark times: 2048 solves (the mix above), FP32 sweeps with FP64
+    refinement to 1e-8 (inner tolerance 1e-2, residual every 50 inner sweeps,
+    at most 40 outer steps), one persistent launch.  Every solve converges;
+    for a sample (the smallest, the largest and every 256th) the oracle's own
+    FP64 residual of the returned solution is within tol and matches the
+    reported one, and the smallest and largest solved alone give the same
+    bits."""
+    import torch
+    sizes = [tuple(int(v) for v in s) for s in si.log_uniform_sizes(2048, 16, 128, 4)]
+    tol = 1e-8
+    counts = [(nx + 2) * (ny + 2) * (nz + 2) for nx, ny, nz in sizes]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    d_b = torch.empty(int(offs[-1]), dtype=torch.float64, device="cuda")
+    for i, (nx, ny, nz) in enumerate(sizes):
+        d_b[offs[i]:offs[i + 1]] = torch.from_numpy(si.normal_interior(nx, ny, nz, 1, seed=5 * 1000003 + i).ravel())
+    d_u = torch.zeros_like(d_b)
+    us = [d_u[offs[i]:offs[i + 1]].view(nz + 2, ny + 2, nx + 2) for i, (nx, ny, nz) in enumerate(sizes)]
+    bs = [d_b[offs[i]:offs[i + 1]].view(nz + 2, ny + 2, nx + 2) for i, (nx, ny, nz) in enumerate(sizes)]
+    rc, infos = lib.jacobi_solve_batched_refined(us, bs, L7, 1, tol, 200000, 1e-2, 50, 40)
+    assert rc == 0
+    assert all(i["status"] == 0 and i["rel_res"] <= tol for i in infos)
+    pts = np.array([nx * ny * nz for nx, ny, nz in sizes])
+    small, large = int(np.argmin(pts)), int(np.argmax(pts))
+    for i in sorted({small, large, *range(0, 2048, 256)}):
+        b, got = to_host(bs[i]), to_host(us[i])
+        rel = oracle.residual_norm(got, L7, 1, b) / oracle.interior_norm(b, 1)
+        assert rel <= tol and abs(rel - infos[i]["rel_res"]) <= 1e-6 * tol, (i, sizes[i])
+    alone = [torch.zeros_like(bs[i]) for i in (small, large)]
+    rc2, infos2 = lib.jacobi_solve_batched_refined(alone, [bs[small], bs[large]], L7, 1, tol, 200000, 1e-2, 50, 40)
+    assert rc2 == 0
+    for n, i in enumerate((small, large)):
+        assert bitwise(to_host(alone[n]), to_host(us[i])), (i, sizes[i])
+        assert (infos2[n]["iters"], infos2[n]["outer"]) == (infos[i]["iters"], infos[i]["outer"])
